@@ -1,0 +1,174 @@
+/*
+ * mpfc.h -- C ABI of libmpfc, a GB300 (sm_103a) solver for the Modified Phase
+ * Field Crystal equation by the convex-splitting finite-difference schemes of
+ * Baskaran, Zhou, Hu, Wang, Wise and Lowengrub (arXiv:1208.2643), each time step
+ * solved by a nonlinear FAS multigrid V-cycle.
+ *
+ * Problem (Sec. 2, (2.4) and (2.9)): d_tt phi + beta d_t phi = M Delta mu,
+ *   mu = phi^3 + alpha phi + 2 Delta phi + Delta^2 phi, alpha = 1 - epsilon,
+ * on a periodic m x n cell-centred grid of spacing h (App. A).
+ *
+ * Conventions for every entry point:
+ *  - return value: MPFC_OK (0) or a negative MPFC_ERR_* status;
+ *  - grid functions are double arrays of m*n values, row-major, f[j*m + i], i the
+ *    x index; pointers are device pointers unless an argument says otherwise;
+ *  - calls are ordered on the CUDA stream given to mpfc_create; entry points that
+ *    return host results (mpfc_step, mpfc_step_cycles, mpfc_mass, mpfc_energy,
+ *    mpfc_get_state to host memory) synchronise that stream before returning;
+ *  - a handle allocates no device memory: everything lives in the workspace the
+ *    caller passes to mpfc_create (size from mpfc_workspace_bytes), which the
+ *    caller owns and must keep alive until mpfc_destroy.
+ */
+#ifndef MPFC_H
+#define MPFC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPFC_OK 0
+#define MPFC_ERR_INVALID (-1)       /* bad argument, grid size or parameter            */
+#define MPFC_ERR_WORKSPACE (-2)     /* workspace too small or misaligned                */
+#define MPFC_ERR_CUDA (-3)          /* a CUDA runtime call failed                       */
+#define MPFC_ERR_NOT_CONVERGED (-4) /* max_cycles V-cycles without reaching tol         */
+#define MPFC_ERR_DIVERGED (-5)      /* residual became non-finite or grew by > 1e10     */
+
+#define MPFC_FP64 0       /* every V-cycle kernel in FP64                                  */
+#define MPFC_FP32_INNER 1 /* FP64 outer defect correction around FP32 inner V-cycles       */
+
+#define MPFC_GUESS_PREV 0    /* phi^(0) = phi^k                                            */
+#define MPFC_GUESS_EXTRAP 1  /* phi^(0) = 2 phi^k - phi^{k-1}                              */
+#define MPFC_GUESS_LEARNED 2 /* extrapolation plus the learned correction (mpfc_set_guess_model) */
+
+typedef struct {
+  int m, n;          /* cells in x and y; the hierarchy halves both while they stay even
+                        and at least `coarsest` cells per side remain                    */
+  double h;          /* grid spacing (App. A), L_x = m h, L_y = n h                      */
+  double M;          /* mobility (Sec. 2)                                                 */
+  double epsilon;    /* alpha = 1 - epsilon (Sec. 2, (2.1))                               */
+  double beta;       /* damping (Sec. 2, (2.4))                                           */
+  double dt;         /* time step s (Sec. 3)                                              */
+  int nu1, nu2;      /* red-black sweeps before / after the coarse-grid correction        */
+  int coarsest;      /* minimum cells per side on the coarsest level (default 4)          */
+  double omega;      /* relaxation of the smoother's cell update: 1 = App. B as printed   */
+  double tol;        /* stop when sqrt(sum_{c,i,j} r_c^2 / (3 m n)) <= tol                */
+  int max_cycles;    /* V-cycle limit per step                                            */
+  int precision;     /* MPFC_FP64 or MPFC_FP32_INNER                                      */
+  int guess;         /* MPFC_GUESS_*                                                      */
+} mpfc_params;
+
+typedef struct {
+  int cycles;        /* V-cycles taken (outer iterations for MPFC_FP32_INNER)             */
+  int status;        /* MPFC_OK, MPFC_ERR_NOT_CONVERGED or MPFC_ERR_DIVERGED              */
+  double res0;       /* scaled residual of the initial guess                              */
+  double res_final;  /* scaled residual when the step stopped                             */
+} mpfc_step_info;
+
+typedef struct {
+  double F;          /* F(phi^k), Sec. 3 (3.1)                                            */
+  double pseudoF;    /* F + ||psi^k||_{-1}^2 / (2M), Sec. 3 (3.2)                         */
+  double tildeF;     /* pseudoF + ||grad_h(phi^k - phi^{k-1})||^2 / 2, Sec. 3.4 (3.26)     */
+} mpfc_energy_t;
+
+typedef struct mpfc_s mpfc_t;
+
+/* Fills p with the defaults: 64 x 64, h = 0.5, M = 1, epsilon = 0.025, beta = 0.9,
+ * dt = 0.01, V(2,2), coarsest 4, omega = 0.8, tol = 1e-10, max_cycles = 100, FP64,
+ * extrapolated guess. */
+void mpfc_default_params(mpfc_params* p);
+
+/* Workspace bytes a handle with these parameters needs (0 if the parameters are
+ * invalid).  The workspace must be device memory aligned to 256 bytes. */
+size_t mpfc_workspace_bytes(const mpfc_params* p);
+
+/* Creates a solver handle on `cuda_stream` (a cudaStream_t; NULL = legacy stream).
+ * The state is phi = 0, psi = 0 until mpfc_set_state.  Returns MPFC_ERR_INVALID for
+ * bad parameters, MPFC_ERR_WORKSPACE if `bytes` is short or d_workspace misaligned. */
+int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes, void* cuda_stream, mpfc_t** out);
+
+/* Releases the handle (its CUDA graphs and host memory; not the workspace). */
+void mpfc_destroy(mpfc_t* h);
+
+/* Sets the time-level state (phi^k, phi^{k-1}, psi^k) of Sec. 3.1/3.2 by copying.
+ * phi_prev NULL means phi^{-1} = phi^0 and psi NULL means psi^0 = 0, the start-up
+ * rule of Sec. 3.2.  Pointers may be host or device memory. */
+int mpfc_set_state(mpfc_t* h, const double* phi, const double* phi_prev, const double* psi);
+
+/* Copies the state out; any pointer may be NULL; host or device memory. */
+int mpfc_get_state(mpfc_t* h, double* phi, double* phi_prev, double* psi);
+
+/* Advances nsteps steps of scheme 1 (first order, Sec. 3.1, (3.6)-(3.9)) or scheme 2
+ * (second order, Sec. 3.2, (3.12)-(3.15)).  Each step builds the FAS source S of
+ * App. B.1/B.2, runs V-cycles until the scaled residual is at or below tol, and
+ * updates psi by (3.9) or (3.15).  A step that ends NOT_CONVERGED or DIVERGED leaves
+ * the state at the last good step and stops the remaining steps of the call; the
+ * first such status is returned.  per_step (nullable, nsteps entries, host memory)
+ * receives each step's record.  Synchronises the stream. */
+int mpfc_step(mpfc_t* h, int scheme, int nsteps, mpfc_step_info* per_step);
+
+/* One step with exactly ncycles V-cycles (no tolerance test), for lockstep
+ * comparisons.  Same state update and synchronisation as mpfc_step. */
+int mpfc_step_cycles(mpfc_t* h, int scheme, int ncycles, mpfc_step_info* info);
+
+/* Mass h^2 sum phi^k (conserved, Sec. 3.3, first theorem).  Synchronises. */
+int mpfc_mass(mpfc_t* h, double* out);
+
+/* Discrete energies of Sec. 3 at the current state.  The -1 norm of App. A,
+ * (A.16)-(A.18), comes from a periodic Poisson multigrid solve to 1e-13 relative
+ * residual.  Synchronises. */
+int mpfc_energy(mpfc_t* h, mpfc_energy_t* out);
+
+/* Message for a status code. */
+const char* mpfc_strerror(int status);
+
+/* Number of grid levels of the handle's hierarchy and the size of one level. */
+int mpfc_levels(const mpfc_t* h);
+int mpfc_level_size(const mpfc_t* h, int level, int* m, int* n, double* hl);
+
+/* ---------------------------------------------------------------------------
+ * Component entry points.  Each runs one building block of the V-cycle on caller
+ * arrays of the given level's size (device pointers, asynchronous on the handle's
+ * stream), with the handle's coefficients.  `phik` is phi^k on that level and is
+ * read only by scheme 2 (pass NULL for scheme 1).
+ * ------------------------------------------------------------------------- */
+
+/* S of App. B.1 (scheme 1) or App. B.2 (scheme 2) on the finest level. */
+int mpfc_op_source(mpfc_t* h, int scheme, const double* phik, const double* phikm1, const double* psik,
+                   double* S1, double* S2, double* S3);
+
+/* `sweeps` nonlinear red-black block Gauss-Seidel sweeps (App. B), red cells
+ * ((i+j) even) first; each cell: one local Newton linearisation of the cubic and a
+ * 3x3 solve by Cramer's rule, relaxed by omega. */
+int mpfc_op_smooth(mpfc_t* h, int scheme, int level, double* phi, double* mu, double* kappa, const double* S1,
+                   const double* S2, const double* S3, const double* phik, int sweeps);
+
+/* r = S - N(u), N of App. B.1/B.2. */
+int mpfc_op_residual(mpfc_t* h, int scheme, int level, const double* phi, const double* mu, const double* kappa,
+                     const double* S1, const double* S2, const double* S3, const double* phik, double* r1,
+                     double* r2, double* r3);
+
+/* FAS restriction from `level` to level+1: u_c = R u (2x2 average) and
+ * S_c = N_c(u_c) + R(S - N(u)).  phik_c is phi^k on level+1 (scheme 2). */
+int mpfc_op_restrict(mpfc_t* h, int scheme, int level, const double* phi, const double* mu, const double* kappa,
+                     const double* S1, const double* S2, const double* S3, const double* phik,
+                     const double* phik_c, double* phi_c, double* mu_c, double* kappa_c, double* S1_c,
+                     double* S2_c, double* S3_c);
+
+/* FAS correction of `level` from level+1: u += P(u_c_new - u_c_old), P the
+ * cell-centred bilinear interpolation. */
+int mpfc_op_prolong(mpfc_t* h, int level, const double* phi_c_new, const double* mu_c_new,
+                    const double* kappa_c_new, const double* phi_c_old, const double* mu_c_old,
+                    const double* kappa_c_old, double* phi, double* mu, double* kappa);
+
+/* Exact solve of N(u) = S on the coarsest level (Newton on the eliminated
+ * equation for phi; mu, kappa recovered from the second and third rows). */
+int mpfc_op_coarse_solve(mpfc_t* h, int scheme, double* phi, double* mu, double* kappa, const double* S1,
+                         const double* S2, const double* S3, const double* phik);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPFC_H */

@@ -1,0 +1,686 @@
+// FP64 kernels of the FAS V-cycle for the MPFC convex-splitting schemes.
+//
+// Every kernel works on one level of SoA planes (row-major [n][m], periodic wrap by
+// index arithmetic, App. A (A.8)-(A.9)).  On GB300 the FP64 pipe issues about 1.6
+// DFMA per clock per SM, so these kernels are bound by FP64 instruction issue, not
+// by HBM: they keep loads simple (L1-cached neighbour reads) and spend their effort
+// on the FP64 instruction count per cell.
+#pragma once
+
+#include "mpfc_common.cuh"
+
+namespace mpfc {
+
+// ---------------------------------------------------------------------------
+// Source S and initial guess (App. B.1 / B.2; guess: extrapolation of phi, then
+// kappa and mu chosen so that rows 2 and 3 of N(u) = S hold exactly).
+// ---------------------------------------------------------------------------
+struct SourceArgs {
+  const double* phik;
+  const double* phikm1;
+  const double* psik;
+  double psi_coef;   // 1/(beta+1/s) (scheme 1) or 2/(beta+2/s) (scheme 2)
+  double half_alpha; // alpha/2 (scheme 2)
+  int guess;         // 0 prev, 1 extrapolated, 2 given in L.phi already
+};
+
+template <int SCH>
+__global__ void k_source_guess(Lev L, SourceArgs A) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.m || j >= L.n) return;
+  int m = L.m;
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  size_t c = (size_t)j * m + i;
+  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
+  double ih2 = 1.0 / (L.h * L.h);
+  const double* pk = A.phik;
+  double p0 = pk[c];
+  double lap_k = ((pk[w] + pk[e]) + (pk[s] + pk[nn]) - 4.0 * p0) * ih2;
+  double q0 = A.phikm1[c];
+  if (SCH == 1) {
+    L.S1[c] = p0 + A.psi_coef * A.psik[c];
+    L.S2[c] = 2.0 * lap_k;
+    L.S3[c] = 0.0;
+  } else {
+    const double* pm = A.phikm1;
+    // phitilde = (3 phik - phikm1)/2 at the five points, then Delta_h of it
+    double t0 = 0.5 * (3.0 * p0 - q0);
+    double tw = 0.5 * (3.0 * pk[w] - pm[w]), te = 0.5 * (3.0 * pk[e] - pm[e]);
+    double ts = 0.5 * (3.0 * pk[s] - pm[s]), tn = 0.5 * (3.0 * pk[nn] - pm[nn]);
+    double lap_t = ((tw + te) + (ts + tn) - 4.0 * t0) * ih2;
+    L.S1[c] = p0 + A.psi_coef * A.psik[c];
+    L.S2[c] = A.half_alpha * p0 + 2.0 * lap_t;
+    L.S3[c] = 0.5 * lap_k;
+  }
+  if (A.guess == 0) L.phi[c] = p0;
+  else if (A.guess == 1) L.phi[c] = 2.0 * p0 - q0;
+}
+
+// kappa0 = S3 + theta Delta_h phi0
+__global__ void k_guess_kappa(Lev L, Coef k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.m || j >= L.n) return;
+  int m = L.m;
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  size_t c = (size_t)j * m + i;
+  const double* f = L.phi;
+  double sum = (f[(size_t)j * m + im] + f[(size_t)j * m + ip]) + (f[(size_t)jm * m + i] + f[(size_t)jp * m + i]);
+  L.ka[c] = L.S3[c] + k.th2 * (sum - 4.0 * f[c]);
+}
+
+// mu0 = S2 + g(phi0) + gam phi0 + Delta_h kappa0
+template <int SCH>
+__global__ void k_guess_mu(Lev L, Coef k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.m || j >= L.n) return;
+  int m = L.m;
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  size_t c = (size_t)j * m + i;
+  const double* f = L.ka;
+  double sum = (f[(size_t)j * m + im] + f[(size_t)j * m + ip]) + (f[(size_t)jm * m + i] + f[(size_t)jp * m + i]);
+  double p = L.phi[c];
+  double pk = (SCH == 2) ? L.pk[c] : 0.0;
+  L.mu[c] = L.S2[c] + g_of<SCH>(p, pk) + k.gam * p + k.ih2 * (sum - 4.0 * f[c]);
+}
+
+// ---------------------------------------------------------------------------
+// Red-black nonlinear block Gauss-Seidel half sweep (App. B.1 / B.2 smoothing
+// scheme).  Thread (x, j) visits cell i = 2x + ((j + color) & 1) of colour
+// `color` (0 = red, (i+j) even).  Cells of one colour only read the other colour,
+// so a half sweep is exactly parallel.
+// ---------------------------------------------------------------------------
+template <int SCH>
+__global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, int color) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int m = L.m;
+  if (x >= (m >> 1) || j >= L.n) return;
+  int i = 2 * x + ((j + color) & 1);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  size_t c = (size_t)j * m + i;
+  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
+  double* __restrict__ phi = L.phi;
+  double* __restrict__ mu = L.mu;
+  double* __restrict__ ka = L.ka;
+  // neighbours belong to the other colour: read-only during this launch
+  double smu = (__ldg(mu + w) + __ldg(mu + e)) + (__ldg(mu + s) + __ldg(mu + nn));
+  double ska = (__ldg(ka + w) + __ldg(ka + e)) + (__ldg(ka + s) + __ldg(ka + nn));
+  double sph = (__ldg(phi + w) + __ldg(phi + e)) + (__ldg(phi + s) + __ldg(phi + nn));
+  double p = phi[c];
+  double pk = (SCH == 2) ? __ldg(L.pk + c) : 0.0;
+  // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p)
+  double q = dg_of<SCH>(p, pk);
+  double eterm = g_of<SCH>(p, pk) - q * p;
+  double R1 = fma(k.cmu, smu, __ldg(L.S1 + c));
+  double R2 = fma(k.ih2, ska, __ldg(L.S2 + c) + eterm);
+  double R3 = fma(k.th2, sph, __ldg(L.S3 + c));
+  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]]
+  double det = fma(k.a, q, k.D0);
+  double rdet = 1.0 / det;
+  double nphi = fma(k.a, fma(k.b, R3, -R2), R1);
+  double nmu = fma(k.Q0 + q, R1, fma(-k.b, R3, R2));
+  double phin = nphi * rdet;
+  double mun = nmu * rdet;
+  double kan = fma(-k.b3, phin, R3);
+  if (k.omega != 1.0) {
+    double m0 = mu[c], k0 = ka[c];
+    phin = fma(k.omega, phin - p, p);
+    mun = fma(k.omega, mun - m0, m0);
+    kan = fma(k.omega, kan - k0, k0);
+  }
+  phi[c] = phin;
+  mu[c] = mun;
+  ka[c] = kan;
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = S - N(u) at one cell (App. B.1 / B.2 operator N).
+// ---------------------------------------------------------------------------
+template <int SCH>
+__device__ __forceinline__ void resid_at(const Lev& L, const Coef& k, int i, int j, double& r1, double& r2,
+                                         double& r3) {
+  int m = L.m;
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  size_t c = (size_t)j * m + i;
+  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
+  const double* phi = L.phi;
+  const double* mu = L.mu;
+  const double* ka = L.ka;
+  double p = __ldg(phi + c), u = __ldg(mu + c), v = __ldg(ka + c);
+  double smu = (__ldg(mu + w) + __ldg(mu + e)) + (__ldg(mu + s) + __ldg(mu + nn));
+  double ska = (__ldg(ka + w) + __ldg(ka + e)) + (__ldg(ka + s) + __ldg(ka + nn));
+  double sph = (__ldg(phi + w) + __ldg(phi + e)) + (__ldg(phi + s) + __ldg(phi + nn));
+  double pk = (SCH == 2) ? __ldg(L.pk + c) : 0.0;
+  // r1 = S1 - phi + c Delta_h mu
+  r1 = fma(k.cmu, fma(-4.0, u, smu), __ldg(L.S1 + c) - p);
+  // r2 = S2 - mu + g(phi) + gam phi + Delta_h kappa
+  r2 = fma(k.ih2, fma(-4.0, v, ska), fma(k.gam, p, __ldg(L.S2 + c) - u) + g_of<SCH>(p, pk));
+  // r3 = S3 - kappa + theta Delta_h phi
+  r3 = fma(k.th2, fma(-4.0, p, sph), __ldg(L.S3 + c) - v);
+}
+
+template <int SCH>
+__global__ void k_residual(Lev L, Coef k, double* r1, double* r2, double* r3) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.m || j >= L.n) return;
+  double a, b, c;
+  resid_at<SCH>(L, k, i, j, a, b, c);
+  size_t id = (size_t)j * L.m + i;
+  r1[id] = a;
+  r2[id] = b;
+  r3[id] = c;
+}
+
+// ---------------------------------------------------------------------------
+// FAS restriction, part 1: per coarse cell, the 2x2 averages of u and of the
+// fine residual.  u_c = R u (also kept in b), S_c = R r (part 2 adds N_c(u_c)).
+// ---------------------------------------------------------------------------
+template <int SCH>
+__global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.m || J >= C.n) return;
+  double sr1 = 0.0, sr2 = 0.0, sr3 = 0.0, sp = 0.0, sm = 0.0, sk = 0.0;
+#pragma unroll
+  for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+    for (int di = 0; di < 2; ++di) {
+      int i = 2 * I + di, j = 2 * J + dj;
+      double a, b, c;
+      resid_at<SCH>(F, kf, i, j, a, b, c);
+      sr1 += a;
+      sr2 += b;
+      sr3 += c;
+      size_t id = (size_t)j * F.m + i;
+      sp += __ldg(F.phi + id);
+      sm += __ldg(F.mu + id);
+      sk += __ldg(F.ka + id);
+    }
+  size_t cid = (size_t)J * C.m + I;
+  double up = 0.25 * sp, um = 0.25 * sm, uk = 0.25 * sk;
+  C.phi[cid] = up;
+  C.mu[cid] = um;
+  C.ka[cid] = uk;
+  if (keep_b) {
+    C.b1[cid] = up;
+    C.b2[cid] = um;
+    C.b3[cid] = uk;
+  }
+  C.S1[cid] = 0.25 * sr1;
+  C.S2[cid] = 0.25 * sr2;
+  C.S3[cid] = 0.25 * sr3;
+}
+
+// FAS restriction, part 2: S_c += N_c(u_c).
+template <int SCH>
+__global__ void k_tau(Lev C, Coef k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= C.m || j >= C.n) return;
+  int m = C.m;
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, C.n), jp = wrapm(j + 1, C.n);
+  size_t c = (size_t)j * m + i;
+  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
+  const double* phi = C.phi;
+  const double* mu = C.mu;
+  const double* ka = C.ka;
+  double p = phi[c], u = mu[c], v = ka[c];
+  double smu = (mu[w] + mu[e]) + (mu[s] + mu[nn]);
+  double ska = (ka[w] + ka[e]) + (ka[s] + ka[nn]);
+  double sph = (phi[w] + phi[e]) + (phi[s] + phi[nn]);
+  double pk = (SCH == 2) ? C.pk[c] : 0.0;
+  double N1 = fma(-k.cmu, fma(-4.0, u, smu), p);
+  double N2 = fma(-k.ih2, fma(-4.0, v, ska), fma(-k.gam, p, u) - g_of<SCH>(p, pk));
+  double N3 = fma(-k.th2, fma(-4.0, p, sph), v);
+  C.S1[c] += N1;
+  C.S2[c] += N2;
+  C.S3[c] += N3;
+}
+
+// Plain 2x2 average of one plane (phi^k onto the coarse levels, scheme 2).
+__global__ void k_restrict_plane(const double* __restrict__ f, double* __restrict__ c, int mc, int nc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= mc || J >= nc) return;
+  int mf = 2 * mc;
+  size_t a = (size_t)(2 * J) * mf + 2 * I, b = a + mf;
+  c[(size_t)J * mc + I] = 0.25 * ((f[a] + f[a + 1]) + (f[b] + f[b + 1]));
+}
+
+// ---------------------------------------------------------------------------
+// FAS correction: u_f += P(u_c - b_c), P the cell-centred bilinear stencil
+// (9, 3, 3, 1)/16.  One thread per coarse cell writes its 2x2 fine children.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, const double* __restrict__ co,
+                                              double* __restrict__ f, int mc, int nc, int I, int J) {
+  int Im = wrapm(I - 1, mc), Ip = wrapm(I + 1, mc), Jm = wrapm(J - 1, nc), Jp = wrapm(J + 1, nc);
+  auto E = [&](int a, int b) {
+    size_t id = (size_t)b * mc + a;
+    return __ldg(cn + id) - __ldg(co + id);
+  };
+  double e00 = E(I, J);
+  double eW = E(Im, J), eE = E(Ip, J), eS = E(I, Jm), eN = E(I, Jp);
+  double eSW = E(Im, Jm), eSE = E(Ip, Jm), eNW = E(Im, Jp), eNE = E(Ip, Jp);
+  const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
+  int mf = 2 * mc;
+  size_t f00 = (size_t)(2 * J) * mf + 2 * I;
+  size_t f01 = f00 + mf;
+  f[f00] += fma(w9, e00, fma(w3, eW + eS, w1 * eSW));
+  f[f00 + 1] += fma(w9, e00, fma(w3, eE + eS, w1 * eSE));
+  f[f01] += fma(w9, e00, fma(w3, eW + eN, w1 * eNW));
+  f[f01 + 1] += fma(w9, e00, fma(w3, eE + eN, w1 * eNE));
+}
+
+struct ProlongArgs {
+  const double *cphi, *cmu, *cka;   // coarse u after the coarse solve
+  const double *ophi, *omu, *oka;   // coarse R u_f before it
+  double *fphi, *fmu, *fka;         // fine u (in/out)
+  int mc, nc;
+};
+
+__global__ void k_prolong(ProlongArgs A) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= A.mc || J >= A.nc) return;
+  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, I, J);
+  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, I, J);
+  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, I, J);
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: Newton on the eliminated equation for phi,
+//   F(phi) = phi - c L (S2 + g(phi) + gam phi + L (S3 + theta L phi)) - S1 = 0,
+// with Jacobian J = K3 - c L diag(gam + g'(phi)), K3 = I - c theta L^3 built on the
+// host.  Dense Gaussian elimination with partial pivoting in shared memory, one
+// CTA.  Stops one iteration after the update falls below 1e-15 (1 + |phi|_inf);
+// at most 40 iterations.  mu and kappa are then recovered from rows 3 and 2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t) {
+  int i = t % m, j = t / m;
+  return (f[j * m + wrapm(i - 1, m)] + f[j * m + wrapm(i + 1, m)]) + (f[wrapm(j - 1, n) * m + i] + f[wrapm(j + 1, n) * m + i]);
+}
+
+template <int SCH>
+__global__ void k_coarse_solve(Lev C, Coef k, const double* __restrict__ K3) {
+  extern __shared__ double sm[];
+  const int m = C.m, n = C.n, G = m * n, W = G + 1;
+  double* Jm = sm;              // G x (G+1), last column = right-hand side
+  double* ph = Jm + G * W;
+  double* s1 = ph + G;
+  double* s2 = s1 + G;
+  double* s3 = s2 + G;
+  double* pk = s3 + G;
+  double* kap = pk + G;
+  double* muv = kap + G;
+  double* d = muv + G;
+  __shared__ int s_piv, s_stop, s_extra;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < G; t += nt) {
+    ph[t] = C.phi[t];
+    s1[t] = C.S1[t];
+    s2[t] = C.S2[t];
+    s3[t] = C.S3[t];
+    pk[t] = (SCH == 2) ? C.pk[t] : 0.0;
+  }
+  if (tid == 0) { s_stop = 0; s_extra = 0; }
+  __syncthreads();
+  for (int it = 0; it < 40; ++it) {
+    for (int t = tid; t < G; t += nt) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
+    __syncthreads();
+    for (int t = tid; t < G; t += nt)
+      muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t) - 4.0 * kap[t]);
+    __syncthreads();
+    for (int t = tid; t < G; t += nt) Jm[t * W + G] = s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t) - 4.0 * muv[t]);
+    for (int idx = tid; idx < G * G; idx += nt) {
+      int r = idx / G, col = idx % G;
+      int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
+      int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
+                (ci == ri && cj == wrapm(rj - 1, n)) + (ci == ri && cj == wrapm(rj + 1, n));
+      double Lrc = k.ih2 * ((double)cnt - (r == col ? 4.0 : 0.0));
+      Jm[r * W + col] = K3[idx] - k.c * Lrc * (k.gam + dg_of<SCH>(ph[col], pk[col]));
+    }
+    __syncthreads();
+    for (int col = 0; col < G; ++col) {
+      if (tid == 0) {
+        int piv = col;
+        double best = fabs(Jm[col * W + col]);
+        for (int r = col + 1; r < G; ++r) {
+          double v = fabs(Jm[r * W + col]);
+          if (v > best) { best = v; piv = r; }
+        }
+        s_piv = piv;
+      }
+      __syncthreads();
+      int piv = s_piv;
+      if (piv != col)
+        for (int c2 = col + tid; c2 <= G; c2 += nt) {
+          double t = Jm[col * W + c2];
+          Jm[col * W + c2] = Jm[piv * W + c2];
+          Jm[piv * W + c2] = t;
+        }
+      __syncthreads();
+      for (int r = col + 1 + tid; r < G; r += nt) d[r] = Jm[r * W + col] / Jm[col * W + col];
+      __syncthreads();
+      int rows = G - col - 1, cols = G - col;   // columns col+1 .. G
+      for (int idx = tid; idx < rows * cols; idx += nt) {
+        int r = col + 1 + idx / cols, c2 = col + 1 + idx % cols;
+        Jm[r * W + c2] -= d[r] * Jm[col * W + c2];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      for (int r = G - 1; r >= 0; --r) {
+        double acc = Jm[r * W + G];
+        for (int c2 = r + 1; c2 < G; ++c2) acc -= Jm[r * W + c2] * d[c2];
+        d[r] = acc / Jm[r * W + r];
+      }
+      double dmax = 0.0, umax = 0.0;
+      for (int t = 0; t < G; ++t) {
+        ph[t] += d[t];
+        dmax = fmax(dmax, fabs(d[t]));
+        umax = fmax(umax, fabs(ph[t]));
+      }
+      if (s_extra) s_stop = 1;
+      else if (dmax <= 1e-15 * (1.0 + umax)) s_extra = 1;
+      if (!(dmax == dmax)) s_stop = 1;
+    }
+    __syncthreads();
+    if (s_stop) break;
+  }
+  for (int t = tid; t < G; t += nt) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
+  __syncthreads();
+  for (int t = tid; t < G; t += nt) {
+    muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t) - 4.0 * kap[t]);
+    C.phi[t] = ph[t];
+    C.ka[t] = kap[t];
+  }
+  __syncthreads();
+  for (int t = tid; t < G; t += nt) C.mu[t] = muv[t];
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: per-block partial sums (fixed tree), then the last
+// block to finish adds the partials in index order.
+// ---------------------------------------------------------------------------
+template <int NS>
+__device__ __forceinline__ void block_sum(double (&v)[NS], double* red /* NS * 32 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[s] += __shfl_down_sync(0xffffffffu, v[s], o);
+  if (lane == 0)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) red[s * 32 + wid] = v[s];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = lane < nw ? red[s * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[s] = x;
+    }
+  }
+}
+
+// Returns true in the one thread (thread 0 of the last block) that holds the
+// totals in v after the call.
+template <int NS>
+__device__ __forceinline__ bool grid_sum(double (&v)[NS], double* partials, unsigned int* counter) {
+  __shared__ double red[NS * 32];
+  __shared__ bool last;
+  block_sum<NS>(v, red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) partials[s * kMaxPartials + blockIdx.x] = v[s];
+    __threadfence();
+    unsigned int done = atomicAdd(counter, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double w[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    w[s] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) w[s] += ((volatile double*)partials)[s * kMaxPartials + b];
+  }
+  block_sum<NS>(w, red);
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) v[s] = w[s];
+    return true;
+  }
+  return false;
+}
+
+// Scaled residual norm at the finest level, and the V-cycle loop decision.
+// mode 0: after the initial guess (sets res0); mode 1: after a V-cycle.
+template <int SCH>
+__global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double* partials, int mode,
+                                                 cudaGraphConditionalHandle hnd, int set_cond) {
+  double v[1] = {0.0};
+  int G = L.m * L.n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+    int i = t % L.m, j = t / L.m;
+    double a, b, c;
+    resid_at<SCH>(L, k, i, j, a, b, c);
+    v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));
+  }
+  if (!grid_sum<1>(v, partials, &ctl->counter)) return;
+  double res = sqrt(v[0] / (3.0 * (double)G));
+  int cond;
+  if (mode == 0) {
+    ctl->res0 = res;
+    ctl->res = res;
+    ctl->cycles = 0;
+    ctl->status = 0;
+  } else {
+    ctl->res = res;
+    ctl->cycles += 1;
+    if (!(res == res) || isinf(res) || res > 1e10 * fmax(ctl->res0, ctl->tol)) ctl->status = 2;
+  }
+  if (ctl->skip || ctl->status != 0) cond = 0;
+  else if (ctl->fixed_cycles > 0) cond = ctl->cycles < ctl->fixed_cycles;
+  else cond = (res > ctl->tol) && (ctl->cycles < ctl->max_cycles);
+  if (mode == 0 && !(res == res)) { ctl->status = 2; cond = 0; }
+  if (set_cond) cudaGraphSetConditional(hnd, cond ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Step bookkeeping and the psi update.
+// ---------------------------------------------------------------------------
+__global__ void k_step_begin(Ctl* ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctl->skip = ctl->halt;
+    ctl->cycles = 0;
+    ctl->status = 0;
+  }
+}
+
+__global__ void k_ctl_reset(Ctl* ctl, int fixed_cycles) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctl->halt = 0;
+    ctl->slot = 0;
+    ctl->fixed_cycles = fixed_cycles;
+    ctl->counter = 0u;
+  }
+}
+
+// Final status of a step: 0 ok, -4 not converged, -5 diverged.
+__device__ __forceinline__ int step_status(const Ctl* ctl) {
+  if (ctl->status == 2) return -5;
+  if (ctl->fixed_cycles <= 0 && !(ctl->res <= ctl->tol)) return -4;
+  return 0;
+}
+
+// psi^{k+1} = (phi - phi^k)/s (scheme 1, (3.9)) or (2/s)(phi - phi^k) - psi^k
+// (scheme 2, (3.15)); then phi^{k-1} <- phi^k, phi^k <- phi.  Skipped for a
+// failed or skipped step, which also halts the remaining steps of the call.
+template <int SCH>
+__global__ void k_commit(const double* __restrict__ phinew, double* phik, double* phikm1, double* psik, int G,
+                         double inv_s, Ctl* ctl, StepRecord* info) {
+  int st = step_status(ctl);
+  int skip = ctl->skip;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !skip) {
+    StepRecord r;
+    r.cycles = ctl->cycles;
+    r.status = st;
+    r.res0 = ctl->res0;
+    r.res_final = ctl->res;
+    info[ctl->slot] = r;
+    ctl->slot += 1;
+    if (st != 0) ctl->halt = 1;
+  }
+  if (skip || st != 0) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+    double pn = phinew[t], p0 = phik[t];
+    double ps = (SCH == 1) ? (pn - p0) * inv_s : 2.0 * inv_s * (pn - p0) - psik[t];
+    psik[t] = ps;
+    phikm1[t] = p0;
+    phik[t] = pn;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: mass and energy sums, periodic Poisson multigrid for the -1 norm.
+// ---------------------------------------------------------------------------
+__global__ void k_sum1(const double* __restrict__ f, int G, Ctl* ctl, double* partials) {
+  double v[1] = {0.0};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) v[0] += f[t];
+  if (grid_sum<1>(v, partials, &ctl->counter)) ctl->sums[0] = v[0];
+}
+
+// sums: 0 phi^4, 1 phi^2, 2 |grad phi|^2 (edge differences), 3 (Delta_h phi)^2 h^4,
+// 4 psi * xi, 5 |grad (phi - phi_prev)|^2
+__global__ void k_energy_sums(const double* __restrict__ phi, const double* __restrict__ phip,
+                              const double* __restrict__ psi, const double* __restrict__ xi, int m, int n, Ctl* ctl,
+                              double* partials) {
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  int G = m * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+    int i = t % m, j = t / m;
+    int ip = wrapm(i + 1, m), im = wrapm(i - 1, m), jp = wrapm(j + 1, n), jm = wrapm(j - 1, n);
+    double p = phi[t];
+    double pe = phi[j * m + ip], pw = phi[j * m + im], pn = phi[jp * m + i], ps = phi[jm * m + i];
+    double p2 = p * p;
+    v[0] += p2 * p2;
+    v[1] += p2;
+    double dx = pe - p, dy = pn - p;
+    v[2] += dx * dx + dy * dy;
+    double lap = (pe + pw) + (pn + ps) - 4.0 * p;
+    v[3] += lap * lap;
+    v[4] += psi[t] * xi[t];
+    double d0 = p - phip[t];
+    double ddx = (pe - phip[j * m + ip]) - d0, ddy = (pn - phip[jp * m + i]) - d0;
+    v[5] += ddx * ddx + ddy * ddy;
+  }
+  if (grid_sum<6>(v, partials, &ctl->counter))
+    for (int s = 0; s < 6; ++s) ctl->sums[s] = v[s];
+}
+
+// x = f - mean: the right-hand side of the mean-zero Poisson problem
+__global__ void k_sub_mean(const double* __restrict__ f, double* __restrict__ out, int G, const Ctl* ctl) {
+  double mean = ctl->sums[0] / (double)G;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) out[t] = f[t] - mean;
+}
+
+// Red-black Gauss-Seidel half sweep for -Delta_h x = f (periodic).
+__global__ void k_pois_smooth(double* __restrict__ x, const double* __restrict__ f, int m, int n, double h2,
+                              int color) {
+  int xi = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (xi >= (m >> 1) || j >= n) return;
+  int i = 2 * xi + ((j + color) & 1);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, n), jp = wrapm(j + 1, n);
+  double s = (x[j * m + im] + x[j * m + ip]) + (x[jm * m + i] + x[jp * m + i]);
+  x[j * m + i] = 0.25 * (s + h2 * f[j * m + i]);
+}
+
+// coarse f = R (f + Delta_h x), coarse x = 0; also the sum of squared fine residuals
+__global__ void k_pois_restrict(const double* __restrict__ x, const double* __restrict__ f, double* __restrict__ fc,
+                                double* __restrict__ xc, int mc, int nc, double ih2) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= mc || J >= nc) return;
+  int m = 2 * mc, n = 2 * nc;
+  double acc = 0.0;
+  for (int dj = 0; dj < 2; ++dj)
+    for (int di = 0; di < 2; ++di) {
+      int i = 2 * I + di, j = 2 * J + dj;
+      int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, n), jp = wrapm(j + 1, n);
+      double lap = ((x[j * m + im] + x[j * m + ip]) + (x[jm * m + i] + x[jp * m + i]) - 4.0 * x[j * m + i]) * ih2;
+      acc += f[j * m + i] + lap;
+    }
+  fc[J * mc + I] = 0.25 * acc;
+  xc[J * mc + I] = 0.0;
+}
+
+__global__ void k_pois_prolong(const double* __restrict__ xc, double* __restrict__ x, int mc, int nc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= mc || J >= nc) return;
+  int Im = wrapm(I - 1, mc), Ip = wrapm(I + 1, mc), Jm = wrapm(J - 1, nc), Jp = wrapm(J + 1, nc);
+  auto X = [&](int a, int b) { return xc[b * mc + a]; };
+  double e00 = X(I, J), eW = X(Im, J), eE = X(Ip, J), eS = X(I, Jm), eN = X(I, Jp);
+  double eSW = X(Im, Jm), eSE = X(Ip, Jm), eNW = X(Im, Jp), eNE = X(Ip, Jp);
+  const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
+  int mf = 2 * mc;
+  size_t f00 = (size_t)(2 * J) * mf + 2 * I, f01 = f00 + mf;
+  x[f00] += fma(w9, e00, fma(w3, eW + eS, w1 * eSW));
+  x[f00 + 1] += fma(w9, e00, fma(w3, eE + eS, w1 * eSE));
+  x[f01] += fma(w9, e00, fma(w3, eW + eN, w1 * eNW));
+  x[f01 + 1] += fma(w9, e00, fma(w3, eE + eN, w1 * eNE));
+}
+
+// Coarsest Poisson level: `sweeps` red-black sweeps in one CTA, then the mean removed.
+__global__ void k_pois_coarse(double* x, const double* f, int m, int n, double h2, int sweeps) {
+  extern __shared__ double xs[];
+  int G = m * n;
+  for (int t = threadIdx.x; t < G; t += blockDim.x) xs[t] = x[t];
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int color = 0; color < 2; ++color) {
+      for (int t = threadIdx.x; t < G; t += blockDim.x) {
+        int i = t % m, j = t / m;
+        if (((i + j) & 1) != color) continue;
+        xs[t] = 0.25 * (nbsum_s(xs, m, n, t) + h2 * f[t]);
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) {
+    double mean = 0.0;
+    for (int t = 0; t < G; ++t) mean += xs[t];
+    xs[G] = mean / G;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < G; t += blockDim.x) x[t] = xs[t] - xs[G];
+}
+
+// sum of squared residuals of -Delta_h x = f, and sum of f^2
+__global__ void k_pois_resnorm(const double* __restrict__ x, const double* __restrict__ f, int m, int n, double ih2,
+                               Ctl* ctl, double* partials) {
+  double v[2] = {0.0, 0.0};
+  int G = m * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+    int i = t % m, j = t / m;
+    int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, n), jp = wrapm(j + 1, n);
+    double lap = ((x[j * m + im] + x[j * m + ip]) + (x[jm * m + i] + x[jp * m + i]) - 4.0 * x[t]) * ih2;
+    double r = f[t] + lap;
+    v[0] += r * r;
+    v[1] += f[t] * f[t];
+  }
+  if (grid_sum<2>(v, partials, &ctl->counter)) {
+    ctl->sums[0] = v[0];
+    ctl->sums[1] = v[1];
+  }
+}
+
+}  // namespace mpfc

@@ -1,0 +1,763 @@
+// libmpfc: host driver and C ABI (see include/mpfc.h).
+//
+// A handle carves every device array out of the caller's workspace, builds one
+// CUDA graph per scheme for a whole time step (source, guess, a conditional WHILE
+// node that runs V-cycles until the device-side residual test fails, and the psi
+// update), and replays it once per step.  No host synchronisation happens inside a
+// step; the residual test, cycle counting and divergence detection run on the GPU.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/mpfc.h"
+#include "fp64_kernels.cuh"
+#include "mpfc_internal.h"
+
+using namespace mpfc;
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t err_ = (call);                                \
+    if (err_ != cudaSuccess) {                                \
+      mpfc_set_cuda_error(err_, #call, __FILE__, __LINE__);   \
+      return MPFC_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
+static char g_last_cuda_error[512];
+
+void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+}
+
+extern "C" const char* mpfc_last_cuda_error(void) { return g_last_cuda_error; }
+
+// ---------------------------------------------------------------------------
+// Parameters, hierarchy, coefficients
+// ---------------------------------------------------------------------------
+extern "C" void mpfc_default_params(mpfc_params* p) {
+  memset(p, 0, sizeof(*p));
+  p->m = 64;
+  p->n = 64;
+  p->h = 0.5;
+  p->M = 1.0;
+  p->epsilon = 0.025;
+  p->beta = 0.9;
+  p->dt = 0.01;
+  p->nu1 = 2;
+  p->nu2 = 2;
+  p->coarsest = 4;
+  p->omega = 0.8;
+  p->tol = 1e-10;
+  p->max_cycles = 100;
+  p->precision = MPFC_FP64;
+  p->guess = MPFC_GUESS_EXTRAP;
+}
+
+// Halve while both sides stay even and keep at least `coarsest` cells.
+int mpfc_num_levels(int m, int n, int coarsest) {
+  int L = 1;
+  while (L < kMaxLevels && m % 2 == 0 && n % 2 == 0 && m / 2 >= coarsest && n / 2 >= coarsest && (m / 2) % 2 == 0 &&
+         (n / 2) % 2 == 0) {
+    m /= 2;
+    n /= 2;
+    ++L;
+  }
+  return L;
+}
+
+static bool params_valid(const mpfc_params* p) {
+  if (!p) return false;
+  if (p->m < 4 || p->n < 4 || p->m % 2 || p->n % 2) return false;
+  if (!(p->h > 0) || !(p->M > 0) || !(p->beta >= 0) || !(p->dt > 0) || !(p->epsilon <= 1.0)) return false;
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1 || p->coarsest < 2) return false;
+  if (!(p->omega > 0 && p->omega <= 1.0)) return false;
+  if (!(p->tol >= 0) || p->max_cycles < 1) return false;
+  if (p->precision != MPFC_FP64 && p->precision != MPFC_FP32_INNER) return false;
+  if (p->guess < MPFC_GUESS_PREV || p->guess > MPFC_GUESS_LEARNED) return false;
+  int L = mpfc_num_levels(p->m, p->n, p->coarsest);
+  int mc = p->m >> (L - 1), nc = p->n >> (L - 1);
+  if (mc * nc > kMaxCoarseCells) return false;
+  if ((size_t)p->m * (size_t)p->n > ((size_t)1 << 31)) return false;
+  return true;
+}
+
+Coef mpfc_coef(const mpfc_params* p, int scheme, double h) {
+  Coef k;
+  double alpha = 1.0 - p->epsilon;
+  if (scheme == 1) {
+    k.c = p->dt * p->M / (p->beta + 1.0 / p->dt);
+    k.gam = alpha;
+    k.theta = 1.0;
+  } else {
+    k.c = p->dt * p->M / (p->beta + 2.0 / p->dt);
+    k.gam = 0.5 * alpha;
+    k.theta = 0.5;
+  }
+  k.omega = p->omega;
+  double h2 = h * h;
+  k.cmu = k.c / h2;
+  k.a = 4.0 * k.c / h2;
+  k.ih2 = 1.0 / h2;
+  k.b = 4.0 / h2;
+  k.b3 = 4.0 * k.theta / h2;
+  k.th2 = k.theta / h2;
+  k.D0 = 1.0 + k.a * k.gam + k.a * k.b * k.b3;
+  k.Q0 = k.gam + k.b * k.b3;
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carver {
+  char* base;
+  size_t off;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off = align256(off + count * sizeof(T));
+    return p;
+  }
+};
+
+// Walks the layout; with base == nullptr only computes the size.
+static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
+  Carver c{base, 0};
+  int L = mpfc_num_levels(p->m, p->n, p->coarsest);
+  size_t G0 = (size_t)p->m * p->n;
+  Ctl* ctl = c.take<Ctl>(1);
+  double* partials = c.take<double>((size_t)kMaxSums * kMaxPartials);
+  StepRecord* info = c.take<StepRecord>(kInfoCap);
+  double* phik = c.take<double>(G0);
+  double* phikm1 = c.take<double>(G0);
+  double* psik = c.take<double>(G0);
+  int m = p->m, n = p->n;
+  double h = p->h;
+  Lev lev[kMaxLevels];
+  double *px[kMaxLevels], *pf[kMaxLevels];
+  for (int l = 0; l < L; ++l) {
+    size_t G = (size_t)m * n;
+    Lev& v = lev[l];
+    v.m = m;
+    v.n = n;
+    v.h = h;
+    v.phi = c.take<double>(G);
+    v.mu = c.take<double>(G);
+    v.ka = c.take<double>(G);
+    v.S1 = c.take<double>(G);
+    v.S2 = c.take<double>(G);
+    v.S3 = c.take<double>(G);
+    if (l > 0) {
+      v.b1 = c.take<double>(G);
+      v.b2 = c.take<double>(G);
+      v.b3 = c.take<double>(G);
+      v.pk = c.take<double>(G);
+    } else {
+      v.b1 = v.b2 = v.b3 = nullptr;
+      v.pk = phik;
+    }
+    px[l] = c.take<double>(G);
+    pf[l] = c.take<double>(G);
+    m /= 2;
+    n /= 2;
+    h *= 2.0;
+  }
+  int Gc = lev[L - 1].m * lev[L - 1].n;
+  double* K3a = c.take<double>((size_t)Gc * Gc);
+  double* K3b = c.take<double>((size_t)Gc * Gc);
+  size_t extra = mpfc_fp32_carve(H, p, &c.off, base, L);
+  (void)extra;
+  if (H && base) {
+    H->nlev = L;
+    H->ctl = ctl;
+    H->partials = partials;
+    H->info = info;
+    H->phik = phik;
+    H->phikm1 = phikm1;
+    H->psik = psik;
+    for (int l = 0; l < L; ++l) {
+      H->lev[l] = lev[l];
+      H->px[l] = px[l];
+      H->pf[l] = pf[l];
+    }
+    H->K3[0] = K3a;
+    H->K3[1] = K3b;
+  }
+  return c.off;
+}
+
+extern "C" size_t mpfc_workspace_bytes(const mpfc_params* p) {
+  if (!params_valid(p)) return 0;
+  return carve(nullptr, p, nullptr);
+}
+
+// K3 = I - c theta L^3 on the coarsest grid (dense, row-major G x G).
+static void build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
+  int m = C.m, n = C.n, G = m * n;
+  std::vector<double> Lm((size_t)G * G, 0.0), L2((size_t)G * G, 0.0), L3((size_t)G * G, 0.0);
+  double ih2 = 1.0 / (C.h * C.h);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < m; ++i) {
+      int r = j * m + i;
+      Lm[(size_t)r * G + r] -= 4.0 * ih2;
+      int nb[4] = {j * m + (i + m - 1) % m, j * m + (i + 1) % m, ((j + n - 1) % n) * m + i, ((j + 1) % n) * m + i};
+      for (int t = 0; t < 4; ++t) Lm[(size_t)r * G + nb[t]] += ih2;
+    }
+  for (int r = 0; r < G; ++r)
+    for (int t = 0; t < G; ++t) {
+      double a = Lm[(size_t)r * G + t];
+      if (a == 0.0) continue;
+      for (int c2 = 0; c2 < G; ++c2) L2[(size_t)r * G + c2] += a * Lm[(size_t)t * G + c2];
+    }
+  for (int r = 0; r < G; ++r)
+    for (int t = 0; t < G; ++t) {
+      double a = L2[(size_t)r * G + t];
+      if (a == 0.0) continue;
+      for (int c2 = 0; c2 < G; ++c2) L3[(size_t)r * G + c2] += a * Lm[(size_t)t * G + c2];
+    }
+  K3.assign((size_t)G * G, 0.0);
+  for (int r = 0; r < G; ++r)
+    for (int c2 = 0; c2 < G; ++c2)
+      K3[(size_t)r * G + c2] = (r == c2 ? 1.0 : 0.0) - k.c * k.theta * L3[(size_t)r * G + c2];
+}
+
+extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes, void* cuda_stream, mpfc_t** out) {
+  if (!out) return MPFC_ERR_INVALID;
+  *out = nullptr;
+  if (!params_valid(p)) return MPFC_ERR_INVALID;
+  size_t need = carve(nullptr, p, nullptr);
+  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255)) return MPFC_ERR_WORKSPACE;
+  mpfc_s* H = new mpfc_s();
+  H->p = *p;
+  H->stream = (cudaStream_t)cuda_stream;
+  H->ws = (char*)d_workspace;
+  H->ws_bytes = bytes;
+  carve(H, p, (char*)d_workspace);
+  for (int s = 0; s < 2; ++s)
+    for (int l = 0; l < H->nlev; ++l) H->coef[s][l] = mpfc_coef(p, s + 1, H->lev[l].h);
+  int rc = MPFC_OK;
+  do {
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&H->body_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      mpfc_set_cuda_error(e, "cudaStreamCreate", __FILE__, __LINE__);
+      rc = MPFC_ERR_CUDA;
+      break;
+    }
+    Ctl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.tol = p->tol;
+    c0.max_cycles = p->max_cycles;
+    size_t G0 = (size_t)p->m * p->n;
+    const Lev& C = H->lev[H->nlev - 1];
+    std::vector<double> K3;
+    if ((e = cudaMemcpyAsync(H->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, H->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(H->phik, 0, G0 * sizeof(double), H->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(H->phikm1, 0, G0 * sizeof(double), H->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(H->psik, 0, G0 * sizeof(double), H->stream)) != cudaSuccess) {
+      mpfc_set_cuda_error(e, "initialise workspace", __FILE__, __LINE__);
+      rc = MPFC_ERR_CUDA;
+      break;
+    }
+    for (int s = 0; s < 2 && rc == MPFC_OK; ++s) {
+      build_K3(C, H->coef[s][H->nlev - 1], K3);
+      if ((e = cudaMemcpyAsync(H->K3[s], K3.data(), K3.size() * sizeof(double), cudaMemcpyHostToDevice, H->stream)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(H->stream)) != cudaSuccess) {
+        mpfc_set_cuda_error(e, "upload coarse matrix", __FILE__, __LINE__);
+        rc = MPFC_ERR_CUDA;
+      }
+    }
+    if (rc == MPFC_OK) rc = mpfc_fp32_init(H);
+  } while (0);
+  if (rc != MPFC_OK) {
+    mpfc_destroy(H);
+    return rc;
+  }
+  *out = H;
+  return MPFC_OK;
+}
+
+extern "C" void mpfc_destroy(mpfc_t* H) {
+  if (!H) return;
+  for (int s = 0; s < 2; ++s)
+    for (int v = 0; v < 2; ++v)
+      if (H->exec[s][v]) cudaGraphExecDestroy(H->exec[s][v]);
+  mpfc_fp32_destroy(H);
+  if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+  if (H->body_stream) cudaStreamDestroy(H->body_stream);
+  delete H;
+}
+
+extern "C" int mpfc_levels(const mpfc_t* H) { return H ? H->nlev : 0; }
+
+extern "C" int mpfc_level_size(const mpfc_t* H, int level, int* m, int* n, double* hl) {
+  if (!H || level < 0 || level >= H->nlev) return MPFC_ERR_INVALID;
+  if (m) *m = H->lev[level].m;
+  if (n) *n = H->lev[level].n;
+  if (hl) *hl = H->lev[level].h;
+  return MPFC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+static dim3 grid_for(int X, int Y, dim3 b) { return dim3((X + b.x - 1) / b.x, (Y + b.y - 1) / b.y); }
+static const dim3 kBlk2d(32, 8);
+
+int mpfc_reduce_blocks(size_t G) {
+  size_t b = (G + 255) / 256;
+  if (b > (size_t)kMaxPartials) b = kMaxPartials;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <int SCH>
+static void launch_smooth(const Lev& L, const Coef& k, int sweeps, cudaStream_t s) {
+  dim3 g = grid_for(L.m / 2, L.n, kBlk2d);
+  for (int sw = 0; sw < sweeps; ++sw) {
+    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, 0);
+    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, 1);
+  }
+}
+
+static size_t coarse_smem(const Lev& C) {
+  int G = C.m * C.n;
+  return sizeof(double) * ((size_t)G * (G + 1) + 8 * (size_t)G);
+}
+
+template <int SCH>
+static void launch_coarse(mpfc_s* H, const Lev& C, const Coef& k, cudaStream_t s) {
+  k_coarse_solve<SCH><<<1, 256, coarse_smem(C), s>>>(C, k, H->K3[SCH - 1]);
+}
+
+template <int SCH>
+static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
+  const mpfc_params& p = H->p;
+  int L = H->nlev;
+  for (int l = 0; l < L - 1; ++l) {
+    const Lev& F = H->lev[l];
+    const Lev& C = H->lev[l + 1];
+    launch_smooth<SCH>(F, H->coef[SCH - 1][l], p.nu1, s);
+    k_resid_restrict<SCH><<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(F, C, H->coef[SCH - 1][l], 1);
+    k_tau<SCH><<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(C, H->coef[SCH - 1][l + 1]);
+  }
+  launch_coarse<SCH>(H, H->lev[L - 1], H->coef[SCH - 1][L - 1], s);
+  for (int l = L - 2; l >= 0; --l) {
+    const Lev& F = H->lev[l];
+    const Lev& C = H->lev[l + 1];
+    ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n};
+    k_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(A);
+    launch_smooth<SCH>(F, H->coef[SCH - 1][l], p.nu2, s);
+  }
+}
+
+template <int SCH>
+static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
+  const mpfc_params& p = H->p;
+  const Lev& L0 = H->lev[0];
+  k_step_begin<<<1, 32, 0, s>>>(H->ctl);
+  SourceArgs A;
+  A.phik = H->phik;
+  A.phikm1 = H->phikm1;
+  A.psik = H->psik;
+  A.psi_coef = (SCH == 1) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
+  A.half_alpha = 0.5 * (1.0 - p.epsilon);
+  A.guess = (p.guess == MPFC_GUESS_PREV) ? 0 : (p.guess == MPFC_GUESS_EXTRAP ? 1 : 2);
+  dim3 g0 = grid_for(L0.m, L0.n, kBlk2d);
+  k_source_guess<SCH><<<g0, kBlk2d, 0, s>>>(L0, A);
+  if (p.guess == MPFC_GUESS_LEARNED) mpfc_enqueue_learned_guess(H, s);
+  if (SCH == 2)
+    for (int l = 1; l < H->nlev; ++l) {
+      const Lev& C = H->lev[l];
+      k_restrict_plane<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(H->lev[l - 1].pk, C.pk, C.m, C.n);
+    }
+  k_guess_kappa<<<g0, kBlk2d, 0, s>>>(L0, H->coef[SCH - 1][0]);
+  k_guess_mu<SCH><<<g0, kBlk2d, 0, s>>>(L0, H->coef[SCH - 1][0]);
+}
+
+template <int SCH>
+static void enqueue_commit(mpfc_s* H, cudaStream_t s) {
+  size_t G = (size_t)H->p.m * H->p.n;
+  int blocks = (int)((G + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_commit<SCH><<<blocks, 256, 0, s>>>(H->lev[0].phi, H->phik, H->phikm1, H->psik, (int)G, 1.0 / H->p.dt, H->ctl,
+                                       H->info);
+}
+
+template <int SCH>
+static void enqueue_resnorm(mpfc_s* H, int mode, cudaGraphConditionalHandle hnd, int set_cond, cudaStream_t s) {
+  const Lev& L0 = H->lev[0];
+  int blocks = mpfc_reduce_blocks((size_t)L0.m * L0.n);
+  k_resnorm<SCH><<<blocks, 256, 0, s>>>(L0, H->coef[SCH - 1][0], H->ctl, H->partials, mode, hnd, set_cond);
+}
+
+// Body of the FP64 WHILE node: one V-cycle, then the residual test that sets the
+// loop condition.
+static void fp64_body(mpfc_s* H, int scheme, cudaStream_t s) {
+  cudaGraphConditionalHandle hnd = H->cur_handle;
+  if (scheme == 1) {
+    enqueue_vcycle<1>(H, s);
+    enqueue_resnorm<1>(H, 1, hnd, 1, s);
+  } else {
+    enqueue_vcycle<2>(H, s);
+    enqueue_resnorm<2>(H, 1, hnd, 1, s);
+  }
+}
+
+// Builds the step graph of one scheme:
+//   prologue -> resnorm(mode 0, sets cond) -> WHILE(cond){ V-cycle; resnorm(mode 1) } -> commit
+template <int SCH>
+static int build_step_graph(mpfc_s* H) {
+  cudaStream_t cs = H->cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaGraphConditionalHandle hnd;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps));
+  CK(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0));
+  H->cur_handle = hnd;
+  if (H->p.precision == MPFC_FP32_INNER) {
+    int rc = mpfc_fp32_enqueue_step(H, SCH, cs, hnd);
+    if (rc != MPFC_OK) return rc;
+  } else {
+    enqueue_prologue<SCH>(H, cs);
+    enqueue_resnorm<SCH>(H, 0, hnd, 1, cs);
+    int rc = mpfc_capture_while(H, cs, hnd, &fp64_body, SCH);
+    if (rc != MPFC_OK) return rc;
+    enqueue_commit<SCH>(H, cs);
+  }
+  CK(cudaStreamEndCapture(cs, &graph));
+  cudaGraphExec_t exec;
+  CK(cudaGraphInstantiate(&exec, graph, 0));
+  CK(cudaGraphDestroy(graph));
+  H->exec[SCH - 1][0] = exec;
+  return MPFC_OK;
+}
+
+int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd, void (*body_fn)(mpfc_s*, int, cudaStream_t),
+                       int scheme) {
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = hnd;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CK(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(cudaStreamBeginCaptureToGraph(H->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  body_fn(H, scheme, H->body_stream);
+  CK(cudaStreamEndCapture(H->body_stream, &body));
+  return MPFC_OK;
+}
+
+// Shared pieces used by the FP32-inner driver.
+void mpfc_enqueue_prologue(mpfc_s* H, int scheme, cudaStream_t s) {
+  if (scheme == 1) enqueue_prologue<1>(H, s);
+  else enqueue_prologue<2>(H, s);
+}
+void mpfc_enqueue_commit(mpfc_s* H, int scheme, cudaStream_t s) {
+  if (scheme == 1) enqueue_commit<1>(H, s);
+  else enqueue_commit<2>(H, s);
+}
+
+static int ensure_graph(mpfc_s* H, int scheme) {
+  if (H->exec[scheme - 1][0]) return MPFC_OK;
+  return scheme == 1 ? build_step_graph<1>(H) : build_step_graph<2>(H);
+}
+
+// ---------------------------------------------------------------------------
+// State and stepping
+// ---------------------------------------------------------------------------
+extern "C" int mpfc_set_state(mpfc_t* H, const double* phi, const double* phi_prev, const double* psi) {
+  if (!H || !phi) return MPFC_ERR_INVALID;
+  size_t bytes = (size_t)H->p.m * H->p.n * sizeof(double);
+  CK(cudaMemcpyAsync(H->phik, phi, bytes, cudaMemcpyDefault, H->stream));
+  CK(cudaMemcpyAsync(H->phikm1, phi_prev ? phi_prev : phi, bytes, cudaMemcpyDefault, H->stream));
+  if (psi) CK(cudaMemcpyAsync(H->psik, psi, bytes, cudaMemcpyDefault, H->stream));
+  else CK(cudaMemsetAsync(H->psik, 0, bytes, H->stream));
+  k_ctl_reset<<<1, 32, 0, H->stream>>>(H->ctl, 0);
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_get_state(mpfc_t* H, double* phi, double* phi_prev, double* psi) {
+  if (!H) return MPFC_ERR_INVALID;
+  size_t bytes = (size_t)H->p.m * H->p.n * sizeof(double);
+  if (phi) CK(cudaMemcpyAsync(phi, H->phik, bytes, cudaMemcpyDefault, H->stream));
+  if (phi_prev) CK(cudaMemcpyAsync(phi_prev, H->phikm1, bytes, cudaMemcpyDefault, H->stream));
+  if (psi) CK(cudaMemcpyAsync(psi, H->psik, bytes, cudaMemcpyDefault, H->stream));
+  CK(cudaStreamSynchronize(H->stream));
+  return MPFC_OK;
+}
+
+static int run_steps(mpfc_s* H, int scheme, int nsteps, int fixed_cycles, mpfc_step_info* per_step) {
+  if (!H || (scheme != 1 && scheme != 2) || nsteps < 0) return MPFC_ERR_INVALID;
+  if (H->p.guess == MPFC_GUESS_LEARNED && !mpfc_has_guess_model(H)) return MPFC_ERR_INVALID;
+  int rc = ensure_graph(H, scheme);
+  if (rc != MPFC_OK) return rc;
+  std::vector<StepRecord> rec(kInfoCap);
+  int done = 0;
+  int first_err = MPFC_OK;
+  while (done < nsteps && first_err == MPFC_OK) {
+    int chunk = nsteps - done < kInfoCap ? nsteps - done : kInfoCap;
+    k_ctl_reset<<<1, 32, 0, H->stream>>>(H->ctl, fixed_cycles);
+    CK(cudaGetLastError());
+    for (int k = 0; k < chunk; ++k) CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
+    CK(cudaMemcpyAsync(rec.data(), H->info, chunk * sizeof(StepRecord), cudaMemcpyDeviceToHost, H->stream));
+    CK(cudaStreamSynchronize(H->stream));
+    for (int k = 0; k < chunk; ++k) {
+      const StepRecord& r = rec[k];
+      if (per_step) {
+        per_step[done + k].cycles = r.cycles;
+        per_step[done + k].status = r.status;
+        per_step[done + k].res0 = r.res0;
+        per_step[done + k].res_final = r.res_final;
+      }
+      if (r.status != 0 && first_err == MPFC_OK) {
+        first_err = r.status;
+        // later records of this chunk were skipped steps; mark them
+        for (int q = k + 1; q < chunk && per_step; ++q) {
+          per_step[done + q].cycles = 0;
+          per_step[done + q].status = r.status;
+          per_step[done + q].res0 = per_step[done + q].res_final = 0.0;
+        }
+        break;
+      }
+    }
+    done += chunk;
+  }
+  if (first_err != MPFC_OK && per_step)
+    for (int q = done; q < nsteps; ++q) {
+      per_step[q].cycles = 0;
+      per_step[q].status = first_err;
+      per_step[q].res0 = per_step[q].res_final = 0.0;
+    }
+  return first_err;
+}
+
+extern "C" int mpfc_step(mpfc_t* H, int scheme, int nsteps, mpfc_step_info* per_step) {
+  return run_steps(H, scheme, nsteps, 0, per_step);
+}
+
+extern "C" int mpfc_step_cycles(mpfc_t* H, int scheme, int ncycles, mpfc_step_info* info) {
+  if (ncycles < 1) return MPFC_ERR_INVALID;
+  return run_steps(H, scheme, 1, ncycles, info);
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics
+// ---------------------------------------------------------------------------
+static int read_sums(mpfc_s* H, double* out, int count) {
+  double tmp[kMaxSums];
+  CK(cudaMemcpyAsync(tmp, H->ctl->sums, sizeof(double) * kMaxSums, cudaMemcpyDeviceToHost, H->stream));
+  CK(cudaStreamSynchronize(H->stream));
+  for (int i = 0; i < count; ++i) out[i] = tmp[i];
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_mass(mpfc_t* H, double* out) {
+  if (!H || !out) return MPFC_ERR_INVALID;
+  size_t G = (size_t)H->p.m * H->p.n;
+  k_sum1<<<mpfc_reduce_blocks(G), 256, 0, H->stream>>>(H->phik, (int)G, H->ctl, H->partials);
+  CK(cudaGetLastError());
+  double s;
+  int rc = read_sums(H, &s, 1);
+  if (rc) return rc;
+  *out = H->p.h * H->p.h * s;
+  return MPFC_OK;
+}
+
+// Periodic Poisson multigrid: -Delta_h x = f (f mean-zero), V(2,2) red-black
+// cycles until ||r|| <= 1e-13 ||f|| (at most 60).  Result in H->px[0].
+static int poisson_solve(mpfc_s* H, const double* rhs) {
+  int L = H->nlev;
+  size_t G0 = (size_t)H->p.m * H->p.n;
+  cudaStream_t s = H->stream;
+  k_sum1<<<mpfc_reduce_blocks(G0), 256, 0, s>>>(rhs, (int)G0, H->ctl, H->partials);
+  k_sub_mean<<<mpfc_reduce_blocks(G0), 256, 0, s>>>(rhs, H->pf[0], (int)G0, H->ctl);
+  CK(cudaMemsetAsync(H->px[0], 0, G0 * sizeof(double), s));
+  for (int cyc = 0; cyc < 60; ++cyc) {
+    for (int l = 0; l < L - 1; ++l) {
+      const Lev& F = H->lev[l];
+      dim3 g = grid_for(F.m / 2, F.n, kBlk2d);
+      for (int sw = 0; sw < 2; ++sw)
+        for (int c = 0; c < 2; ++c) k_pois_smooth<<<g, kBlk2d, 0, s>>>(H->px[l], H->pf[l], F.m, F.n, F.h * F.h, c);
+      const Lev& C = H->lev[l + 1];
+      k_pois_restrict<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(H->px[l], H->pf[l], H->pf[l + 1], H->px[l + 1],
+                                                                     C.m, C.n, 1.0 / (F.h * F.h));
+    }
+    const Lev& Cc = H->lev[L - 1];
+    k_pois_coarse<<<1, 128, sizeof(double) * (Cc.m * Cc.n + 1), s>>>(H->px[L - 1], H->pf[L - 1], Cc.m, Cc.n,
+                                                                      Cc.h * Cc.h, 200);
+    for (int l = L - 2; l >= 0; --l) {
+      const Lev& F = H->lev[l];
+      const Lev& C = H->lev[l + 1];
+      k_pois_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(H->px[l + 1], H->px[l], C.m, C.n);
+      dim3 g = grid_for(F.m / 2, F.n, kBlk2d);
+      for (int sw = 0; sw < 2; ++sw)
+        for (int c = 0; c < 2; ++c) k_pois_smooth<<<g, kBlk2d, 0, s>>>(H->px[l], H->pf[l], F.m, F.n, F.h * F.h, c);
+    }
+    const Lev& F0 = H->lev[0];
+    k_pois_resnorm<<<mpfc_reduce_blocks(G0), 256, 0, s>>>(H->px[0], H->pf[0], F0.m, F0.n, 1.0 / (F0.h * F0.h),
+                                                          H->ctl, H->partials);
+    CK(cudaGetLastError());
+    double v[2];
+    int rc = read_sums(H, v, 2);
+    if (rc) return rc;
+    if (!(v[0] == v[0])) return MPFC_ERR_DIVERGED;
+    if (v[0] <= 1e-26 * v[1] || v[1] == 0.0) break;
+  }
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_energy(mpfc_t* H, mpfc_energy_t* out) {
+  if (!H || !out) return MPFC_ERR_INVALID;
+  int rc = poisson_solve(H, H->psik);
+  if (rc) return rc;
+  size_t G = (size_t)H->p.m * H->p.n;
+  k_energy_sums<<<mpfc_reduce_blocks(G), 256, 0, H->stream>>>(H->phik, H->phikm1, H->psik, H->px[0], H->p.m, H->p.n,
+                                                              H->ctl, H->partials);
+  CK(cudaGetLastError());
+  double v[6];
+  rc = read_sums(H, v, 6);
+  if (rc) return rc;
+  double h = H->p.h, h2 = h * h, alpha = 1.0 - H->p.epsilon;
+  double F = 0.25 * h2 * v[0] + 0.5 * alpha * h2 * v[1] - v[2] + 0.5 * h2 * v[3] / (h2 * h2);
+  double m1 = h2 * v[4];
+  out->F = F;
+  out->pseudoF = F + m1 / (2.0 * H->p.M);
+  out->tildeF = out->pseudoF + 0.5 * v[5];
+  return MPFC_OK;
+}
+
+extern "C" const char* mpfc_strerror(int status) {
+  switch (status) {
+    case MPFC_OK: return "ok";
+    case MPFC_ERR_INVALID: return "invalid argument or parameters";
+    case MPFC_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+    case MPFC_ERR_CUDA: return g_last_cuda_error[0] ? g_last_cuda_error : "CUDA error";
+    case MPFC_ERR_NOT_CONVERGED: return "V-cycle limit reached before the tolerance";
+    case MPFC_ERR_DIVERGED: return "residual became non-finite or grew beyond 1e10 times its start";
+    default: return "unknown status";
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Component entry points
+// ---------------------------------------------------------------------------
+static bool level_ok(const mpfc_s* H, int level) { return H && level >= 0 && level < H->nlev; }
+
+extern "C" int mpfc_op_source(mpfc_t* H, int scheme, const double* phik, const double* phikm1, const double* psik,
+                              double* S1, double* S2, double* S3) {
+  if (!H || (scheme != 1 && scheme != 2) || !phik || !phikm1 || !psik || !S1 || !S2 || !S3) return MPFC_ERR_INVALID;
+  const mpfc_params& p = H->p;
+  Lev L = H->lev[0];
+  L.S1 = S1;
+  L.S2 = S2;
+  L.S3 = S3;
+  L.phi = nullptr;
+  SourceArgs A{phik, phikm1, psik, scheme == 1 ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt),
+               0.5 * (1.0 - p.epsilon), 2};
+  dim3 g = grid_for(L.m, L.n, kBlk2d);
+  if (scheme == 1) k_source_guess<1><<<g, kBlk2d, 0, H->stream>>>(L, A);
+  else k_source_guess<2><<<g, kBlk2d, 0, H->stream>>>(L, A);
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}
+
+static Lev user_level(const mpfc_s* H, int level, double* phi, double* mu, double* ka, const double* S1,
+                      const double* S2, const double* S3, const double* pk) {
+  Lev L = H->lev[level];
+  L.phi = phi;
+  L.mu = mu;
+  L.ka = ka;
+  L.S1 = const_cast<double*>(S1);
+  L.S2 = const_cast<double*>(S2);
+  L.S3 = const_cast<double*>(S3);
+  L.pk = const_cast<double*>(pk);
+  L.b1 = L.b2 = L.b3 = nullptr;
+  return L;
+}
+
+extern "C" int mpfc_op_smooth(mpfc_t* H, int scheme, int level, double* phi, double* mu, double* kappa,
+                              const double* S1, const double* S2, const double* S3, const double* phik, int sweeps) {
+  if (!level_ok(H, level) || (scheme != 1 && scheme != 2) || sweeps < 0 || (scheme == 2 && !phik))
+    return MPFC_ERR_INVALID;
+  Lev L = user_level(H, level, phi, mu, kappa, S1, S2, S3, phik);
+  if (scheme == 1) launch_smooth<1>(L, H->coef[0][level], sweeps, H->stream);
+  else launch_smooth<2>(L, H->coef[1][level], sweeps, H->stream);
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_op_residual(mpfc_t* H, int scheme, int level, const double* phi, const double* mu,
+                                const double* kappa, const double* S1, const double* S2, const double* S3,
+                                const double* phik, double* r1, double* r2, double* r3) {
+  if (!level_ok(H, level) || (scheme != 1 && scheme != 2) || (scheme == 2 && !phik)) return MPFC_ERR_INVALID;
+  Lev L = user_level(H, level, const_cast<double*>(phi), const_cast<double*>(mu), const_cast<double*>(kappa), S1, S2,
+                     S3, phik);
+  dim3 g = grid_for(L.m, L.n, kBlk2d);
+  if (scheme == 1) k_residual<1><<<g, kBlk2d, 0, H->stream>>>(L, H->coef[0][level], r1, r2, r3);
+  else k_residual<2><<<g, kBlk2d, 0, H->stream>>>(L, H->coef[1][level], r1, r2, r3);
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_op_restrict(mpfc_t* H, int scheme, int level, const double* phi, const double* mu,
+                                const double* kappa, const double* S1, const double* S2, const double* S3,
+                                const double* phik, const double* phik_c, double* phi_c, double* mu_c,
+                                double* kappa_c, double* S1_c, double* S2_c, double* S3_c) {
+  if (!level_ok(H, level) || level + 1 >= H->nlev || (scheme != 1 && scheme != 2) ||
+      (scheme == 2 && (!phik || !phik_c)))
+    return MPFC_ERR_INVALID;
+  Lev F = user_level(H, level, const_cast<double*>(phi), const_cast<double*>(mu), const_cast<double*>(kappa), S1, S2,
+                     S3, phik);
+  Lev C = user_level(H, level + 1, phi_c, mu_c, kappa_c, S1_c, S2_c, S3_c, phik_c);
+  dim3 g = grid_for(C.m, C.n, kBlk2d);
+  if (scheme == 1) {
+    k_resid_restrict<1><<<g, kBlk2d, 0, H->stream>>>(F, C, H->coef[0][level], 0);
+    k_tau<1><<<g, kBlk2d, 0, H->stream>>>(C, H->coef[0][level + 1]);
+  } else {
+    k_resid_restrict<2><<<g, kBlk2d, 0, H->stream>>>(F, C, H->coef[1][level], 0);
+    k_tau<2><<<g, kBlk2d, 0, H->stream>>>(C, H->coef[1][level + 1]);
+  }
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_op_prolong(mpfc_t* H, int level, const double* phi_c_new, const double* mu_c_new,
+                               const double* kappa_c_new, const double* phi_c_old, const double* mu_c_old,
+                               const double* kappa_c_old, double* phi, double* mu, double* kappa) {
+  if (!level_ok(H, level) || level + 1 >= H->nlev) return MPFC_ERR_INVALID;
+  const Lev& C = H->lev[level + 1];
+  ProlongArgs A{phi_c_new, mu_c_new, kappa_c_new, phi_c_old, mu_c_old, kappa_c_old, phi, mu, kappa, C.m, C.n};
+  k_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, H->stream>>>(A);
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_op_coarse_solve(mpfc_t* H, int scheme, double* phi, double* mu, double* kappa, const double* S1,
+                                    const double* S2, const double* S3, const double* phik) {
+  if (!H || (scheme != 1 && scheme != 2) || (scheme == 2 && !phik)) return MPFC_ERR_INVALID;
+  int l = H->nlev - 1;
+  Lev C = user_level(H, l, phi, mu, kappa, S1, S2, S3, phik);
+  if (scheme == 1) launch_coarse<1>(H, C, H->coef[0][l], H->stream);
+  else launch_coarse<2>(H, C, H->coef[1][l], H->stream);
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}

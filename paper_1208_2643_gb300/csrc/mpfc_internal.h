@@ -1,0 +1,65 @@
+// Internal handle layout of libmpfc, shared by the translation units of the CUDA path.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/mpfc.h"
+#include "mpfc_common.cuh"
+
+// FP32 copy of one level for the inner V-cycles of the mixed-precision form.
+struct Lev32 {
+  int m, n;
+  float h;
+  float *ephi, *emu, *eka;   // correction e = (e_phi, e_mu, e_kappa)
+  float *r1, *r2, *r3;       // source of the correction equation (restricted defect)
+  float *b1, *b2, *b3;       // R e_f kept for the FAS-style correction (levels >= 1)
+  float* q;                  // gam + g'(phi) of the FP64 iterate, restricted
+};
+
+struct mpfc_s {
+  mpfc_params p;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaStream_t body_stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int nlev = 0;
+  mpfc::Lev lev[mpfc::kMaxLevels];
+  mpfc::Coef coef[2][mpfc::kMaxLevels];
+  double* phik = nullptr;
+  double* phikm1 = nullptr;
+  double* psik = nullptr;
+  mpfc::Ctl* ctl = nullptr;
+  double* partials = nullptr;
+  mpfc::StepRecord* info = nullptr;
+  double* K3[2] = {nullptr, nullptr};
+  double* px[mpfc::kMaxLevels];
+  double* pf[mpfc::kMaxLevels];
+  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphConditionalHandle cur_handle = 0;   // handle of the graph being captured
+  // mixed precision
+  Lev32 lev32[mpfc::kMaxLevels];
+  float* K3f[2] = {nullptr, nullptr};
+  int outer_max = 0;
+  // learned initial guess
+  void* guess_model = nullptr;
+};
+
+void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+int mpfc_num_levels(int m, int n, int coarsest);
+mpfc::Coef mpfc_coef(const mpfc_params* p, int scheme, double h);
+int mpfc_reduce_blocks(size_t G);
+int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd,
+                       void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme);
+void mpfc_enqueue_prologue(mpfc_s* H, int scheme, cudaStream_t s);
+void mpfc_enqueue_commit(mpfc_s* H, int scheme, cudaStream_t s);
+
+// mixed-precision form (fp32_inner.cu)
+size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base, int nlev);
+int mpfc_fp32_init(mpfc_s* H);
+void mpfc_fp32_destroy(mpfc_s* H);
+int mpfc_fp32_enqueue_step(mpfc_s* H, int scheme, cudaStream_t cs, cudaGraphConditionalHandle hnd);
+
+// learned initial guess (guess_cnn.cu)
+bool mpfc_has_guess_model(const mpfc_s* H);
+void mpfc_enqueue_learned_guess(mpfc_s* H, cudaStream_t s);

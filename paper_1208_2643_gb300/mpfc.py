@@ -1,0 +1,283 @@
+"""Python binding of libmpfc (argument marshalling only; every step runs in the CUDA library).
+
+The names follow include/mpfc.h.  PyTorch supplies device memory (the workspace and
+any field tensors) and the CUDA stream; the library never falls back to a CPU path:
+if libmpfc.so cannot be loaded, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+MPFC_OK = 0
+MPFC_ERR_INVALID = -1
+MPFC_ERR_WORKSPACE = -2
+MPFC_ERR_CUDA = -3
+MPFC_ERR_NOT_CONVERGED = -4
+MPFC_ERR_DIVERGED = -5
+
+MPFC_FP64 = 0
+MPFC_FP32_INNER = 1
+
+MPFC_GUESS_PREV = 0
+MPFC_GUESS_EXTRAP = 1
+MPFC_GUESS_LEARNED = 2
+
+
+class mpfc_params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("h", ctypes.c_double), ("M", ctypes.c_double),
+                ("epsilon", ctypes.c_double), ("beta", ctypes.c_double), ("dt", ctypes.c_double),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarsest", ctypes.c_int),
+                ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
+                ("precision", ctypes.c_int), ("guess", ctypes.c_int)]
+
+
+class mpfc_step_info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res_final", ctypes.c_double)]
+
+
+class mpfc_energy_t(ctypes.Structure):
+    _fields_ = [("F", ctypes.c_double), ("pseudoF", ctypes.c_double), ("tildeF", ctypes.c_double)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+class MPFCError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libmpfc.so (building it first if needed); raises if that fails."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmpfc.so not found at {path}; run paper_1208_2643_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.mpfc_default_params.argtypes = [P(mpfc_params)]
+    lib.mpfc_default_params.restype = None
+    lib.mpfc_workspace_bytes.argtypes = [P(mpfc_params)]
+    lib.mpfc_workspace_bytes.restype = ctypes.c_size_t
+    lib.mpfc_create.argtypes = [P(mpfc_params), _VP, ctypes.c_size_t, _VP, P(_VP)]
+    lib.mpfc_destroy.argtypes = [_VP]
+    lib.mpfc_destroy.restype = None
+    lib.mpfc_set_state.argtypes = [_VP, _VP, _VP, _VP]
+    lib.mpfc_get_state.argtypes = [_VP, _VP, _VP, _VP]
+    lib.mpfc_step.argtypes = [_VP, ctypes.c_int, ctypes.c_int, P(mpfc_step_info)]
+    lib.mpfc_step_cycles.argtypes = [_VP, ctypes.c_int, ctypes.c_int, P(mpfc_step_info)]
+    lib.mpfc_mass.argtypes = [_VP, P(ctypes.c_double)]
+    lib.mpfc_energy.argtypes = [_VP, P(mpfc_energy_t)]
+    lib.mpfc_strerror.argtypes = [ctypes.c_int]
+    lib.mpfc_strerror.restype = ctypes.c_char_p
+    lib.mpfc_levels.argtypes = [_VP]
+    lib.mpfc_level_size.argtypes = [_VP, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_double)]
+    lib.mpfc_op_source.argtypes = [_VP, ctypes.c_int] + [_VP] * 6
+    lib.mpfc_op_smooth.argtypes = [_VP, ctypes.c_int, ctypes.c_int] + [_VP] * 7 + [ctypes.c_int]
+    lib.mpfc_op_residual.argtypes = [_VP, ctypes.c_int, ctypes.c_int] + [_VP] * 10
+    lib.mpfc_op_restrict.argtypes = [_VP, ctypes.c_int, ctypes.c_int] + [_VP] * 14
+    lib.mpfc_op_prolong.argtypes = [_VP, ctypes.c_int] + [_VP] * 9
+    lib.mpfc_op_coarse_solve.argtypes = [_VP, ctypes.c_int] + [_VP] * 7
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load(build_if_missing=False).mpfc_strerror(status).decode()
+    except Exception:
+        return f"status {status}"
+
+
+def _check(rc, where):
+    if rc != MPFC_OK:
+        raise MPFCError(rc, where)
+
+
+def default_params(**kw) -> mpfc_params:
+    p = mpfc_params()
+    load().mpfc_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def workspace_bytes(p: mpfc_params) -> int:
+    return int(load().mpfc_workspace_bytes(ctypes.byref(p)))
+
+
+def _ptr(t):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.dtype == np.float64 and t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+class Solver:
+    """One MPFC instance on the current CUDA device: workspace, state and stepping."""
+
+    def __init__(self, params: mpfc_params | None = None, stream=None, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmpfc needs a CUDA device")
+        self._torch = torch
+        self.lib = load()
+        self.p = params if params is not None else default_params(**kw)
+        nbytes = workspace_bytes(self.p)
+        if nbytes == 0:
+            raise MPFCError(MPFC_ERR_INVALID, "mpfc_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        h = _VP()
+        _check(self.lib.mpfc_create(ctypes.byref(self.p), aligned, nbytes, self.stream.cuda_stream, ctypes.byref(h)),
+               "mpfc_create")
+        self.h = h
+        self.shape = (self.p.n, self.p.m)
+        self.levels = self.lib.mpfc_levels(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpfc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_size(self, level):
+        m, n, hl = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(self.lib.mpfc_level_size(self.h, level, ctypes.byref(m), ctypes.byref(n), ctypes.byref(hl)),
+               "mpfc_level_size")
+        return m.value, n.value, hl.value
+
+    def _dev(self, a):
+        torch = self._torch
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to("cuda")
+        return a.to(device="cuda", dtype=torch.float64).contiguous()
+
+    def set_state(self, phi, phi_prev=None, psi=None):
+        """Copies (phi^k, phi^{k-1}, psi^k) in; numpy arrays (host) or tensors (device)."""
+        args = [phi, phi_prev, psi]
+        keep = []
+        ptrs = []
+        for a in args:
+            if a is None:
+                ptrs.append(None)
+            elif isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(a)
+                ptrs.append(a.ctypes.data)
+            else:
+                a = a.contiguous()
+                keep.append(a)
+                ptrs.append(a.data_ptr())
+        _check(self.lib.mpfc_set_state(self.h, *ptrs), "mpfc_set_state")
+        self.stream.synchronize()
+
+    def get_state(self, device=False):
+        """Returns (phi^k, phi^{k-1}, psi^k) as numpy arrays (or device tensors)."""
+        torch = self._torch
+        if device:
+            outs = [torch.empty(self.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+            _check(self.lib.mpfc_get_state(self.h, *[o.data_ptr() for o in outs]), "mpfc_get_state")
+            return outs
+        outs = [np.empty(self.shape) for _ in range(3)]
+        _check(self.lib.mpfc_get_state(self.h, *[o.ctypes.data for o in outs]), "mpfc_get_state")
+        return outs
+
+    def step(self, scheme: int, nsteps: int = 1, raise_on_error=True):
+        """Advances nsteps steps; returns a list of dicts (cycles, status, res0, res)."""
+        infos = (mpfc_step_info * max(nsteps, 1))()
+        rc = self.lib.mpfc_step(self.h, scheme, nsteps, infos)
+        out = [dict(cycles=i.cycles, status=i.status, res0=i.res0, res=i.res_final) for i in infos[:nsteps]]
+        if rc != MPFC_OK and raise_on_error:
+            raise MPFCError(rc, "mpfc_step")
+        return out if raise_on_error else (rc, out)
+
+    def step_cycles(self, scheme: int, ncycles: int):
+        info = mpfc_step_info()
+        _check(self.lib.mpfc_step_cycles(self.h, scheme, ncycles, ctypes.byref(info)), "mpfc_step_cycles")
+        return dict(cycles=info.cycles, status=info.status, res0=info.res0, res=info.res_final)
+
+    def mass(self) -> float:
+        v = ctypes.c_double()
+        _check(self.lib.mpfc_mass(self.h, ctypes.byref(v)), "mpfc_mass")
+        return v.value
+
+    def energy(self):
+        e = mpfc_energy_t()
+        _check(self.lib.mpfc_energy(self.h, ctypes.byref(e)), "mpfc_energy")
+        return dict(F=e.F, pseudoF=e.pseudoF, tildeF=e.tildeF)
+
+    # component entry points (device tensors in and out)
+    def op_source(self, scheme, phik, phikm1, psik):
+        torch = self._torch
+        S = [torch.empty(self.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+        _check(self.lib.mpfc_op_source(self.h, scheme, _ptr(phik), _ptr(phikm1), _ptr(psik), *[_ptr(s) for s in S]),
+               "mpfc_op_source")
+        return S
+
+    def op_smooth(self, scheme, level, u, S, phik=None, sweeps=1):
+        u = [x.clone() for x in u]
+        _check(self.lib.mpfc_op_smooth(self.h, scheme, level, *[_ptr(x) for x in u], *[_ptr(s) for s in S],
+                                       _ptr(phik), sweeps), "mpfc_op_smooth")
+        return u
+
+    def op_residual(self, scheme, level, u, S, phik=None):
+        torch = self._torch
+        r = [torch.empty_like(u[0]) for _ in range(3)]
+        _check(self.lib.mpfc_op_residual(self.h, scheme, level, *[_ptr(x) for x in u], *[_ptr(s) for s in S],
+                                         _ptr(phik), *[_ptr(x) for x in r]), "mpfc_op_residual")
+        return r
+
+    def op_restrict(self, scheme, level, u, S, phik=None, phik_c=None):
+        torch = self._torch
+        m, n, _ = self.level_size(level + 1)
+        uc = [torch.empty((n, m), dtype=torch.float64, device="cuda") for _ in range(3)]
+        Sc = [torch.empty((n, m), dtype=torch.float64, device="cuda") for _ in range(3)]
+        _check(self.lib.mpfc_op_restrict(self.h, scheme, level, *[_ptr(x) for x in u], *[_ptr(s) for s in S],
+                                         _ptr(phik), _ptr(phik_c), *[_ptr(x) for x in uc], *[_ptr(x) for x in Sc]),
+               "mpfc_op_restrict")
+        return uc, Sc
+
+    def op_prolong(self, level, uc_new, uc_old, u):
+        u = [x.clone() for x in u]
+        _check(self.lib.mpfc_op_prolong(self.h, level, *[_ptr(x) for x in uc_new], *[_ptr(x) for x in uc_old],
+                                        *[_ptr(x) for x in u]), "mpfc_op_prolong")
+        return u
+
+    def op_coarse_solve(self, scheme, u, S, phik=None):
+        u = [x.clone() for x in u]
+        _check(self.lib.mpfc_op_coarse_solve(self.h, scheme, *[_ptr(x) for x in u], *[_ptr(s) for s in S],
+                                             _ptr(phik)), "mpfc_op_coarse_solve")
+        return u

@@ -1,0 +1,321 @@
+"""Parity of the FP64 CUDA path (through the C ABI) with the CPU oracle.
+
+Kernel-level checks run every building block on the same seeded inputs as the
+oracle routine of the same name, at sizes that are not multiples of the 32 x 8
+thread tiles.  Step-level checks run whole time steps in lockstep (the GPU takes
+the oracle's V-cycle count) and require max-norm relative error <= 1e-10 per
+step, the bar the solver is built to.
+"""
+import numpy as np
+import pytest
+
+from paper_1208_2643_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_2643_gb300 import mpfc
+    mpfc.load()
+    return mpfc
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def make(mp, m, n, h, s, **kw):
+    return mp.Solver(mp.default_params(m=m, n=n, h=h, dt=s, **kw))
+
+
+def rand_fields(m, n, seed):
+    phik = inputs.noise_field(m, n, 0.07, 0.05, seed)
+    phikm1 = inputs.noise_field(m, n, 0.07, 0.05, seed + 1)
+    psik = inputs.noise_field(m, n, 0.0, 0.02, seed + 2)
+    psik -= psik.mean()
+    return phik, phikm1, psik
+
+
+SIZES = [(96, 160), (64, 64)]
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("m,n", SIZES)
+def test_source(mp, oracle_mod, scheme, m, n):
+    h, s = 0.7, 0.05
+    g = make(mp, m, n, h, s)
+    p = oracle_mod.Params(m=m, n=n, h=h, s=s)
+    phik, phikm1, psik = rand_fields(m, n, 3)
+    Sg = g.op_source(scheme, dev(phik), dev(phikm1), dev(psik))
+    So = oracle_mod.source(scheme, p, phik, phikm1, psik)
+    for a, b in zip(Sg, So):
+        if np.abs(b).max() == 0:
+            assert np.abs(host(a)).max() == 0
+        else:
+            assert relerr(host(a), b) < 1e-13
+
+
+def _level_inputs(oracle_mod, mp, scheme, m, n, h, s, level, seed):
+    g = make(mp, m, n, h, s)
+    ml, nl, hl = g.level_size(level)
+    p = oracle_mod.Params(m=m, n=n, h=h, s=s)
+    consts = oracle_mod.scheme_consts(p, scheme)
+    rng = np.random.default_rng(seed)
+    u = [0.07 + 0.05 * rng.uniform(-1, 1, (nl, ml)), rng.normal(size=(nl, ml)), rng.normal(size=(nl, ml))]
+    S = [rng.normal(scale=0.05, size=(nl, ml)), rng.normal(size=(nl, ml)), rng.normal(size=(nl, ml))]
+    phik = 0.07 + 0.05 * rng.uniform(-1, 1, (nl, ml)) if scheme == 2 else None
+    return g, consts, hl, u, S, phik
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("level", [0, 1, 3])
+def test_residual(mp, oracle_mod, scheme, level):
+    g, consts, hl, u, S, phik = _level_inputs(oracle_mod, mp, scheme, 96, 160, 0.5, 0.3, level, 5)
+    rg = g.op_residual(scheme, level, [dev(x) for x in u], [dev(x) for x in S], dev(phik) if phik is not None else None)
+    ro = oracle_mod.residual(scheme, consts, hl, u, S, phik)
+    for a, b in zip(rg, ro):
+        assert relerr(host(a), b) < 1e-13
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("omega", [1.0, 0.8])
+@pytest.mark.parametrize("level,sweeps", [(0, 1), (0, 3), (2, 2)])
+def test_smooth(mp, oracle_mod, scheme, omega, level, sweeps):
+    m, n, h, s = 96, 160, 0.5, 0.3
+    g = mp.Solver(mp.default_params(m=m, n=n, h=h, dt=s, omega=omega))
+    ml, nl, hl = g.level_size(level)
+    p = oracle_mod.Params(m=m, n=n, h=h, s=s)
+    consts = oracle_mod.scheme_consts(p, scheme)
+    phik = inputs.noise_field(ml, nl, 0.07, 0.05, 8)
+    S = oracle_mod.source(scheme, oracle_mod.Params(m=ml, n=nl, h=hl, s=s), phik, phik,
+                          inputs.noise_field(ml, nl, 0, 0.01, 9))
+    rng = np.random.default_rng(10)
+    u = [phik + 0.01 * rng.uniform(-1, 1, (nl, ml)), rng.normal(size=(nl, ml)), rng.normal(size=(nl, ml))]
+    pk = phik if scheme == 2 else None
+    ug = g.op_smooth(scheme, level, [dev(x) for x in u], [dev(x) for x in S], dev(pk) if pk is not None else None,
+                     sweeps)
+    uo = oracle_mod.smooth(scheme, consts, hl, u, S, pk, sweeps=sweeps, omega=omega)
+    for a, b in zip(ug, uo):
+        assert relerr(host(a), b) < 1e-11
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("level", [0, 2])
+def test_restrict_tau(mp, oracle_mod, scheme, level):
+    m, n, h, s = 96, 160, 0.5, 0.3
+    g, consts, hl, u, S, phik = _level_inputs(oracle_mod, mp, scheme, m, n, h, s, level, 12)
+    p = oracle_mod.Params(m=m, n=n, h=h, s=s)
+    phik_c = oracle_mod.restrict(phik) if scheme == 2 else None
+    uc, Sc = g.op_restrict(scheme, level, [dev(x) for x in u], [dev(x) for x in S],
+                           dev(phik) if phik is not None else None, dev(phik_c) if phik_c is not None else None)
+    r = oracle_mod.residual(scheme, consts, hl, u, S, phik)
+    uco = [oracle_mod.restrict(x) for x in u]
+    No = oracle_mod.apply_N(scheme, consts, 2 * hl, *uco, phik_c)
+    Sco = [a + oracle_mod.restrict(b) for a, b in zip(No, r)]
+    for a, b in zip(uc, uco):
+        assert relerr(host(a), b) < 1e-14
+    for a, b in zip(Sc, Sco):
+        assert relerr(host(a), b) < 1e-12
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_prolong(mp, oracle_mod, level):
+    g = make(mp, 96, 160, 0.5, 0.3)
+    mc, nc, _ = g.level_size(level + 1)
+    mf, nf, _ = g.level_size(level)
+    rng = np.random.default_rng(13)
+    new = [rng.normal(size=(nc, mc)) for _ in range(3)]
+    old = [rng.normal(size=(nc, mc)) for _ in range(3)]
+    fine = [rng.normal(size=(nf, mf)) for _ in range(3)]
+    out = g.op_prolong(level, [dev(x) for x in new], [dev(x) for x in old], [dev(x) for x in fine])
+    for a, c_new, c_old, f in zip(out, new, old, fine):
+        assert relerr(host(a), oracle_mod.prolong_add(c_new - c_old, f)) < 1e-14
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("m,n,s", [(64, 64, 0.3), (96, 160, 10.0), (128, 32, 0.01)])
+def test_coarse_solve(mp, oracle_mod, scheme, m, n, s):
+    g = make(mp, m, n, 0.5, s)
+    L = g.levels - 1
+    mc, nc, hc = g.level_size(L)
+    p = oracle_mod.Params(m=m, n=n, h=0.5, s=s)
+    consts = oracle_mod.scheme_consts(p, scheme)
+    rng = np.random.default_rng(14)
+    S = [rng.normal(scale=0.05, size=(nc, mc)) + 0.07 * (i == 0) for i in range(3)]
+    phik = 0.07 + 0.05 * rng.uniform(-1, 1, (nc, mc)) if scheme == 2 else None
+    u0 = [np.full((nc, mc), 0.07), np.zeros((nc, mc)), np.zeros((nc, mc))]
+    ug = g.op_coarse_solve(scheme, [dev(x) for x in u0], [dev(x) for x in S], dev(phik) if phik is not None else None)
+    uo, _ = oracle_mod.coarse_newton(scheme, consts, hc, u0, S, phik)
+    for a, b in zip(ug, uo):
+        assert relerr(host(a), b) < 1e-11
+    # and it really solves N(u) = S
+    r = oracle_mod.residual(scheme, consts, hc, [host(x) for x in ug], S, phik)
+    assert max(np.abs(x).max() for x in r) < 1e-11 * max(1.0, max(np.abs(x).max() for x in S))
+
+
+def _lockstep(mp, oracle_mod, scheme, m, n, h, s, steps, phi0, omega=0.8, guess=1, tol=1e-10):
+    g = mp.Solver(mp.default_params(m=m, n=n, h=h, dt=s, omega=omega, guess=guess, tol=tol))
+    g.set_state(phi0)
+    o = oracle_mod.Solver(oracle_mod.Params(m=m, n=n, h=h, s=s, omega=omega))
+    o.set_state(phi0)
+    worst = 0.0
+    for k in range(steps):
+        ro = o.step(scheme, tol=tol, guess=guess)
+        assert ro["status"] == 0
+        rg = g.step_cycles(scheme, ro["cycles"])
+        assert rg["status"] == 0
+        pg, _, psig = g.get_state()
+        po, _, psio = o.get_state()
+        e = relerr(pg, po)
+        worst = max(worst, e)
+        assert e <= 1e-10, (k, e)
+        assert np.abs(psig - psio).max() <= 1e-10 * max(np.abs(psio).max(), np.abs(po).max() / s)
+    return g, o, worst
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_steps_lockstep_64(mp, oracle_mod, scheme):
+    """The 64^2 first-order workload (h = 0.5, eps = 0.025, beta = 0.9, s = 0.01, 20 steps,
+    phi0 = 0.07 + 0.05 U) for both schemes, lockstep with the oracle."""
+    phi0 = inputs.noise_field(64, 64, 0.07, 0.05, 1)
+    _lockstep(mp, oracle_mod, scheme, 64, 64, 0.5, 0.01, 20, phi0)
+
+
+def test_steps_lockstep_ragged_scheme2(mp, oracle_mod):
+    phi0 = inputs.crystallite_field(96, 160, np.pi / 4, -0.285, 0.25, count=2, radius_cells=12, seed=2)
+    _lockstep(mp, oracle_mod, 2, 96, 160, np.pi / 4, 0.05, 6, phi0)
+
+
+def test_steps_lockstep_undamped(mp, oracle_mod):
+    phi0 = inputs.noise_field(64, 64, 0.07, 0.05, 1)
+    _lockstep(mp, oracle_mod, 1, 64, 64, 0.5, 0.01, 5, phi0, omega=1.0, guess=0)
+
+
+def test_own_cycle_count_matches_oracle(mp, oracle_mod):
+    """Without lockstep the GPU's device-side tolerance test picks the oracle's cycle counts."""
+    m, h, s = 64, 0.5, 0.01
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    g = make(mp, m, m, h, s)
+    g.set_state(phi0)
+    o = oracle_mod.Solver(oracle_mod.Params(m=m, n=m, h=h, s=s))
+    o.set_state(phi0)
+    infos = g.step(1, 10)
+    oc = [o.step(1, tol=1e-10, guess=1)["cycles"] for _ in range(10)]
+    assert [i["cycles"] for i in infos] == oc
+    assert relerr(g.get_state()[0], o.get_state()[0]) < 1e-10
+
+
+def test_headline_size_one_step(mp, oracle_mod):
+    """One lockstep step at the 1024^2 headline size (all cells compared)."""
+    m, h, s = 1024, 0.5, 0.01
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    _lockstep(mp, oracle_mod, 1, m, m, h, s, 1, phi0)
+
+
+def test_mass_and_energy(mp, oracle_mod):
+    from oracle import energy
+    m, h, s = 96, 0.5, 0.05
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    g = make(mp, m, m, h, s)
+    g.set_state(phi0)
+    g.step(2, 3)
+    phi, phip, psi = g.get_state()
+    assert abs(g.mass() - energy.mass(phi, h)) < 1e-12 * abs(energy.mass(phi, h))
+    e = g.energy()
+    assert abs(e["F"] - energy.F(phi, h, 0.025)) < 1e-11 * abs(energy.F(phi, h, 0.025))
+    ref_p = energy.pseudo_F(phi, psi, h, 0.025, 1.0)
+    ref_t = energy.tilde_F(phi, phip, psi, h, 0.025, 1.0)
+    assert abs(e["pseudoF"] - ref_p) < 1e-10 * abs(ref_p)
+    assert abs(e["tildeF"] - ref_t) < 1e-10 * abs(ref_t)
+
+
+def test_mass_conserved_over_many_steps(mp):
+    m, h, s = 128, 0.5, 0.01
+    g = make(mp, m, m, h, s)
+    g.set_state(inputs.noise_field(m, m, 0.07, 0.05, 1))
+    m0 = g.mass()
+    g.step(1, 50)
+    assert abs(g.mass() - m0) < 1e-8 * abs(m0)
+
+
+def test_not_converged_keeps_state(mp):
+    m = 64
+    g = mp.Solver(mp.default_params(m=m, n=m, max_cycles=1, tol=1e-14))
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    g.set_state(phi0)
+    rc, infos = g.step(1, 3, raise_on_error=False)
+    assert rc == mp.MPFC_ERR_NOT_CONVERGED
+    assert infos[0]["status"] == mp.MPFC_ERR_NOT_CONVERGED and infos[0]["cycles"] == 1
+    assert np.array_equal(g.get_state()[0], phi0)
+
+
+def test_diverged_on_nan(mp):
+    m = 32
+    g = make(mp, m, m, 0.5, 0.01)
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    phi0[3, 4] = np.nan
+    g.set_state(phi0)
+    rc, infos = g.step(1, 2, raise_on_error=False)
+    assert rc == mp.MPFC_ERR_DIVERGED
+    # a good state afterwards steps normally again
+    g.set_state(inputs.noise_field(m, m, 0.07, 0.05, 1))
+    assert g.step(1, 1)[0]["status"] == 0
+
+
+def test_invalid_arguments(mp):
+    import ctypes
+    lib = mp.load()
+    p = mp.default_params(m=62, n=64)   # 62 -> 31 is odd: hierarchy stops at a coarse grid too big for the dense solve
+    assert mp.workspace_bytes(p) == 0
+    p = mp.default_params(m=64, n=64)
+    nbytes = mp.workspace_bytes(p)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h = ctypes.c_void_p()
+    assert lib.mpfc_create(ctypes.byref(p), ws.data_ptr(), nbytes - 1024, None, ctypes.byref(h)) == mp.MPFC_ERR_WORKSPACE
+    assert lib.mpfc_create(ctypes.byref(p), ws.data_ptr() + 8, nbytes, None, ctypes.byref(h)) == mp.MPFC_ERR_WORKSPACE
+    g = make(mp, 64, 64, 0.5, 0.01)
+    assert lib.mpfc_step(g.h, 3, 1, None) == mp.MPFC_ERR_INVALID
+
+
+def test_checkpoint_resume_bitwise(mp):
+    m, h, s = 64, 0.5, 0.05
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    a = make(mp, m, m, h, s)
+    a.set_state(phi0)
+    a.step(2, 10)
+    b = make(mp, m, m, h, s)
+    b.set_state(phi0)
+    b.step(2, 5)
+    st = b.get_state()
+    c = make(mp, m, m, h, s)
+    c.set_state(*st)
+    c.step(2, 5)
+    for x, y in zip(a.get_state(), c.get_state()):
+        assert np.array_equal(x, y)
+
+
+def test_multi_step_call_equals_single_steps(mp):
+    m = 64
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    a = make(mp, m, m, 0.5, 0.01)
+    a.set_state(phi0)
+    a.step(1, 6)
+    b = make(mp, m, m, 0.5, 0.01)
+    b.set_state(phi0)
+    for _ in range(6):
+        b.step(1, 1)
+    assert np.array_equal(a.get_state()[0], b.get_state()[0])
