@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the MPFC solver: time steps/s and fine-grid cell-updates/s.
+
+Workload (default): first-order convex-splitting scheme (Sec. 3.1) on a 1024 x 1024
+periodic grid, h = 0.5, M = 1, epsilon = 0.025, beta = 0.9, s = 0.01, phi^0 =
+0.07 + 0.05 U(-1, 1) (seeded), psi^0 = 0, FAS V(2,2) cycles to scaled residual 1e-10,
+plain FP64.  One benchmark "step" is one time step of that solve.
+
+Prints one JSON line (rank 0).  Timing: W warm-up steps, then K steps, each on the
+device between CUDA events on the solver's stream, with a 512 MB write between steps
+to flush L2 (outside the events).  Under torchrun each rank advances its own
+independent instance (weak scaling, no collective on the data path); the time is the
+maximum over ranks.
+
+--impl reference times the CPU oracle (plain serial C, FP64) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MPFC steps/s & cell-updates/s at 1024^2: plain FAS vs learned/FP32/batched, tol 1e-10"
+UNIT = "steps/s"
+
+# Algorithmic FP64 flops of one red-black sweep per cell (scheme 1, relaxed update):
+# neighbour sums 9, right-hand sides 7, Newton terms of the cubic 5, determinant 2,
+# reciprocal 1, Cramer numerators 9, phi/mu products 2, kappa 2, relaxation 9.
+SMOOTH_FLOPS_PER_CELL = 46
+# Algorithmic bytes of one sweep per cell: read u (24) and S (24), write u (24).
+SMOOTH_BYTES_PER_CELL = 72
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=1024, help="grid cells per side (workload is named by it)")
+    ap.add_argument("--scheme", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="steps only, no flush and no extras (ncu launch list)")
+    ap.add_argument("--profile-smooth", action="store_true",
+                    help="only the finest-level sweep kernel, two sweeps (ncu capture of the top kernel)")
+    return ap.parse_args()
+
+
+def workload(size, scheme):
+    return {"workload": f"mpfc-scheme{scheme}-{size}x{size}-fp64-fas-v22", "m": size, "n": size, "h": 0.5,
+            "M": 1.0, "epsilon": 0.025, "beta": 0.9, "dt": 0.01, "scheme": scheme, "tol": 1e-10,
+            "cycle": "V(2,2)", "omega": 0.8, "guess": "extrapolated", "init": "0.07+0.05*U(-1,1) seed 1",
+            "l2": "flushed between steps (512 MB write)"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+# ----------------------------------------------------------------------------- helpers
+def kernel_launches_per_step(levels, nu1, nu2, cycles, scheme):
+    prologue = 5 + (levels - 1 if scheme == 2 else 0)
+    per_cycle = (levels - 1) * (2 * nu1 + 2 + 1 + 2 * nu2) + 1 + 1
+    return prologue + cycles * per_cycle + 1
+
+
+def traffic_for(kernel, size):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source it
+    was taken on is unchanged; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except Exception:
+        return None
+    ent = data.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    if digest != ent.get("sha256"):
+        return None
+    return ent["bytes_per_launch_per_cell"] * size * size
+
+
+def cpu_oracle_rate(size, scheme, max_steps, budget_s, warmup=0):
+    """The oracle as it stands (serial C, 1 thread) on the same workload: steps/s."""
+    import oracle
+    from paper_1208_2643_gb300 import inputs
+    oracle.build()
+    w = workload(size, scheme)
+    sol = oracle.Solver(oracle.Params(m=size, n=size, h=w["h"], M=w["M"], eps=w["epsilon"], beta=w["beta"],
+                                      s=w["dt"], omega=w["omega"]))
+    sol.set_state(inputs.noise_field(size, size, 0.07, 0.05, 1))
+    for _ in range(warmup):
+        sol.step(scheme, tol=w["tol"], guess=oracle.GUESS_EXTRAP)
+    t0 = time.perf_counter()
+    done = 0
+    cycles = 0
+    while done < max_steps:
+        r = sol.step(scheme, tol=w["tol"], guess=oracle.GUESS_EXTRAP)
+        cycles += r["cycles"]
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, cycles
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    size, scheme = args.size, args.scheme
+    rate, done, dt, cycles = cpu_oracle_rate(size, scheme, max(args.steps, 1), budget_s=120.0,
+                                             warmup=min(args.warmup, 1))
+    w = workload(size, scheme)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": done, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * dt / done,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": w,
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{done} time steps of the {size}^2 workload (time budget 120 s), "
+                                       f"{cycles / done:.2f} V-cycles/step"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "cell_updates_per_s": rate * size * size}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1208_2643_gb300 import inputs, mpfc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    size, scheme = args.size, args.scheme
+    w = workload(size, scheme)
+    p = mpfc.default_params(m=size, n=size, h=w["h"], M=w["M"], epsilon=w["epsilon"], beta=w["beta"], dt=w["dt"],
+                            tol=w["tol"], omega=w["omega"], guess=mpfc.MPFC_GUESS_EXTRAP)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    solver = mpfc.Solver(p, stream=stream)
+    phi0 = inputs.noise_field(size, size, 0.07, 0.05, 1 + rank)
+    solver.set_state(phi0)
+    if args.profile_smooth:
+        phik, _, _ = solver.get_state(device=True)
+        S = solver.op_source(scheme, phik, phik, torch.zeros_like(phik))
+        u = [phik.clone(), torch.zeros_like(phik), torch.zeros_like(phik)]
+        solver.op_smooth(scheme, 0, u, S, phik if scheme == 2 else None, 2)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile_smooth": True}), flush=True)
+        return
+    solver.step(scheme, max(args.warmup, 0))
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(K):
+        if not args.profile:
+            flush.fill_(float(k))
+        starts[k].record(stream)
+        solver.step_async(scheme, 1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    rc, recs, count = solver.records(max(K, 1))
+    if rc != mpfc.MPFC_OK:
+        raise mpfc.MPFCError(rc, "timed steps")
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    cycles = [r["cycles"] for r in recs]
+    steps_per_s = world * K / (ms * 1e-3)
+    launches = sum(kernel_launches_per_step(solver.levels, p.nu1, p.nu2, c, scheme) for c in cycles)
+
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms": ms, "cycles": cycles[:5]}), flush=True)
+        return
+
+    # dominant kernel: the finest-level red-black sweep, timed on the solver's stream
+    phik, _, _ = solver.get_state(device=True)
+    S = solver.op_source(scheme, phik, phik, torch.zeros_like(phik))
+    u = [phik.clone(), torch.zeros_like(phik), torch.zeros_like(phik)]
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _check = mpfc._check
+    for it in range(2):
+        flush.fill_(1.0)
+        e0.record(stream)
+        _check(solver.lib.mpfc_op_smooth(solver.h, scheme, 0, u[0].data_ptr(), u[1].data_ptr(), u[2].data_ptr(),
+                                         S[0].data_ptr(), S[1].data_ptr(), S[2].data_ptr(),
+                                         phik.data_ptr() if scheme == 2 else None, reps), "smooth")
+        e1.record(stream)
+        torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / reps
+    fp64_peak = mpfc.probe_fp64_tflops(stream)
+    achieved = SMOOTH_FLOPS_PER_CELL * size * size / (sweep_ms * 1e-3) / 1e12
+    achieved_gbs = SMOOTH_BYTES_PER_CELL * size * size / (sweep_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = torch.from_numpy(phi0).pin_memory()
+        out_pin = torch.empty_like(pin).pin_memory()
+        Ke = K
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _check(solver.lib.mpfc_set_state(solver.h, pin.data_ptr(), None, None), "set_state")
+        infos = (mpfc.mpfc_step_info * 1)()
+        for _ in range(Ke):
+            _check(solver.lib.mpfc_step(solver.h, scheme, 1, infos), "step")
+        _check(solver.lib.mpfc_get_state(solver.h, out_pin.data_ptr(), None, None), "get_state")
+        t1 = time.perf_counter()
+        G = size * size
+        e2e = {"value": world * Ke / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": 8 * G / Ke,
+               "d2h_bytes_per_step": (8 * G + Ke * 24) / Ke,
+               "how": "mpfc_set_state from pinned host phi^0, then K x mpfc_step(1) (each reads its step "
+                      "record back), then mpfc_get_state to pinned host; host wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, done, dt, cyc = cpu_oracle_rate(size, scheme, 3, budget_s=30.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{done} time steps of the same {size}^2 workload from phi^0 "
+                         f"({cyc / done:.2f} V-cycles/step), serial C oracle"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": steps_per_s, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": w,
+                "cell_updates_per_s": steps_per_s * size * size,
+                "vcycles_per_step": float(np.mean(cycles)) if cycles else None,
+                "sweep_cell_updates_per_s": steps_per_s * size * size * (p.nu1 + p.nu2) *
+                (float(np.mean(cycles)) if cycles else 0.0),
+                "roofline": {"bound": "alu", "kernel": "k_smooth<1> (finest level, one red+black sweep)",
+                             "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s (FP64, FMA = 2)",
+                             "frac": achieved / fp64_peak,
+                             "peak_source": "measured live: FP64 FMA-chain probe on this GPU",
+                             "hbm_gbs_algorithmic": achieved_gbs,
+                             "sweep_ms": sweep_ms,
+                             "traffic": traffic_for("k_smooth", size)},
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

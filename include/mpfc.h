@@ -108,6 +108,19 @@ int mpfc_get_state(mpfc_t* h, double* phi, double* phi_prev, double* psi);
  * receives each step's record.  Synchronises the stream. */
 int mpfc_step(mpfc_t* h, int scheme, int nsteps, mpfc_step_info* per_step);
 
+/* Enqueues nsteps steps on the handle's stream and returns without synchronising.
+ * Each step appends its record to a device-side log of 1024 entries (later records
+ * are counted but not kept); a failing step halts the steps after it until
+ * mpfc_records or mpfc_set_state.  Graph construction on the first call of a scheme
+ * must not happen inside a stream capture. */
+int mpfc_step_async(mpfc_t* h, int scheme, int nsteps);
+
+/* Synchronises, copies up to max_records step records (oldest first) to `out`
+ * (host, nullable), stores the number of steps logged since the last call in
+ * *count (nullable), clears the log and the halt flag, and returns the first
+ * failing status among the copied records (MPFC_OK if none). */
+int mpfc_records(mpfc_t* h, mpfc_step_info* out, int max_records, int* count);
+
 /* One step with exactly ncycles V-cycles (no tolerance test), for lockstep
  * comparisons.  Same state update and synchronisation as mpfc_step. */
 int mpfc_step_cycles(mpfc_t* h, int scheme, int ncycles, mpfc_step_info* info);

@@ -1,0 +1,25 @@
+/*
+ * mpfc_probe.h -- measurement helpers of libmpfc (no counterpart in the paper).
+ *
+ * The FP64 kernels of the solver are bound by FP64 instruction issue on GB300, so
+ * their roofline needs the FP64 FMA rate of the GPU they run on.
+ */
+#ifndef MPFC_PROBE_H
+#define MPFC_PROBE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Measures the sustained FP64 FMA rate of the current device with a kernel of
+ * independent FMA chains on every SM (about 10 ms of work, timed with CUDA events on
+ * `cuda_stream`, best of three).  *tflops receives 2 x FMAs per second / 1e12.
+ * `d_scratch` is device memory of at least 152*8*256*8 bytes (written).  Returns 0
+ * or MPFC_ERR_CUDA. */
+int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

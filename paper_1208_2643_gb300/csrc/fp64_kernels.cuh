@@ -535,7 +535,7 @@ __global__ void k_commit(const double* __restrict__ phinew, double* phik, double
     r.status = st;
     r.res0 = ctl->res0;
     r.res_final = ctl->res;
-    info[ctl->slot] = r;
+    if (ctl->slot < kInfoCap) info[ctl->slot] = r;
     ctl->slot += 1;
     if (st != 0) ctl->halt = 1;
   }

@@ -554,6 +554,41 @@ extern "C" int mpfc_step(mpfc_t* H, int scheme, int nsteps, mpfc_step_info* per_
   return run_steps(H, scheme, nsteps, 0, per_step);
 }
 
+extern "C" int mpfc_step_async(mpfc_t* H, int scheme, int nsteps) {
+  if (!H || (scheme != 1 && scheme != 2) || nsteps < 0) return MPFC_ERR_INVALID;
+  if (H->p.guess == MPFC_GUESS_LEARNED && !mpfc_has_guess_model(H)) return MPFC_ERR_INVALID;
+  int rc = ensure_graph(H, scheme);
+  if (rc != MPFC_OK) return rc;
+  for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_records(mpfc_t* H, mpfc_step_info* out, int max_records, int* count) {
+  if (!H || max_records < 0) return MPFC_ERR_INVALID;
+  Ctl c;
+  CK(cudaMemcpyAsync(&c, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, H->stream));
+  CK(cudaStreamSynchronize(H->stream));
+  int n = c.slot < kInfoCap ? c.slot : kInfoCap;
+  if (n > max_records) n = max_records;
+  std::vector<StepRecord> rec(n > 0 ? n : 1);
+  if (n > 0) CK(cudaMemcpyAsync(rec.data(), H->info, n * sizeof(StepRecord), cudaMemcpyDeviceToHost, H->stream));
+  k_ctl_reset<<<1, 32, 0, H->stream>>>(H->ctl, 0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(H->stream));
+  int first = MPFC_OK;
+  for (int k = 0; k < n; ++k) {
+    if (out) {
+      out[k].cycles = rec[k].cycles;
+      out[k].status = rec[k].status;
+      out[k].res0 = rec[k].res0;
+      out[k].res_final = rec[k].res_final;
+    }
+    if (rec[k].status != 0 && first == MPFC_OK) first = rec[k].status;
+  }
+  if (count) *count = c.slot;
+  return first;
+}
+
 extern "C" int mpfc_step_cycles(mpfc_t* H, int scheme, int ncycles, mpfc_step_info* info) {
   if (ncycles < 1) return MPFC_ERR_INVALID;
   return run_steps(H, scheme, 1, ncycles, info);

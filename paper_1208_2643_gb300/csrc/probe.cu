@@ -1,0 +1,44 @@
+// FP64 FMA-rate probe used for the roofline of the FP64 kernels (see include/mpfc_probe.h).
+#include <cuda_runtime.h>
+
+#include "../../include/mpfc.h"
+#include "../../include/mpfc_probe.h"
+
+namespace {
+constexpr int kBlocks = 152 * 8, kThreads = 256, kIters = 2000;
+
+__global__ void k_fma_chains(double* out, double seed) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double a0 = seed + t * 1e-9, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+         a7 = a0 + 7;
+  const double m = 0.999999, c = 1e-7;
+  for (int i = 0; i < kIters; ++i) {
+    a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+  }
+  out[t] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+}  // namespace
+
+extern "C" int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* tflops) {
+  if (!d_scratch || !tflops) return MPFC_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MPFC_ERR_CUDA;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, s);
+    k_fma_chains<<<kBlocks, kThreads, 0, s>>>((double*)d_scratch, 1.0);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return MPFC_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) return MPFC_ERR_CUDA;
+  double fmas = (double)kBlocks * kThreads * kIters * 8.0;
+  *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+  return MPFC_OK;
+}

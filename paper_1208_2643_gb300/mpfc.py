@@ -83,6 +83,9 @@ def load(build_if_missing: bool = True):
     lib.mpfc_get_state.argtypes = [_VP, _VP, _VP, _VP]
     lib.mpfc_step.argtypes = [_VP, ctypes.c_int, ctypes.c_int, P(mpfc_step_info)]
     lib.mpfc_step_cycles.argtypes = [_VP, ctypes.c_int, ctypes.c_int, P(mpfc_step_info)]
+    lib.mpfc_step_async.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+    lib.mpfc_records.argtypes = [_VP, P(mpfc_step_info), ctypes.c_int, P(ctypes.c_int)]
+    lib.mpfc_probe_fp64_fma.argtypes = [_VP, _VP, P(ctypes.c_double)]
     lib.mpfc_mass.argtypes = [_VP, P(ctypes.c_double)]
     lib.mpfc_energy.argtypes = [_VP, P(mpfc_energy_t)]
     lib.mpfc_strerror.argtypes = [ctypes.c_int]
@@ -224,6 +227,18 @@ class Solver:
             raise MPFCError(rc, "mpfc_step")
         return out if raise_on_error else (rc, out)
 
+    def step_async(self, scheme: int, nsteps: int = 1):
+        """Enqueues steps without synchronising (records via records())."""
+        _check(self.lib.mpfc_step_async(self.h, scheme, nsteps), "mpfc_step_async")
+
+    def records(self, max_records: int = 1024):
+        """Synchronises and returns (status, records, count) of the steps since the last call."""
+        infos = (mpfc_step_info * max(max_records, 1))()
+        cnt = ctypes.c_int()
+        rc = self.lib.mpfc_records(self.h, infos, max_records, ctypes.byref(cnt))
+        n = min(cnt.value, max_records)
+        return rc, [dict(cycles=i.cycles, status=i.status, res0=i.res0, res=i.res_final) for i in infos[:n]], cnt.value
+
     def step_cycles(self, scheme: int, ncycles: int):
         info = mpfc_step_info()
         _check(self.lib.mpfc_step_cycles(self.h, scheme, ncycles, ctypes.byref(info)), "mpfc_step_cycles")
@@ -281,3 +296,14 @@ class Solver:
         _check(self.lib.mpfc_op_coarse_solve(self.h, scheme, *[_ptr(x) for x in u], *[_ptr(s) for s in S],
                                              _ptr(phik)), "mpfc_op_coarse_solve")
         return u
+
+
+def probe_fp64_tflops(stream=None) -> float:
+    """Measured FP64 FMA rate of the current GPU (2 flops per FMA), in TFLOP/s."""
+    import torch
+    lib = load()
+    scratch = torch.empty(152 * 8 * 256, dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = ctypes.c_double()
+    _check(lib.mpfc_probe_fp64_fma(scratch.data_ptr(), st.cuda_stream, ctypes.byref(v)), "mpfc_probe_fp64_fma")
+    return v.value
