@@ -34,6 +34,7 @@ extern "C" {
 #define MPFC_ERR_CUDA (-3)          /* a CUDA runtime call failed                       */
 #define MPFC_ERR_NOT_CONVERGED (-4) /* max_cycles V-cycles without reaching tol         */
 #define MPFC_ERR_DIVERGED (-5)      /* residual became non-finite or grew by > 1e10     */
+#define MPFC_ERR_TOO_LARGE (-6)     /* grid larger than mpfc_mass_noalloc's static scratch allows */
 
 #define MPFC_FP64 0       /* every V-cycle kernel in FP64                                  */
 #define MPFC_FP32_INNER 1 /* FP64 outer defect correction around FP32 inner V-cycles       */
@@ -132,6 +133,22 @@ int mpfc_mass(mpfc_t* h, double* out);
  * (A.16)-(A.18), comes from a periodic Poisson multigrid solve to 1e-13 relative
  * residual.  Synchronises. */
 int mpfc_energy(mpfc_t* h, mpfc_energy_t* out);
+
+/* Mass h^2 sum phi of a caller's device array, without any device allocation and
+ * without a handle.  The paper has no counterpart: this is for callers that cannot
+ * allocate device memory -- code running while a stream is being captured into a
+ * CUDA graph (where cudaMalloc is not allowed), hosts that own all of the GPU's memory
+ * through their own pool, and latency-bound loops that cannot afford cudaMalloc's
+ * implicit synchronisation -- and that hold only a field, not a solver workspace.
+ * Its scratch (8.2 KB of partial sums) is a static array in the library's device
+ * image, present on every GPU that loads the library until the process exits.
+ * The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  Every call shares the array, so
+ * calls whose kernels overlap on the GPU race: serialise them (one stream, or
+ * synchronise between calls).  Grids above 2048 x 2048 cells are rejected with
+ * MPFC_ERR_TOO_LARGE.  d_phi: m*n doubles on the current device; out: host.
+ * Synchronises `cuda_stream` (a cudaStream_t; NULL = legacy stream). */
+int mpfc_mass_noalloc(const double* d_phi, int m, int n, double h, void* cuda_stream, double* out);
 
 /* Message for a status code. */
 const char* mpfc_strerror(int status);

@@ -688,6 +688,7 @@ extern "C" const char* mpfc_strerror(int status) {
     case MPFC_ERR_CUDA: return g_last_cuda_error[0] ? g_last_cuda_error : "CUDA error";
     case MPFC_ERR_NOT_CONVERGED: return "V-cycle limit reached before the tolerance";
     case MPFC_ERR_DIVERGED: return "residual became non-finite or grew beyond 1e10 times its start";
+    case MPFC_ERR_TOO_LARGE: return "grid exceeds the 2048 x 2048 cells the static scratch of mpfc_mass_noalloc allows";
     default: return "unknown status";
   }
 }
