@@ -220,6 +220,8 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"profile_smooth": True}), flush=True)
         return
+    if args.profile:
+        solver.set_launch_mode(mpfc.MPFC_LAUNCH_STREAM)   # profilers cannot see inside conditional graph nodes
     solver.step(scheme, max(args.warmup, 0))
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

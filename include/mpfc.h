@@ -39,6 +39,9 @@ extern "C" {
 #define MPFC_FP64 0       /* every V-cycle kernel in FP64                                  */
 #define MPFC_FP32_INNER 1 /* FP64 outer defect correction around FP32 inner V-cycles       */
 
+#define MPFC_LAUNCH_GRAPH 0  /* a time step is one CUDA graph with a device-side loop (default) */
+#define MPFC_LAUNCH_STREAM 1 /* kernels launched one by one, loop decided on the host           */
+
 #define MPFC_GUESS_PREV 0    /* phi^(0) = phi^k                                            */
 #define MPFC_GUESS_EXTRAP 1  /* phi^(0) = 2 phi^k - phi^{k-1}                              */
 #define MPFC_GUESS_LEARNED 2 /* extrapolation plus the learned correction (mpfc_set_guess_model) */
@@ -121,6 +124,14 @@ int mpfc_step_async(mpfc_t* h, int scheme, int nsteps);
  * *count (nullable), clears the log and the halt flag, and returns the first
  * failing status among the copied records (MPFC_OK if none). */
 int mpfc_records(mpfc_t* h, mpfc_step_info* out, int max_records, int* count);
+
+/* Chooses how steps are launched.  MPFC_LAUNCH_GRAPH replays one CUDA graph per step
+ * whose conditional WHILE node runs the V-cycles until the device-side residual test
+ * fails.  MPFC_LAUNCH_STREAM launches the same kernels in the same order on the
+ * stream and reads the loop decision back after each cycle (for profilers and
+ * debuggers that cannot look inside conditional graph nodes); with it mpfc_step_async
+ * synchronises once per V-cycle. */
+int mpfc_set_launch_mode(mpfc_t* h, int mode);
 
 /* One step with exactly ncycles V-cycles (no tolerance test), for lockstep
  * comparisons.  Same state update and synchronisation as mpfc_step. */

@@ -18,6 +18,11 @@ extern "C" {
  * or MPFC_ERR_CUDA. */
 int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* tflops);
 
+/* Applies the smoother's double-precision reciprocal (one Newton-Raphson step from
+ * the correctly rounded single-precision reciprocal) to n device doubles, for tests
+ * of its error bound.  Asynchronous on `cuda_stream`. */
+int mpfc_probe_rcp(const double* d_x, double* d_out, int n, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

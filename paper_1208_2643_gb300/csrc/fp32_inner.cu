@@ -11,3 +11,7 @@ int mpfc_fp32_enqueue_step(mpfc_s* H, int scheme, cudaStream_t cs, cudaGraphCond
   (void)H; (void)scheme; (void)cs; (void)hnd;
   return MPFC_ERR_INVALID;
 }
+int mpfc_fp32_step_stream(mpfc_s* H, int scheme) {
+  (void)H; (void)scheme;
+  return MPFC_ERR_INVALID;
+}

@@ -110,30 +110,43 @@ __global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, int color) {
   double ska = (__ldg(ka + w) + __ldg(ka + e)) + (__ldg(ka + s) + __ldg(ka + nn));
   double sph = (__ldg(phi + w) + __ldg(phi + e)) + (__ldg(phi + s) + __ldg(phi + nn));
   double p = phi[c];
-  double pk = (SCH == 2) ? __ldg(L.pk + c) : 0.0;
-  // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p)
-  double q = dg_of<SCH>(p, pk);
-  double eterm = g_of<SCH>(p, pk) - q * p;
   double R1 = fma(k.cmu, smu, __ldg(L.S1 + c));
-  double R2 = fma(k.ih2, ska, __ldg(L.S2 + c) + eterm);
   double R3 = fma(k.th2, sph, __ldg(L.S3 + c));
-  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]]
-  double det = fma(k.a, q, k.D0);
-  double rdet = 1.0 / det;
-  double nphi = fma(k.a, fma(k.b, R3, -R2), R1);
-  double nmu = fma(k.Q0 + q, R1, fma(-k.b, R3, R2));
-  double phin = nphi * rdet;
-  double mun = nmu * rdet;
-  double kan = fma(-k.b3, phin, R3);
-  if (k.omega != 1.0) {
-    double m0 = mu[c], k0 = ka[c];
-    phin = fma(k.omega, phin - p, p);
-    mun = fma(k.omega, mun - m0, m0);
-    kan = fma(k.omega, kan - k0, k0);
+  // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
+  // q = g'(p) enters the determinant and the Cramer numerator of mu, and
+  // e = g(p) - g'(p) p the right-hand side of row 2
+  double R2, det, Qq;
+  if (SCH == 1) {
+    double p2 = p * p;
+    R2 = fma(k.ih2, ska, fma(-2.0, p2 * p, __ldg(L.S2 + c)));   // e = -2 p^3
+    det = fma(k.a3, p2, k.D0);                                    // q = 3 p^2
+    Qq = fma(3.0, p2, k.Q0);
+  } else {
+    double pk = __ldg(L.pk + c);
+    double q = dg_of<2>(p, pk);
+    R2 = fma(k.ih2, ska, __ldg(L.S2 + c) + (g_of<2>(p, pk) - q * p));
+    det = fma(k.a, q, k.D0);
+    Qq = k.Q0 + q;
   }
-  phi[c] = phin;
-  mu[c] = mun;
-  ka[c] = kan;
+  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]]:
+  //   phi* = (R1 + a (b R3 - R2)) / det,  mu* = ((Q0 + q) R1 + R2 - b R3) / det,
+  //   kappa* = R3 - b3 phi*; then u <- (1 - omega) u + omega u*
+  double rdet = rcp_nr(det);
+  double nphi = fma(k.a, fma(k.b, R3, -R2), R1);
+  double nmu = fma(Qq, R1, fma(-k.b, R3, R2));
+  if (k.relax) {
+    double wr = k.omega * rdet;
+    double wphi = nphi * wr;
+    double m0 = mu[c], k0 = ka[c];
+    phi[c] = fma(k.omw, p, wphi);
+    mu[c] = fma(k.omw, m0, nmu * wr);
+    ka[c] = fma(-k.b3, wphi, fma(k.omega, R3, k.omw * k0));
+  } else {
+    double phin = nphi * rdet;
+    phi[c] = phin;
+    mu[c] = nmu * rdet;
+    ka[c] = fma(-k.b3, phin, R3);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -255,26 +268,6 @@ __global__ void k_restrict_plane(const double* __restrict__ f, double* __restric
 // FAS correction: u_f += P(u_c - b_c), P the cell-centred bilinear stencil
 // (9, 3, 3, 1)/16.  One thread per coarse cell writes its 2x2 fine children.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, const double* __restrict__ co,
-                                              double* __restrict__ f, int mc, int nc, int I, int J) {
-  int Im = wrapm(I - 1, mc), Ip = wrapm(I + 1, mc), Jm = wrapm(J - 1, nc), Jp = wrapm(J + 1, nc);
-  auto E = [&](int a, int b) {
-    size_t id = (size_t)b * mc + a;
-    return __ldg(cn + id) - __ldg(co + id);
-  };
-  double e00 = E(I, J);
-  double eW = E(Im, J), eE = E(Ip, J), eS = E(I, Jm), eN = E(I, Jp);
-  double eSW = E(Im, Jm), eSE = E(Ip, Jm), eNW = E(Im, Jp), eNE = E(Ip, Jp);
-  const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
-  int mf = 2 * mc;
-  size_t f00 = (size_t)(2 * J) * mf + 2 * I;
-  size_t f01 = f00 + mf;
-  f[f00] += fma(w9, e00, fma(w3, eW + eS, w1 * eSW));
-  f[f00 + 1] += fma(w9, e00, fma(w3, eE + eS, w1 * eSE));
-  f[f01] += fma(w9, e00, fma(w3, eW + eN, w1 * eNW));
-  f[f01 + 1] += fma(w9, e00, fma(w3, eE + eN, w1 * eNE));
-}
-
 struct ProlongArgs {
   const double *cphi, *cmu, *cka;   // coarse u after the coarse solve
   const double *ophi, *omu, *oka;   // coarse R u_f before it
@@ -282,13 +275,46 @@ struct ProlongArgs {
   int mc, nc;
 };
 
-__global__ void k_prolong(ProlongArgs A) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I >= A.mc || J >= A.nc) return;
-  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, I, J);
-  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, I, J);
-  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, I, J);
+// One thread per coarse cell; the block first stages e = u_c - b_c on its
+// (32+2) x (8+2) coarse tile (periodic halo) in shared memory, so each difference
+// is formed once, then writes the bilinear correction into its 2x2 fine children.
+constexpr int kPTX = 32, kPTY = 8;
+__device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, const double* __restrict__ co,
+                                              double* __restrict__ f, int mc, int nc, double (*E)[kPTX + 2]) {
+  const int I0 = blockIdx.x * kPTX, J0 = blockIdx.y * kPTY;
+  for (int t = threadIdx.y * kPTX + threadIdx.x; t < (kPTX + 2) * (kPTY + 2); t += kPTX * kPTY) {
+    int ty = t / (kPTX + 2), tx = t % (kPTX + 2);
+    int I = wrapm(I0 + tx - 1, mc), J = wrapm(J0 + ty - 1, nc);
+    if (I0 + tx - 1 < mc + 1 && J0 + ty - 1 < nc + 1) {
+      size_t id = (size_t)J * mc + I;
+      E[ty][tx] = __ldg(cn + id) - __ldg(co + id);
+    }
+  }
+  __syncthreads();
+  int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  if (I < mc && J < nc) {
+    int x = threadIdx.x + 1, y = threadIdx.y + 1;
+    double e00 = E[y][x];
+    double eW = E[y][x - 1], eE = E[y][x + 1], eS = E[y - 1][x], eN = E[y + 1][x];
+    double eSW = E[y - 1][x - 1], eSE = E[y - 1][x + 1], eNW = E[y + 1][x - 1], eNE = E[y + 1][x + 1];
+    const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
+    int mf = 2 * mc;
+    size_t f00 = (size_t)(2 * J) * mf + 2 * I;
+    size_t f01 = f00 + mf;
+    double c9 = w9 * e00;
+    f[f00] += fma(w3, eW + eS, fma(w1, eSW, c9));
+    f[f00 + 1] += fma(w3, eE + eS, fma(w1, eSE, c9));
+    f[f01] += fma(w3, eW + eN, fma(w1, eNW, c9));
+    f[f01 + 1] += fma(w3, eE + eN, fma(w1, eNE, c9));
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
+  __shared__ double E[kPTY + 2][kPTX + 2];
+  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, E);
+  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, E);
+  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, E);
 }
 
 // ---------------------------------------------------------------------------

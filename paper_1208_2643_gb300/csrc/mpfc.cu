@@ -107,6 +107,10 @@ Coef mpfc_coef(const mpfc_params* p, int scheme, double h) {
   k.th2 = k.theta / h2;
   k.D0 = 1.0 + k.a * k.gam + k.a * k.b * k.b3;
   k.Q0 = k.gam + k.b * k.b3;
+  k.a3 = 3.0 * k.a;
+  k.omw = 1.0 - k.omega;
+  k.relax = (k.omega != 1.0);
+  k.pad = 0;
   return k;
 }
 
@@ -475,7 +479,66 @@ void mpfc_enqueue_commit(mpfc_s* H, int scheme, cudaStream_t s) {
   else enqueue_commit<2>(H, s);
 }
 
+// Host mirror of the device-side loop decision of k_resnorm.
+static bool host_continue(const Ctl& c) {
+  if (c.skip || c.status != 0) return false;
+  if (c.fixed_cycles > 0) return c.cycles < c.fixed_cycles;
+  return c.res > c.tol && c.cycles < c.max_cycles;
+}
+
+// One step launched kernel by kernel on the stream, with the loop decision read
+// back after every residual test (same kernels, same order as the graph).
+static int step_stream_mode(mpfc_s* H, int scheme) {
+  cudaStream_t s = H->stream;
+  if (H->p.precision == MPFC_FP32_INNER) return mpfc_fp32_step_stream(H, scheme);
+  if (scheme == 1) {
+    enqueue_prologue<1>(H, s);
+    enqueue_resnorm<1>(H, 0, 0, 0, s);
+  } else {
+    enqueue_prologue<2>(H, s);
+    enqueue_resnorm<2>(H, 0, 0, 0, s);
+  }
+  for (;;) {
+    Ctl c;
+    CK(cudaMemcpyAsync(&c, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!host_continue(c)) break;
+    if (scheme == 1) {
+      enqueue_vcycle<1>(H, s);
+      enqueue_resnorm<1>(H, 1, 0, 0, s);
+    } else {
+      enqueue_vcycle<2>(H, s);
+      enqueue_resnorm<2>(H, 1, 0, 0, s);
+    }
+  }
+  if (scheme == 1) enqueue_commit<1>(H, s);
+  else enqueue_commit<2>(H, s);
+  CK(cudaGetLastError());
+  return MPFC_OK;
+}
+
+int mpfc_host_continue(const Ctl* c) { return host_continue(*c) ? 1 : 0; }
+
+static int launch_steps(mpfc_s* H, int scheme, int nsteps) {
+  if (H->launch_mode == MPFC_LAUNCH_STREAM) {
+    for (int k = 0; k < nsteps; ++k) {
+      int rc = step_stream_mode(H, scheme);
+      if (rc != MPFC_OK) return rc;
+    }
+    return MPFC_OK;
+  }
+  for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_set_launch_mode(mpfc_t* H, int mode) {
+  if (!H || (mode != MPFC_LAUNCH_GRAPH && mode != MPFC_LAUNCH_STREAM)) return MPFC_ERR_INVALID;
+  H->launch_mode = mode;
+  return MPFC_OK;
+}
+
 static int ensure_graph(mpfc_s* H, int scheme) {
+  if (H->launch_mode == MPFC_LAUNCH_STREAM) return MPFC_OK;
   if (H->exec[scheme - 1][0]) return MPFC_OK;
   return scheme == 1 ? build_step_graph<1>(H) : build_step_graph<2>(H);
 }
@@ -517,7 +580,8 @@ static int run_steps(mpfc_s* H, int scheme, int nsteps, int fixed_cycles, mpfc_s
     int chunk = nsteps - done < kInfoCap ? nsteps - done : kInfoCap;
     k_ctl_reset<<<1, 32, 0, H->stream>>>(H->ctl, fixed_cycles);
     CK(cudaGetLastError());
-    for (int k = 0; k < chunk; ++k) CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
+    rc = launch_steps(H, scheme, chunk);
+    if (rc != MPFC_OK) return rc;
     CK(cudaMemcpyAsync(rec.data(), H->info, chunk * sizeof(StepRecord), cudaMemcpyDeviceToHost, H->stream));
     CK(cudaStreamSynchronize(H->stream));
     for (int k = 0; k < chunk; ++k) {
@@ -559,8 +623,7 @@ extern "C" int mpfc_step_async(mpfc_t* H, int scheme, int nsteps) {
   if (H->p.guess == MPFC_GUESS_LEARNED && !mpfc_has_guess_model(H)) return MPFC_ERR_INVALID;
   int rc = ensure_graph(H, scheme);
   if (rc != MPFC_OK) return rc;
-  for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
-  return MPFC_OK;
+  return launch_steps(H, scheme, nsteps);
 }
 
 extern "C" int mpfc_records(mpfc_t* H, mpfc_step_info* out, int max_records, int* count) {

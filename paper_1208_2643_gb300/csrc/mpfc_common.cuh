@@ -36,7 +36,22 @@ struct Coef {
   double th2;   // theta / h^2
   double D0;    // 1 + a gam + a b b3    (determinant without the cubic)
   double Q0;    // gam + b b3            (Cramer numerator of mu without the cubic)
+  double a3;    // 3 a                   (scheme 1: det = D0 + 3 a p^2)
+  double omw;   // 1 - omega
+  int relax;    // omega != 1
+  int pad;
 };
+
+// Reciprocal by one Newton-Raphson step (r <- r + r (1 - x r), Newton's method for
+// f(r) = 1/r - x) from the correctly rounded single-precision reciprocal of x.  The
+// seed's relative error is below 2^-23 (including the rounding of x to single), and
+// one step squares it: |r x - 1| < 2^-45 for x in the normal single range.  The
+// smoother's cell solve needs no more: its error only perturbs an iterate, not the
+// fixed point.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r = (double)__frcp_rn(__double2float_rn(x));
+  return fma(r, fma(-x, r, 1.0), r);
+}
 
 // Device-side control block of the time stepper.
 struct Ctl {

@@ -37,6 +37,7 @@ struct mpfc_s {
   double* pf[mpfc::kMaxLevels];
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaGraphConditionalHandle cur_handle = 0;   // handle of the graph being captured
+  int launch_mode = MPFC_LAUNCH_GRAPH;
   // mixed precision
   Lev32 lev32[mpfc::kMaxLevels];
   float* K3f[2] = {nullptr, nullptr};
@@ -59,6 +60,8 @@ size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base,
 int mpfc_fp32_init(mpfc_s* H);
 void mpfc_fp32_destroy(mpfc_s* H);
 int mpfc_fp32_enqueue_step(mpfc_s* H, int scheme, cudaStream_t cs, cudaGraphConditionalHandle hnd);
+int mpfc_fp32_step_stream(mpfc_s* H, int scheme);
+int mpfc_host_continue(const mpfc::Ctl* c);
 
 // learned initial guess (guess_cnn.cu)
 bool mpfc_has_guess_model(const mpfc_s* H);

@@ -3,6 +3,7 @@
 
 #include "../../include/mpfc.h"
 #include "../../include/mpfc_probe.h"
+#include "mpfc_common.cuh"
 
 namespace {
 constexpr int kBlocks = 152 * 8, kThreads = 256, kIters = 2000;
@@ -41,4 +42,18 @@ extern "C" int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* t
   double fmas = (double)kBlocks * kThreads * kIters * 8.0;
   *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
   return MPFC_OK;
+}
+
+namespace {
+__global__ void k_rcp(const double* __restrict__ x, double* __restrict__ y, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = mpfc::rcp_nr(x[i]);
+}
+}  // namespace
+
+extern "C" int mpfc_probe_rcp(const double* d_x, double* d_out, int n, void* cuda_stream) {
+  if (!d_x || !d_out || n < 0) return MPFC_ERR_INVALID;
+  if (n == 0) return MPFC_OK;
+  k_rcp<<<(n + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(d_x, d_out, n);
+  return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
 }

@@ -24,6 +24,9 @@ MPFC_ERR_DIVERGED = -5
 MPFC_FP64 = 0
 MPFC_FP32_INNER = 1
 
+MPFC_LAUNCH_GRAPH = 0
+MPFC_LAUNCH_STREAM = 1
+
 MPFC_GUESS_PREV = 0
 MPFC_GUESS_EXTRAP = 1
 MPFC_GUESS_LEARNED = 2
@@ -86,6 +89,8 @@ def load(build_if_missing: bool = True):
     lib.mpfc_step_async.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
     lib.mpfc_records.argtypes = [_VP, P(mpfc_step_info), ctypes.c_int, P(ctypes.c_int)]
     lib.mpfc_probe_fp64_fma.argtypes = [_VP, _VP, P(ctypes.c_double)]
+    lib.mpfc_probe_rcp.argtypes = [_VP, _VP, ctypes.c_int, _VP]
+    lib.mpfc_set_launch_mode.argtypes = [_VP, ctypes.c_int]
     lib.mpfc_mass.argtypes = [_VP, P(ctypes.c_double)]
     lib.mpfc_energy.argtypes = [_VP, P(mpfc_energy_t)]
     lib.mpfc_strerror.argtypes = [ctypes.c_int]
@@ -226,6 +231,9 @@ class Solver:
         if rc != MPFC_OK and raise_on_error:
             raise MPFCError(rc, "mpfc_step")
         return out if raise_on_error else (rc, out)
+
+    def set_launch_mode(self, mode: int):
+        _check(self.lib.mpfc_set_launch_mode(self.h, mode), "mpfc_set_launch_mode")
 
     def step_async(self, scheme: int, nsteps: int = 1):
         """Enqueues steps without synchronising (records via records())."""

@@ -319,3 +319,31 @@ def test_multi_step_call_equals_single_steps(mp):
     for _ in range(6):
         b.step(1, 1)
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
+
+
+def test_stream_launch_mode_matches_graph(mp):
+    """The same kernels launched one by one (host-side loop test) give bitwise the same steps."""
+    m = 96
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    res = []
+    for mode in (mp.MPFC_LAUNCH_GRAPH, mp.MPFC_LAUNCH_STREAM):
+        g = make(mp, m, m, 0.5, 0.05)
+        g.set_launch_mode(mode)
+        g.set_state(phi0)
+        infos = g.step(2, 4)
+        res.append((g.get_state()[0], [i["cycles"] for i in infos]))
+    assert res[0][1] == res[1][1]
+    assert np.array_equal(res[0][0], res[1][0])
+
+
+def test_smoother_reciprocal_error_bound(mp):
+    """The cell solve's reciprocal (Newton-Raphson step from the single-precision
+    reciprocal) stays within 2^-44 relative of the IEEE double quotient."""
+    lib = mp.load()
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.uniform(1.0, 2.0, 4096), 10.0 ** rng.uniform(-3, 12, 4096), [1.0, 3.0, 7.0, 1e10]])
+    xd = dev(x)
+    y = torch.empty_like(xd)
+    assert lib.mpfc_probe_rcp(xd.data_ptr(), y.data_ptr(), x.size, None) == 0
+    rel = np.abs(host(y) * x - 1.0)
+    assert rel.max() < 2.0 ** -44, rel.max()
