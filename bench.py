@@ -225,6 +225,24 @@ def run_ours(args):
     solver.step(scheme, max(args.warmup, 0))
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed_steps(slv, K, warm):
+        """K steps of slv, each between events on the stream, L2 flushed in between."""
+        slv.step(scheme, warm)
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.fill_(float(k))
+            st[k].record(stream)
+            slv.step_async(scheme, 1)
+            en[k].record(stream)
+        torch.cuda.synchronize()
+        rc_, recs_, _ = slv.records(max(K, 1))
+        if rc_ != mpfc.MPFC_OK:
+            raise mpfc.MPFCError(rc_, "timed steps")
+        return sum(a.elapsed_time(b) for a, b in zip(st, en)), recs_
+
     K = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
@@ -299,6 +317,38 @@ def run_ours(args):
                "how": "mpfc_set_state from pinned host phi^0, then K x mpfc_step(1) (each reads its step "
                       "record back), then mpfc_get_state to pinned host; host wall clock"}
 
+    # the other forms on the same workload and protocol
+    forms = {"fp64": {"steps_per_s": steps_per_s, "vcycles_per_step": float(np.mean(cycles)),
+                      "error_vs_fp64_oracle": "lockstep parity <= 1e-10 per step (tests)"}}
+    p32 = mpfc.default_params(m=size, n=size, h=w["h"], M=w["M"], epsilon=w["epsilon"], beta=w["beta"], dt=w["dt"],
+                              tol=w["tol"], omega=w["omega"], guess=mpfc.MPFC_GUESS_EXTRAP,
+                              precision=mpfc.MPFC_FP32_INNER)
+    s32 = mpfc.Solver(p32, stream=stream)
+    s32.set_state(phi0)
+    ms32, recs32 = timed_steps(s32, K, max(args.warmup, 0))
+    if world > 1:
+        t = torch.tensor([ms32], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms32 = float(t.item())
+    # error of the mixed-precision steps against the FP64 path, 5 steps from phi^0
+    a64 = mpfc.Solver(p, stream=stream)
+    a32 = mpfc.Solver(p32, stream=stream)
+    a64.set_state(phi0)
+    a32.set_state(phi0)
+    err32 = 0.0
+    for _ in range(5):
+        a64.step(scheme, 1)
+        a32.step(scheme, 1)
+        x64, x32 = a64.get_state()[0], a32.get_state()[0]
+        err32 = max(err32, float(np.abs(x32 - x64).max() / np.abs(x64).max()))
+    forms["fp32_inner"] = {"steps_per_s": world * K / (ms32 * 1e-3),
+                           "outer_iterations_per_step": float(np.mean([r["cycles"] for r in recs32])),
+                           "fp32_vcycles_per_outer": 2,
+                           "max_rel_error_vs_fp64_per_step": err32,
+                           "speedup_vs_fp64": (world * K / (ms32 * 1e-3)) / steps_per_s}
+    for obj in (s32, a64, a32):
+        obj.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, done, dt, cyc = cpu_oracle_rate(size, scheme, 3, budget_s=30.0)
@@ -321,6 +371,7 @@ def run_ours(args):
                              "hbm_gbs_algorithmic": achieved_gbs,
                              "sweep_ms": sweep_ms,
                              "traffic": traffic_for("k_smooth", size)},
+                "forms": forms,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -61,6 +61,7 @@ typedef struct {
   int max_cycles;    /* V-cycle limit per step                                            */
   int precision;     /* MPFC_FP64 or MPFC_FP32_INNER                                      */
   int guess;         /* MPFC_GUESS_*                                                      */
+  int inner_cycles;  /* MPFC_FP32_INNER: FP32 V-cycles per FP64 outer iteration (0 = 2)   */
 } mpfc_params;
 
 typedef struct {

@@ -1,17 +1,470 @@
 // Mixed-precision form: FP64 outer defect correction around FP32 inner V-cycles.
+//
+// Outer iteration (FP64): r = S - N(u) with N of App. B.1/B.2, and the local Newton
+// linearisation of the cubic, q = gam + g'(phi), both evaluated in double precision.
+// Inner solve (FP32): the linearised correction equation J(u) e = r,
+//   e_phi - c Delta_h e_mu = r1,  e_mu - q e_phi - Delta_h e_kappa = r2,
+//   e_kappa - theta Delta_h e_phi = r3,
+// by `inner_cycles` correction-scheme V-cycles: the same red-black block Gauss-Seidel
+// cell solve as App. B (with q frozen, so no cubic), 2x2 averaging of the defect,
+// bilinear prolongation of the coarse correction, and a direct FP32 solve on the
+// coarsest grid.  Then u += e in FP64, and the loop test runs on the FP64 residual.
+// The converged answer is therefore the FP64 solution at the FP64 tolerance; FP32
+// only limits how much each outer iteration gains.
+#include <string.h>
+
+#include <vector>
+
+#include "fp64_kernels.cuh"
 #include "mpfc_internal.h"
 
+using namespace mpfc;
+
+namespace {
+
+struct Coef32 {
+  float cmu, a, ih2, b, b3, th2, D0, Q0, omega, omw, c, theta;
+  int relax;
+};
+
+Coef32 coef32_of(const Coef& k) {
+  Coef32 f;
+  f.cmu = (float)k.cmu;
+  f.a = (float)k.a;
+  f.ih2 = (float)k.ih2;
+  f.b = (float)k.b;
+  f.b3 = (float)k.b3;
+  f.th2 = (float)k.th2;
+  f.D0 = (float)(1.0 + k.a * k.b * k.b3);   // determinant without q (q includes gam here)
+  f.Q0 = (float)(k.b * k.b3);
+  f.omega = (float)k.omega;
+  f.omw = (float)(1.0 - k.omega);
+  f.c = (float)k.c;
+  f.theta = (float)k.theta;
+  f.relax = k.relax;
+  return f;
+}
+
+const dim3 kBlk(32, 8);
+dim3 grid_of(int X, int Y) { return dim3((X + kBlk.x - 1) / kBlk.x, (Y + kBlk.y - 1) / kBlk.y); }
+
+// ---------------------------------------------------------------------------
+// FP64 defect: r = S - N(u) and q = gam + g'(phi) as FP32 inputs of the inner solve,
+// e = 0, and the scaled residual norm with the outer loop decision.
+// ---------------------------------------------------------------------------
+template <int SCH>
+__global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl, double* partials, int mode,
+                                                cudaGraphConditionalHandle hnd, int set_cond) {
+  double v[1] = {0.0};
+  int G = L.m * L.n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+    int i = t % L.m, j = t / L.m;
+    double a, b, c;
+    resid_at<SCH>(L, k, i, j, a, b, c);
+    v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));
+    double p = L.phi[t];
+    double pk = (SCH == 2) ? L.pk[t] : 0.0;
+    E.r1[t] = (float)a;
+    E.r2[t] = (float)b;
+    E.r3[t] = (float)c;
+    E.q[t] = (float)(k.gam + dg_of<SCH>(p, pk));
+    E.ephi[t] = 0.f;
+    E.emu[t] = 0.f;
+    E.eka[t] = 0.f;
+  }
+  if (!grid_sum<1>(v, partials, &ctl->counter)) return;
+  double res = sqrt(v[0] / (3.0 * (double)G));
+  int cond;
+  if (mode == 0) {
+    ctl->res0 = res;
+    ctl->res = res;
+    ctl->cycles = 0;
+    ctl->status = 0;
+    if (!(res == res)) ctl->status = 2;
+  } else {
+    ctl->res = res;
+    ctl->cycles += 1;
+    if (!(res == res) || isinf(res) || res > 1e10 * fmax(ctl->res0, ctl->tol)) ctl->status = 2;
+  }
+  if (ctl->skip || ctl->status != 0) cond = 0;
+  else if (ctl->fixed_cycles > 0) cond = ctl->cycles < ctl->fixed_cycles;
+  else cond = (res > ctl->tol) && (ctl->cycles < ctl->max_cycles);
+  if (set_cond) cudaGraphSetConditional(hnd, cond ? 1u : 0u);
+}
+
+// u += e (FP64 update with the FP32 correction)
+__global__ void k_update(Lev L, Lev32 E) {
+  int G = L.m * L.n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+    L.phi[t] += (double)E.ephi[t];
+    L.mu[t] += (double)E.emu[t];
+    L.ka[t] += (double)E.eka[t];
+  }
+}
+
+__global__ void k_restrict_q(const float* __restrict__ qf, float* __restrict__ qc, int mc, int nc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= mc || J >= nc) return;
+  int mf = 2 * mc;
+  size_t a = (size_t)(2 * J) * mf + 2 * I, b = a + mf;
+  qc[(size_t)J * mc + I] = 0.25f * ((qf[a] + qf[a + 1]) + (qf[b] + qf[b + 1]));
+}
+
+// ---------------------------------------------------------------------------
+// FP32 red-black half sweep of the correction equation (App. B cell system with
+// the frozen linearisation q = gam + g'(phi)).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_smooth32(Lev32 L, Coef32 k, int color) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int m = L.m;
+  if (x >= (m >> 1) || j >= L.n) return;
+  int i = 2 * x + ((j + color) & 1);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  size_t c = (size_t)j * m + i;
+  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
+  float* __restrict__ ep = L.ephi;
+  float* __restrict__ em = L.emu;
+  float* __restrict__ ek = L.eka;
+  float smu = (__ldg(em + w) + __ldg(em + e)) + (__ldg(em + s) + __ldg(em + nn));
+  float ska = (__ldg(ek + w) + __ldg(ek + e)) + (__ldg(ek + s) + __ldg(ek + nn));
+  float sph = (__ldg(ep + w) + __ldg(ep + e)) + (__ldg(ep + s) + __ldg(ep + nn));
+  float q = __ldg(L.q + c);
+  float R1 = fmaf(k.cmu, smu, __ldg(L.r1 + c));
+  float R2 = fmaf(k.ih2, ska, __ldg(L.r2 + c));
+  float R3 = fmaf(k.th2, sph, __ldg(L.r3 + c));
+  float rdet = __frcp_rn(fmaf(k.a, q, k.D0));
+  float nphi = fmaf(k.a, fmaf(k.b, R3, -R2), R1);
+  float nmu = fmaf(k.Q0 + q, R1, fmaf(-k.b, R3, R2));
+  if (k.relax) {
+    float wr = k.omega * rdet;
+    float wphi = nphi * wr;
+    float p0 = ep[c], m0 = em[c], k0 = ek[c];
+    ep[c] = fmaf(k.omw, p0, wphi);
+    em[c] = fmaf(k.omw, m0, nmu * wr);
+    ek[c] = fmaf(-k.b3, wphi, fmaf(k.omega, R3, k.omw * k0));
+  } else {
+    float phin = nphi * rdet;
+    ep[c] = phin;
+    em[c] = nmu * rdet;
+    ek[c] = fmaf(-k.b3, phin, R3);
+  }
+}
+
+// defect of the correction equation at one cell: rho = r - J e
+__device__ __forceinline__ void defect32(const Lev32& L, const Coef32& k, int i, int j, float& d1, float& d2,
+                                         float& d3) {
+  int m = L.m;
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  size_t c = (size_t)j * m + i;
+  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
+  const float* ep = L.ephi;
+  const float* em = L.emu;
+  const float* ek = L.eka;
+  float p = __ldg(ep + c), u = __ldg(em + c), v = __ldg(ek + c);
+  float smu = (__ldg(em + w) + __ldg(em + e)) + (__ldg(em + s) + __ldg(em + nn));
+  float ska = (__ldg(ek + w) + __ldg(ek + e)) + (__ldg(ek + s) + __ldg(ek + nn));
+  float sph = (__ldg(ep + w) + __ldg(ep + e)) + (__ldg(ep + s) + __ldg(ep + nn));
+  d1 = fmaf(k.cmu, fmaf(-4.f, u, smu), __ldg(L.r1 + c) - p);
+  d2 = fmaf(k.ih2, fmaf(-4.f, v, ska), fmaf(__ldg(L.q + c), p, __ldg(L.r2 + c) - u));
+  d3 = fmaf(k.th2, fmaf(-4.f, p, sph), __ldg(L.r3 + c) - v);
+}
+
+// coarse source = R(r - J e), coarse correction starts at zero
+__global__ void k_restrict_defect32(Lev32 F, Lev32 C, Coef32 kf) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.m || J >= C.n) return;
+  float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+  for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+    for (int di = 0; di < 2; ++di) {
+      float a, b, c;
+      defect32(F, kf, 2 * I + di, 2 * J + dj, a, b, c);
+      s1 += a;
+      s2 += b;
+      s3 += c;
+    }
+  size_t cid = (size_t)J * C.m + I;
+  C.r1[cid] = 0.25f * s1;
+  C.r2[cid] = 0.25f * s2;
+  C.r3[cid] = 0.25f * s3;
+  C.ephi[cid] = 0.f;
+  C.emu[cid] = 0.f;
+  C.eka[cid] = 0.f;
+}
+
+// e_f += P e_c (bilinear, shared-memory tile of the coarse correction)
+constexpr int kTX = 32, kTY = 8;
+__device__ __forceinline__ void prolong32_plane(const float* __restrict__ ec, float* __restrict__ ef, int mc, int nc,
+                                                float (*E)[kTX + 2]) {
+  const int I0 = blockIdx.x * kTX, J0 = blockIdx.y * kTY;
+  for (int t = threadIdx.y * kTX + threadIdx.x; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
+    int ty = t / (kTX + 2), tx = t % (kTX + 2);
+    if (I0 + tx - 1 < mc + 1 && J0 + ty - 1 < nc + 1)
+      E[ty][tx] = __ldg(ec + (size_t)wrapm(J0 + ty - 1, nc) * mc + wrapm(I0 + tx - 1, mc));
+  }
+  __syncthreads();
+  int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  if (I < mc && J < nc) {
+    int x = threadIdx.x + 1, y = threadIdx.y + 1;
+    const float w9 = 9.f / 16.f, w3 = 3.f / 16.f, w1 = 1.f / 16.f;
+    float c9 = w9 * E[y][x];
+    int mf = 2 * mc;
+    size_t f00 = (size_t)(2 * J) * mf + 2 * I, f01 = f00 + mf;
+    ef[f00] += fmaf(w3, E[y][x - 1] + E[y - 1][x], fmaf(w1, E[y - 1][x - 1], c9));
+    ef[f00 + 1] += fmaf(w3, E[y][x + 1] + E[y - 1][x], fmaf(w1, E[y - 1][x + 1], c9));
+    ef[f01] += fmaf(w3, E[y][x - 1] + E[y + 1][x], fmaf(w1, E[y + 1][x - 1], c9));
+    ef[f01 + 1] += fmaf(w3, E[y][x + 1] + E[y + 1][x], fmaf(w1, E[y + 1][x + 1], c9));
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTX * kTY) k_prolong32(Lev32 F, Lev32 C) {
+  __shared__ float E[kTY + 2][kTX + 2];
+  prolong32_plane(C.ephi, F.ephi, C.m, C.n, E);
+  prolong32_plane(C.emu, F.emu, C.m, C.n, E);
+  prolong32_plane(C.eka, F.eka, C.m, C.n, E);
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest grid, FP32: eliminate e_kappa and e_mu,
+//   (I - c L diag(q) - c theta L^3) e_phi = r1 + c L (r2 + L r3),
+// solve by Gaussian elimination with partial pivoting in one CTA, then
+// e_kappa = r3 + theta L e_phi, e_mu = r2 + q e_phi + L e_kappa.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float nbsum32(const float* f, int m, int n, int t) {
+  int i = t % m, j = t / m;
+  return (f[j * m + wrapm(i - 1, m)] + f[j * m + wrapm(i + 1, m)]) +
+         (f[wrapm(j - 1, n) * m + i] + f[wrapm(j + 1, n) * m + i]);
+}
+
+__global__ void k_coarse32(Lev32 C, Coef32 k, const float* __restrict__ K3f) {
+  extern __shared__ float smf[];
+  const int m = C.m, n = C.n, G = m * n, W = G + 1;
+  float* A = smf;
+  float* t1 = A + G * W;
+  float* t2 = t1 + G;
+  float* x = t2 + G;
+  float* d = x + G;
+  __shared__ int s_piv;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // t1 = L r3 (with the 1/h^2 of L), t2 = r2 + t1
+  for (int t = tid; t < G; t += nt) t1[t] = k.ih2 * (nbsum32(C.r3, m, n, t) - 4.f * C.r3[t]);
+  __syncthreads();
+  for (int t = tid; t < G; t += nt) t2[t] = C.r2[t] + t1[t];
+  __syncthreads();
+  for (int t = tid; t < G; t += nt) A[t * W + G] = C.r1[t] + k.cmu * (nbsum32(t2, m, n, t) - 4.f * t2[t]);
+  for (int idx = tid; idx < G * G; idx += nt) {
+    int r = idx / G, col = idx % G;
+    int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
+    int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
+              (ci == ri && cj == wrapm(rj - 1, n)) + (ci == ri && cj == wrapm(rj + 1, n));
+    float Lrc = k.ih2 * ((float)cnt - (r == col ? 4.f : 0.f));
+    A[r * W + col] = K3f[idx] - k.c * Lrc * C.q[col];
+  }
+  __syncthreads();
+  for (int col = 0; col < G; ++col) {
+    if (tid == 0) {
+      int piv = col;
+      float best = fabsf(A[col * W + col]);
+      for (int r = col + 1; r < G; ++r) {
+        float v = fabsf(A[r * W + col]);
+        if (v > best) { best = v; piv = r; }
+      }
+      s_piv = piv;
+    }
+    __syncthreads();
+    int piv = s_piv;
+    if (piv != col)
+      for (int c2 = col + tid; c2 <= G; c2 += nt) {
+        float t = A[col * W + c2];
+        A[col * W + c2] = A[piv * W + c2];
+        A[piv * W + c2] = t;
+      }
+    __syncthreads();
+    for (int r = col + 1 + tid; r < G; r += nt) d[r] = A[r * W + col] / A[col * W + col];
+    __syncthreads();
+    int rows = G - col - 1, cols = G - col;
+    for (int idx = tid; idx < rows * cols; idx += nt) {
+      int r = col + 1 + idx / cols, c2 = col + 1 + idx % cols;
+      A[r * W + c2] -= d[r] * A[col * W + c2];
+    }
+    __syncthreads();
+  }
+  if (tid == 0)
+    for (int r = G - 1; r >= 0; --r) {
+      float acc = A[r * W + G];
+      for (int c2 = r + 1; c2 < G; ++c2) acc -= A[r * W + c2] * x[c2];
+      x[r] = acc / A[r * W + r];
+    }
+  __syncthreads();
+  for (int t = tid; t < G; t += nt) t1[t] = C.r3[t] + k.th2 * (nbsum32(x, m, n, t) - 4.f * x[t]);   // e_kappa
+  __syncthreads();
+  for (int t = tid; t < G; t += nt) {
+    C.emu[t] = C.r2[t] + C.q[t] * x[t] + k.ih2 * (nbsum32(t1, m, n, t) - 4.f * t1[t]);
+    C.ephi[t] = x[t];
+    C.eka[t] = t1[t];
+  }
+}
+
+__global__ void k_k3_to_float(const double* __restrict__ a, float* __restrict__ b, int count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) b[i] = (float)a[i];
+}
+
+size_t coarse32_smem(const Lev32& C) {
+  int G = C.m * C.n;
+  return sizeof(float) * ((size_t)G * (G + 1) + 4 * (size_t)G);
+}
+
+int inner_cycles_of(const mpfc_s* H) { return H->p.inner_cycles > 0 ? H->p.inner_cycles : 2; }
+
+// One inner correction-scheme V-cycle.
+void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
+  const mpfc_params& p = H->p;
+  int L = H->nlev;
+  for (int l = 0; l < L - 1; ++l) {
+    const Lev32& F = H->lev32[l];
+    const Lev32& C = H->lev32[l + 1];
+    Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
+    dim3 g = grid_of(F.m / 2, F.n);
+    for (int sw = 0; sw < p.nu1; ++sw) {
+      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 0);
+      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 1);
+    }
+    k_restrict_defect32<<<grid_of(C.m, C.n), kBlk, 0, s>>>(F, C, kf);
+  }
+  const Lev32& Cc = H->lev32[L - 1];
+  k_coarse32<<<1, 256, coarse32_smem(Cc), s>>>(Cc, coef32_of(H->coef[scheme - 1][L - 1]), H->K3f[scheme - 1]);
+  for (int l = L - 2; l >= 0; --l) {
+    const Lev32& F = H->lev32[l];
+    const Lev32& C = H->lev32[l + 1];
+    Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
+    k_prolong32<<<grid_of(C.m, C.n), kBlk, 0, s>>>(F, C);
+    dim3 g = grid_of(F.m / 2, F.n);
+    for (int sw = 0; sw < p.nu2; ++sw) {
+      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 0);
+      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 1);
+    }
+  }
+}
+
+void enqueue_defect(mpfc_s* H, int scheme, int mode, cudaGraphConditionalHandle hnd, int set_cond, cudaStream_t s) {
+  const Lev& L0 = H->lev[0];
+  int blocks = mpfc_reduce_blocks((size_t)L0.m * L0.n);
+  if (scheme == 1)
+    k_defect<1><<<blocks, 256, 0, s>>>(L0, H->coef[0][0], H->lev32[0], H->ctl, H->partials, mode, hnd, set_cond);
+  else
+    k_defect<2><<<blocks, 256, 0, s>>>(L0, H->coef[1][0], H->lev32[0], H->ctl, H->partials, mode, hnd, set_cond);
+}
+
+// Body of one outer iteration: restrict q to the coarse grids, the inner V-cycles,
+// u += e, and the FP64 defect with the loop test.
+void outer_body(mpfc_s* H, int scheme, cudaStream_t s, cudaGraphConditionalHandle hnd, int set_cond) {
+  for (int l = 1; l < H->nlev; ++l) {
+    const Lev32& C = H->lev32[l];
+    k_restrict_q<<<grid_of(C.m, C.n), kBlk, 0, s>>>(H->lev32[l - 1].q, C.q, C.m, C.n);
+  }
+  for (int c = 0; c < inner_cycles_of(H); ++c) enqueue_inner_vcycle(H, scheme, s);
+  const Lev& L0 = H->lev[0];
+  k_update<<<mpfc_reduce_blocks((size_t)L0.m * L0.n), 256, 0, s>>>(L0, H->lev32[0]);
+  enqueue_defect(H, scheme, 1, hnd, set_cond, s);
+}
+
+void graph_body(mpfc_s* H, int scheme, cudaStream_t s) { outer_body(H, scheme, s, H->cur_handle, 1); }
+
+}  // namespace
+
 size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base, int nlev) {
-  (void)H; (void)p; (void)off; (void)base; (void)nlev;
-  return 0;
+  if (p->precision != MPFC_FP32_INNER) return 0;
+  size_t start = *off;
+  auto take = [&](size_t count) -> float* {
+    float* ptr = base ? reinterpret_cast<float*>(base + *off) : nullptr;
+    *off = (*off + count * sizeof(float) + 255) & ~(size_t)255;
+    return ptr;
+  };
+  int m = p->m, n = p->n;
+  double h = p->h;
+  for (int l = 0; l < nlev; ++l) {
+    size_t G = (size_t)m * n;
+    Lev32 v;
+    v.m = m;
+    v.n = n;
+    v.h = (float)h;
+    v.ephi = take(G);
+    v.emu = take(G);
+    v.eka = take(G);
+    v.r1 = take(G);
+    v.r2 = take(G);
+    v.r3 = take(G);
+    v.q = take(G);
+    v.b1 = v.b2 = v.b3 = nullptr;
+    if (H && base) H->lev32[l] = v;
+    m /= 2;
+    n /= 2;
+    h *= 2.0;
+  }
+  int mc = p->m >> (nlev - 1), nc = p->n >> (nlev - 1);
+  size_t Gc = (size_t)mc * nc;
+  float* k3a = take(Gc * Gc);
+  float* k3b = take(Gc * Gc);
+  if (H && base) {
+    H->K3f[0] = k3a;
+    H->K3f[1] = k3b;
+  }
+  return *off - start;
 }
-int mpfc_fp32_init(mpfc_s* H) { (void)H; return MPFC_OK; }
+
+int mpfc_fp32_init(mpfc_s* H) {
+  if (H->p.precision != MPFC_FP32_INNER) return MPFC_OK;
+  const Lev& C = H->lev[H->nlev - 1];
+  int count = C.m * C.n * C.m * C.n;
+  for (int s = 0; s < 2; ++s) k_k3_to_float<<<(count + 255) / 256, 256, 0, H->stream>>>(H->K3[s], H->K3f[s], count);
+  cudaError_t e = cudaStreamSynchronize(H->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "fp32 init", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
+  return MPFC_OK;
+}
+
 void mpfc_fp32_destroy(mpfc_s* H) { (void)H; }
+
+// Step graph of the mixed-precision form: prologue (FP64 source and guess), FP64
+// defect (sets the loop condition), WHILE(cond){ outer body }, psi update.
 int mpfc_fp32_enqueue_step(mpfc_s* H, int scheme, cudaStream_t cs, cudaGraphConditionalHandle hnd) {
-  (void)H; (void)scheme; (void)cs; (void)hnd;
-  return MPFC_ERR_INVALID;
+  mpfc_enqueue_prologue(H, scheme, cs);
+  enqueue_defect(H, scheme, 0, hnd, 1, cs);
+  int rc = mpfc_capture_while(H, cs, hnd, &graph_body, scheme);
+  if (rc != MPFC_OK) return rc;
+  mpfc_enqueue_commit(H, scheme, cs);
+  return MPFC_OK;
 }
+
 int mpfc_fp32_step_stream(mpfc_s* H, int scheme) {
-  (void)H; (void)scheme;
-  return MPFC_ERR_INVALID;
+  cudaStream_t s = H->stream;
+  mpfc_enqueue_prologue(H, scheme, s);
+  enqueue_defect(H, scheme, 0, 0, 0, s);
+  for (;;) {
+    Ctl c;
+    cudaError_t e = cudaMemcpyAsync(&c, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      mpfc_set_cuda_error(e, "fp32 loop test", __FILE__, __LINE__);
+      return MPFC_ERR_CUDA;
+    }
+    if (!mpfc_host_continue(&c)) break;
+    outer_body(H, scheme, s, 0, 0);
+  }
+  mpfc_enqueue_commit(H, scheme, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "fp32 step", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
+  return MPFC_OK;
 }

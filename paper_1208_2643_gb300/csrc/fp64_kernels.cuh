@@ -10,6 +10,7 @@
 #include "mpfc_common.cuh"
 
 namespace mpfc {
+// Non-template kernels are static: several translation units include this header.
 
 // ---------------------------------------------------------------------------
 // Source S and initial guess (App. B.1 / B.2; guess: extrapolation of phi, then
@@ -58,7 +59,7 @@ __global__ void k_source_guess(Lev L, SourceArgs A) {
 }
 
 // kappa0 = S3 + theta Delta_h phi0
-__global__ void k_guess_kappa(Lev L, Coef k) {
+static __global__ void k_guess_kappa(Lev L, Coef k) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.m || j >= L.n) return;
@@ -255,7 +256,7 @@ __global__ void k_tau(Lev C, Coef k) {
 }
 
 // Plain 2x2 average of one plane (phi^k onto the coarse levels, scheme 2).
-__global__ void k_restrict_plane(const double* __restrict__ f, double* __restrict__ c, int mc, int nc) {
+static __global__ void k_restrict_plane(const double* __restrict__ f, double* __restrict__ c, int mc, int nc) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mc || J >= nc) return;
@@ -310,7 +311,7 @@ __device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, con
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
+static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
   __shared__ double E[kPTY + 2][kPTX + 2];
   prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, E);
   prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, E);
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double
 // ---------------------------------------------------------------------------
 // Step bookkeeping and the psi update.
 // ---------------------------------------------------------------------------
-__global__ void k_step_begin(Ctl* ctl) {
+static __global__ void k_step_begin(Ctl* ctl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl->skip = ctl->halt;
     ctl->cycles = 0;
@@ -531,7 +532,7 @@ __global__ void k_step_begin(Ctl* ctl) {
   }
 }
 
-__global__ void k_ctl_reset(Ctl* ctl, int fixed_cycles) {
+static __global__ void k_ctl_reset(Ctl* ctl, int fixed_cycles) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl->halt = 0;
     ctl->slot = 0;
@@ -578,7 +579,7 @@ __global__ void k_commit(const double* __restrict__ phinew, double* phik, double
 // ---------------------------------------------------------------------------
 // Diagnostics: mass and energy sums, periodic Poisson multigrid for the -1 norm.
 // ---------------------------------------------------------------------------
-__global__ void k_sum1(const double* __restrict__ f, int G, Ctl* ctl, double* partials) {
+static __global__ void k_sum1(const double* __restrict__ f, int G, Ctl* ctl, double* partials) {
   double v[1] = {0.0};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) v[0] += f[t];
   if (grid_sum<1>(v, partials, &ctl->counter)) ctl->sums[0] = v[0];
@@ -586,7 +587,7 @@ __global__ void k_sum1(const double* __restrict__ f, int G, Ctl* ctl, double* pa
 
 // sums: 0 phi^4, 1 phi^2, 2 |grad phi|^2 (edge differences), 3 (Delta_h phi)^2 h^4,
 // 4 psi * xi, 5 |grad (phi - phi_prev)|^2
-__global__ void k_energy_sums(const double* __restrict__ phi, const double* __restrict__ phip,
+static __global__ void k_energy_sums(const double* __restrict__ phi, const double* __restrict__ phip,
                               const double* __restrict__ psi, const double* __restrict__ xi, int m, int n, Ctl* ctl,
                               double* partials) {
   double v[6] = {0, 0, 0, 0, 0, 0};
@@ -613,13 +614,13 @@ __global__ void k_energy_sums(const double* __restrict__ phi, const double* __re
 }
 
 // x = f - mean: the right-hand side of the mean-zero Poisson problem
-__global__ void k_sub_mean(const double* __restrict__ f, double* __restrict__ out, int G, const Ctl* ctl) {
+static __global__ void k_sub_mean(const double* __restrict__ f, double* __restrict__ out, int G, const Ctl* ctl) {
   double mean = ctl->sums[0] / (double)G;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) out[t] = f[t] - mean;
 }
 
 // Red-black Gauss-Seidel half sweep for -Delta_h x = f (periodic).
-__global__ void k_pois_smooth(double* __restrict__ x, const double* __restrict__ f, int m, int n, double h2,
+static __global__ void k_pois_smooth(double* __restrict__ x, const double* __restrict__ f, int m, int n, double h2,
                               int color) {
   int xi = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -631,7 +632,7 @@ __global__ void k_pois_smooth(double* __restrict__ x, const double* __restrict__
 }
 
 // coarse f = R (f + Delta_h x), coarse x = 0; also the sum of squared fine residuals
-__global__ void k_pois_restrict(const double* __restrict__ x, const double* __restrict__ f, double* __restrict__ fc,
+static __global__ void k_pois_restrict(const double* __restrict__ x, const double* __restrict__ f, double* __restrict__ fc,
                                 double* __restrict__ xc, int mc, int nc, double ih2) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
@@ -649,7 +650,7 @@ __global__ void k_pois_restrict(const double* __restrict__ x, const double* __re
   xc[J * mc + I] = 0.0;
 }
 
-__global__ void k_pois_prolong(const double* __restrict__ xc, double* __restrict__ x, int mc, int nc) {
+static __global__ void k_pois_prolong(const double* __restrict__ xc, double* __restrict__ x, int mc, int nc) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mc || J >= nc) return;
@@ -667,7 +668,7 @@ __global__ void k_pois_prolong(const double* __restrict__ xc, double* __restrict
 }
 
 // Coarsest Poisson level: `sweeps` red-black sweeps in one CTA, then the mean removed.
-__global__ void k_pois_coarse(double* x, const double* f, int m, int n, double h2, int sweeps) {
+static __global__ void k_pois_coarse(double* x, const double* f, int m, int n, double h2, int sweeps) {
   extern __shared__ double xs[];
   int G = m * n;
   for (int t = threadIdx.x; t < G; t += blockDim.x) xs[t] = x[t];
@@ -691,7 +692,7 @@ __global__ void k_pois_coarse(double* x, const double* f, int m, int n, double h
 }
 
 // sum of squared residuals of -Delta_h x = f, and sum of f^2
-__global__ void k_pois_resnorm(const double* __restrict__ x, const double* __restrict__ f, int m, int n, double ih2,
+static __global__ void k_pois_resnorm(const double* __restrict__ x, const double* __restrict__ f, int m, int n, double ih2,
                                Ctl* ctl, double* partials) {
   double v[2] = {0.0, 0.0};
   int G = m * n;

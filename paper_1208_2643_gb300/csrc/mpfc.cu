@@ -78,6 +78,7 @@ static bool params_valid(const mpfc_params* p) {
   if (!(p->tol >= 0) || p->max_cycles < 1) return false;
   if (p->precision != MPFC_FP64 && p->precision != MPFC_FP32_INNER) return false;
   if (p->guess < MPFC_GUESS_PREV || p->guess > MPFC_GUESS_LEARNED) return false;
+  if (p->inner_cycles < 0 || p->inner_cycles > 64) return false;
   int L = mpfc_num_levels(p->m, p->n, p->coarsest);
   int mc = p->m >> (L - 1), nc = p->n >> (L - 1);
   if (mc * nc > kMaxCoarseCells) return false;

@@ -37,7 +37,7 @@ class mpfc_params(ctypes.Structure):
                 ("epsilon", ctypes.c_double), ("beta", ctypes.c_double), ("dt", ctypes.c_double),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
-                ("precision", ctypes.c_int), ("guess", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("guess", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
 
 
 class mpfc_step_info(ctypes.Structure):

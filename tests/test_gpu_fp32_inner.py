@@ -1,0 +1,72 @@
+"""The mixed-precision form (FP64 outer defect correction around FP32 inner V-cycles).
+
+It is a different iteration from the FP64 V-cycle, so it is not compared in lockstep:
+each step must reach the same FP64 scaled-residual tolerance, and its phi must stay
+within a stated bound of the FP64 oracle's solution of the same step (solved to
+1e-13): relative max-norm error <= 1e-8 per step.
+"""
+import numpy as np
+import pytest
+
+from paper_1208_2643_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+BOUND = 1e-8
+
+
+@pytest.fixture(scope="module")
+def mp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_2643_gb300 import mpfc
+    mpfc.load()
+    return mpfc
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("scheme,m,n,h,s,steps", [(1, 64, 64, 0.5, 0.01, 10), (2, 96, 160, 0.5, 0.05, 6),
+                                                  (1, 128, 128, 0.5, 0.02, 6), (2, 64, 64, 1.0, 1.0, 4)])
+def test_fp32_inner_matches_fp64_oracle(mp, oracle_mod, scheme, m, n, h, s, steps):
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 1)
+    g = mp.Solver(mp.default_params(m=m, n=n, h=h, dt=s, precision=mp.MPFC_FP32_INNER))
+    g.set_state(phi0)
+    o = oracle_mod.Solver(oracle_mod.Params(m=m, n=n, h=h, s=s))
+    o.set_state(phi0)
+    worst = 0.0
+    for k in range(steps):
+        info = g.step(scheme, 1)[0]
+        assert info["status"] == 0 and info["res"] <= 1e-10
+        r = o.step(scheme, tol=1e-13, guess=1)
+        assert r["status"] == 0
+        # the oracle continues from its own (tighter) state; compare this step's phi
+        e = relerr(g.get_state()[0], o.get_state()[0])
+        worst = max(worst, e)
+        assert e <= BOUND, (k, e)
+
+
+def test_fp32_inner_stream_mode_matches_graph(mp):
+    m = 64
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    out = []
+    for mode in (mp.MPFC_LAUNCH_GRAPH, mp.MPFC_LAUNCH_STREAM):
+        g = mp.Solver(mp.default_params(m=m, n=m, precision=mp.MPFC_FP32_INNER))
+        g.set_launch_mode(mode)
+        g.set_state(phi0)
+        infos = g.step(1, 3)
+        out.append((g.get_state()[0], [i["cycles"] for i in infos]))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_fp32_inner_mass_conservation(mp):
+    m = 128
+    g = mp.Solver(mp.default_params(m=m, n=m, precision=mp.MPFC_FP32_INNER))
+    g.set_state(inputs.noise_field(m, m, 0.07, 0.05, 2))
+    m0 = g.mass()
+    g.step(1, 20)
+    assert abs(g.mass() - m0) < 1e-8 * abs(m0)
