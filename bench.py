@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--scheme", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--profile", action="store_true", help="steps only, no flush and no extras (ncu launch list)")
     ap.add_argument("--profile-smooth", action="store_true",
                     help="only the finest-level sweep kernel, two sweeps (ncu capture of the top kernel)")
@@ -348,6 +349,55 @@ def run_ours(args):
                            "speedup_vs_fp64": (world * K / (ms32 * 1e-3)) / steps_per_s}
     for obj in (s32, a64, a32):
         obj.close()
+
+    # batched ensemble: 64 instances, sizes uniform from {128, 256, 512, 1024}^2, eps ~ U[0.02, 0.1],
+    # beta ~ U[0.5, 1.5], mean density ~ U[0.05, 0.1], h = 0.5, s = 0.01, noise 0.05 U (seed 4)
+    if not args.no_batch:
+        from paper_1208_2643_gb300 import tuning
+        rng = np.random.default_rng(4)
+        bs = rng.choice([128, 256, 512, 1024], size=64)
+        bps = [mpfc.default_params(m=int(m), n=int(m), h=0.5, dt=0.01, epsilon=float(rng.uniform(0.02, 0.1)),
+                                   beta=float(rng.uniform(0.5, 1.5)), tol=w["tol"], omega=w["omega"])
+               for m in bs]
+        bbar = rng.uniform(0.05, 0.1, size=64)
+        b = mpfc.BatchSolver(bps, stream=stream)
+        for i, bp in enumerate(bps):
+            b.set_state(i, inputs.noise_field(bp.m, bp.n, float(bbar[i]), 0.05, 100 + i + 1000 * rank))
+        tiles = tuning.autotune(b, scheme, reps=3)
+        b.step(scheme, 2)
+        Kb = max(2, K // 10)
+        eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(3.0)
+        eb0.record(stream)
+        rcb, stb, cyb = b.step(scheme, Kb)
+        eb1.record(stream)
+        torch.cuda.synchronize()
+        msb = eb0.elapsed_time(eb1)
+        cells_b = sum(bp.m * bp.n for bp in bps)
+        # the same instances one by one through the single-instance solver, same protocol
+        seq_ms = 0.0
+        for i, bp in enumerate(bps[:16]):
+            g1 = mpfc.Solver(bp, stream=stream)
+            g1.set_state(inputs.noise_field(bp.m, bp.n, float(bbar[i]), 0.05, 100 + i + 1000 * rank))
+            g1.step(scheme, 2)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            g1.step(scheme, Kb)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            seq_ms += ea.elapsed_time(eb)
+            g1.close()
+        seq_cells = sum(bp.m * bp.n for bp in bps[:16])
+        forms["batched"] = {"workload": "64 instances, sizes U{128,256,512,1024}^2, eps U[0.02,0.1], "
+                                        "beta U[0.5,1.5], mean U[0.05,0.1], h 0.5, s 0.01, fp64, tol 1e-10",
+                            "instance_steps_per_s": world * 64 * Kb / (msb * 1e-3),
+                            "cell_updates_per_s": world * cells_b * Kb / (msb * 1e-3),
+                            "vcycles_per_instance_step": float(np.mean(cyb)) / Kb,
+                            "sequential_cell_updates_per_s": seq_cells * Kb / (seq_ms * 1e-3),
+                            "speedup_vs_sequential": (cells_b * Kb / (msb * 1e-3)) / (seq_cells * Kb / (seq_ms * 1e-3)),
+                            "tiles": {str(k): v[:2] for k, v in tiles.items()},
+                            "steps": Kb}
+        b.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

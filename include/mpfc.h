@@ -162,6 +162,48 @@ int mpfc_energy(mpfc_t* h, mpfc_energy_t* out);
  * Synchronises `cuda_stream` (a cudaStream_t; NULL = legacy stream). */
 int mpfc_mass_noalloc(const double* d_phi, int m, int n, double h, void* cuda_stream, double* out);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: `count` independent instances, each with its own grid size and
+ * physical parameters (m, n, h, M, epsilon, beta, dt), advanced together.  The solver
+ * settings (nu1, nu2, coarsest, omega, tol, max_cycles, guess) must agree, the
+ * precision must be MPFC_FP64 and the guess not learned.  Every V-cycle kernel runs
+ * as one persistent launch per level over a work list of (instance, tile) items;
+ * instances are aligned at their coarsest grids; each instance has its own residual
+ * test and drops out of the work once converged; a step is one CUDA graph that loops
+ * while any instance is active.  One caller-owned workspace, as for mpfc_create.
+ * ------------------------------------------------------------------------- */
+typedef struct mpfc_batch_s mpfc_batch_t;
+
+/* Workspace bytes for the batch (0 if any instance is invalid or the settings differ). */
+size_t mpfc_batch_workspace_bytes(int count, const mpfc_params* each);
+
+int mpfc_batch_create(int count, const mpfc_params* each, void* d_workspace, size_t bytes, void* cuda_stream,
+                      mpfc_batch_t** out);
+void mpfc_batch_destroy(mpfc_batch_t* b);
+
+/* State of instance `inst` (copies; host or device pointers; NULL as in mpfc_set_state). */
+int mpfc_batch_set_state(mpfc_batch_t* b, int inst, const double* phi, const double* phi_prev, const double* psi);
+int mpfc_batch_get_state(mpfc_batch_t* b, int inst, double* phi, double* phi_prev, double* psi);
+
+/* Advances every instance nsteps steps of scheme 1 or 2.  An instance whose step fails
+ * keeps its last good state and sits out the rest of the call; statuses[i] (nullable)
+ * gets its first failing status (MPFC_OK if none), cycles[i] (nullable) its V-cycles
+ * over the call.  Returns the first failing status of any instance.  Synchronises. */
+int mpfc_batch_step(mpfc_batch_t* b, int scheme, int nsteps, int* statuses, int* cycles);
+
+/* One step with exactly ncycles V-cycles for every instance (lockstep tests). */
+int mpfc_batch_step_cycles(mpfc_batch_t* b, int scheme, int ncycles, int* statuses);
+
+/* Number of aligned levels (the largest instance's hierarchy). */
+int mpfc_batch_levels(const mpfc_batch_t* b);
+
+/* Tile shape (threads, tx * ty a multiple of 32 in [64, 1024]) of the smoother's
+ * work items on aligned level `level`; rebuilds the work lists.  Used by the tile
+ * autotuner, which times candidates with mpfc_batch_time_smooth (milliseconds per full
+ * red-black sweep of that level, all instances, averaged over `reps`). */
+int mpfc_batch_set_tile(mpfc_batch_t* b, int level, int tx, int ty);
+int mpfc_batch_time_smooth(mpfc_batch_t* b, int scheme, int level, int reps, float* ms);
+
 /* Message for a status code. */
 const char* mpfc_strerror(int status);
 

@@ -26,10 +26,7 @@ struct SourceArgs {
 };
 
 template <int SCH>
-__global__ void k_source_guess(Lev L, SourceArgs A) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= L.m || j >= L.n) return;
+__device__ __forceinline__ void source_cell(const Lev& L, const SourceArgs& A, int i, int j) {
   int m = L.m;
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
   size_t c = (size_t)j * m + i;
@@ -58,11 +55,16 @@ __global__ void k_source_guess(Lev L, SourceArgs A) {
   else if (A.guess == 1) L.phi[c] = 2.0 * p0 - q0;
 }
 
-// kappa0 = S3 + theta Delta_h phi0
-static __global__ void k_guess_kappa(Lev L, Coef k) {
+template <int SCH>
+__global__ void k_source_guess(Lev L, SourceArgs A) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.m || j >= L.n) return;
+  source_cell<SCH>(L, A, i, j);
+}
+
+// kappa0 = S3 + theta Delta_h phi0
+__device__ __forceinline__ void guess_kappa_cell(const Lev& L, const Coef& k, int i, int j) {
   int m = L.m;
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
   size_t c = (size_t)j * m + i;
@@ -71,12 +73,16 @@ static __global__ void k_guess_kappa(Lev L, Coef k) {
   L.ka[c] = L.S3[c] + k.th2 * (sum - 4.0 * f[c]);
 }
 
-// mu0 = S2 + g(phi0) + gam phi0 + Delta_h kappa0
-template <int SCH>
-__global__ void k_guess_mu(Lev L, Coef k) {
+static __global__ void k_guess_kappa(Lev L, Coef k) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.m || j >= L.n) return;
+  guess_kappa_cell(L, k, i, j);
+}
+
+// mu0 = S2 + g(phi0) + gam phi0 + Delta_h kappa0
+template <int SCH>
+__device__ __forceinline__ void guess_mu_cell(const Lev& L, const Coef& k, int i, int j) {
   int m = L.m;
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
   size_t c = (size_t)j * m + i;
@@ -87,6 +93,14 @@ __global__ void k_guess_mu(Lev L, Coef k) {
   L.mu[c] = L.S2[c] + g_of<SCH>(p, pk) + k.gam * p + k.ih2 * (sum - 4.0 * f[c]);
 }
 
+template <int SCH>
+__global__ void k_guess_mu(Lev L, Coef k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.m || j >= L.n) return;
+  guess_mu_cell<SCH>(L, k, i, j);
+}
+
 // ---------------------------------------------------------------------------
 // Red-black nonlinear block Gauss-Seidel half sweep (App. B.1 / B.2 smoothing
 // scheme).  Thread (x, j) visits cell i = 2x + ((j + color) & 1) of colour
@@ -94,12 +108,8 @@ __global__ void k_guess_mu(Lev L, Coef k) {
 // so a half sweep is exactly parallel.
 // ---------------------------------------------------------------------------
 template <int SCH>
-__global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, int color) {
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k, int i, int j) {
   int m = L.m;
-  if (x >= (m >> 1) || j >= L.n) return;
-  int i = 2 * x + ((j + color) & 1);
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
@@ -150,6 +160,14 @@ __global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, int color) {
   }
 }
 
+template <int SCH>
+__global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, int color) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= (L.m >> 1) || j >= L.n) return;
+  smooth_cell<SCH>(L, k, 2 * x + ((j + color) & 1), j);
+}
+
 // ---------------------------------------------------------------------------
 // Residual r = S - N(u) at one cell (App. B.1 / B.2 operator N).
 // ---------------------------------------------------------------------------
@@ -194,10 +212,8 @@ __global__ void k_residual(Lev L, Coef k, double* r1, double* r2, double* r3) {
 // fine residual.  u_c = R u (also kept in b), S_c = R r (part 2 adds N_c(u_c)).
 // ---------------------------------------------------------------------------
 template <int SCH>
-__global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I >= C.m || J >= C.n) return;
+__device__ __forceinline__ void resid_restrict_cell(const Lev& F, const Lev& C, const Coef& kf, int keep_b, int I,
+                                                    int J) {
   double sr1 = 0.0, sr2 = 0.0, sr3 = 0.0, sp = 0.0, sm = 0.0, sk = 0.0;
 #pragma unroll
   for (int dj = 0; dj < 2; ++dj)
@@ -229,12 +245,17 @@ __global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
   C.S3[cid] = 0.25 * sr3;
 }
 
+template <int SCH>
+__global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.m || J >= C.n) return;
+  resid_restrict_cell<SCH>(F, C, kf, keep_b, I, J);
+}
+
 // FAS restriction, part 2: S_c += N_c(u_c).
 template <int SCH>
-__global__ void k_tau(Lev C, Coef k) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= C.m || j >= C.n) return;
+__device__ __forceinline__ void tau_cell(const Lev& C, const Coef& k, int i, int j) {
   int m = C.m;
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, C.n), jp = wrapm(j + 1, C.n);
   size_t c = (size_t)j * m + i;
@@ -253,6 +274,14 @@ __global__ void k_tau(Lev C, Coef k) {
   C.S1[c] += N1;
   C.S2[c] += N2;
   C.S3[c] += N3;
+}
+
+template <int SCH>
+__global__ void k_tau(Lev C, Coef k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= C.m || j >= C.n) return;
+  tau_cell<SCH>(C, k, i, j);
 }
 
 // Plain 2x2 average of one plane (phi^k onto the coarse levels, scheme 2).
@@ -281,8 +310,8 @@ struct ProlongArgs {
 // is formed once, then writes the bilinear correction into its 2x2 fine children.
 constexpr int kPTX = 32, kPTY = 8;
 __device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, const double* __restrict__ co,
-                                              double* __restrict__ f, int mc, int nc, double (*E)[kPTX + 2]) {
-  const int I0 = blockIdx.x * kPTX, J0 = blockIdx.y * kPTY;
+                                              double* __restrict__ f, int mc, int nc, double (*E)[kPTX + 2], int I0,
+                                              int J0) {
   for (int t = threadIdx.y * kPTX + threadIdx.x; t < (kPTX + 2) * (kPTY + 2); t += kPTX * kPTY) {
     int ty = t / (kPTX + 2), tx = t % (kPTX + 2);
     int I = wrapm(I0 + tx - 1, mc), J = wrapm(J0 + ty - 1, nc);
@@ -311,11 +340,16 @@ __device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, con
   __syncthreads();
 }
 
+// The block's (kPTX x kPTY) coarse tile at (I0, J0): all three components.
+__device__ __forceinline__ void prolong_tile(const ProlongArgs& A, double (*E)[kPTX + 2], int I0, int J0) {
+  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, E, I0, J0);
+  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, E, I0, J0);
+  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, E, I0, J0);
+}
+
 static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
   __shared__ double E[kPTY + 2][kPTX + 2];
-  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, E);
-  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, E);
-  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, E);
+  prolong_tile(A, E, blockIdx.x * kPTX, blockIdx.y * kPTY);
 }
 
 // ---------------------------------------------------------------------------
@@ -332,7 +366,7 @@ __device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t) 
 }
 
 template <int SCH>
-__global__ void k_coarse_solve(Lev C, Coef k, const double* __restrict__ K3) {
+__device__ void coarse_solve_block(const Lev& C, const Coef& k, const double* __restrict__ K3) {
   extern __shared__ double sm[];
   const int m = C.m, n = C.n, G = m * n, W = G + 1;
   double* Jm = sm;              // G x (G+1), last column = right-hand side
@@ -427,6 +461,11 @@ __global__ void k_coarse_solve(Lev C, Coef k, const double* __restrict__ K3) {
   }
   __syncthreads();
   for (int t = tid; t < G; t += nt) C.mu[t] = muv[t];
+}
+
+template <int SCH>
+__global__ void k_coarse_solve(Lev C, Coef k, const double* __restrict__ K3) {
+  coarse_solve_block<SCH>(C, k, K3);
 }
 
 // ---------------------------------------------------------------------------

@@ -203,7 +203,7 @@ extern "C" size_t mpfc_workspace_bytes(const mpfc_params* p) {
 }
 
 // K3 = I - c theta L^3 on the coarsest grid (dense, row-major G x G).
-static void build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
+void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
   int m = C.m, n = C.n, G = m * n;
   std::vector<double> Lm((size_t)G * G, 0.0), L2((size_t)G * G, 0.0), L3((size_t)G * G, 0.0);
   double ih2 = 1.0 / (C.h * C.h);
@@ -271,7 +271,7 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
       break;
     }
     for (int s = 0; s < 2 && rc == MPFC_OK; ++s) {
-      build_K3(C, H->coef[s][H->nlev - 1], K3);
+      mpfc_build_K3(C, H->coef[s][H->nlev - 1], K3);
       if ((e = cudaMemcpyAsync(H->K3[s], K3.data(), K3.size() * sizeof(double), cudaMemcpyHostToDevice, H->stream)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(H->stream)) != cudaSuccess) {

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/mpfc.h"
 #include "mpfc_common.cuh"
 
@@ -49,6 +51,7 @@ struct mpfc_s {
 void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 int mpfc_num_levels(int m, int n, int coarsest);
 mpfc::Coef mpfc_coef(const mpfc_params* p, int scheme, double h);
+void mpfc_build_K3(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<double>& K3);
 int mpfc_reduce_blocks(size_t G);
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd,
                        void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme);

@@ -91,6 +91,18 @@ def load(build_if_missing: bool = True):
     lib.mpfc_probe_fp64_fma.argtypes = [_VP, _VP, P(ctypes.c_double)]
     lib.mpfc_probe_rcp.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.mpfc_set_launch_mode.argtypes = [_VP, ctypes.c_int]
+    lib.mpfc_batch_workspace_bytes.argtypes = [ctypes.c_int, P(mpfc_params)]
+    lib.mpfc_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.mpfc_batch_create.argtypes = [ctypes.c_int, P(mpfc_params), _VP, ctypes.c_size_t, _VP, P(_VP)]
+    lib.mpfc_batch_destroy.argtypes = [_VP]
+    lib.mpfc_batch_destroy.restype = None
+    lib.mpfc_batch_set_state.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP]
+    lib.mpfc_batch_get_state.argtypes = [_VP, ctypes.c_int, _VP, _VP, _VP]
+    lib.mpfc_batch_step.argtypes = [_VP, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]
+    lib.mpfc_batch_step_cycles.argtypes = [_VP, ctypes.c_int, ctypes.c_int, P(ctypes.c_int)]
+    lib.mpfc_batch_levels.argtypes = [_VP]
+    lib.mpfc_batch_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.mpfc_batch_time_smooth.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_float)]
     lib.mpfc_mass.argtypes = [_VP, P(ctypes.c_double)]
     lib.mpfc_energy.argtypes = [_VP, P(mpfc_energy_t)]
     lib.mpfc_strerror.argtypes = [ctypes.c_int]
@@ -315,3 +327,71 @@ def probe_fp64_tflops(stream=None) -> float:
     v = ctypes.c_double()
     _check(lib.mpfc_probe_fp64_fma(scratch.data_ptr(), st.cuda_stream, ctypes.byref(v)), "mpfc_probe_fp64_fma")
     return v.value
+
+
+class BatchSolver:
+    """Many independent instances advanced together (mpfc_batch_*)."""
+
+    def __init__(self, params_list, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmpfc needs a CUDA device")
+        self._torch = torch
+        self.lib = load()
+        self.count = len(params_list)
+        self.params = (mpfc_params * self.count)(*params_list)
+        nbytes = int(self.lib.mpfc_batch_workspace_bytes(self.count, self.params))
+        if nbytes == 0:
+            raise MPFCError(MPFC_ERR_INVALID, "mpfc_batch_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        aligned = (self.workspace.data_ptr() + 255) & ~255
+        h = _VP()
+        _check(self.lib.mpfc_batch_create(self.count, self.params, aligned, nbytes, self.stream.cuda_stream,
+                                          ctypes.byref(h)), "mpfc_batch_create")
+        self.h = h
+        self.levels = self.lib.mpfc_batch_levels(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpfc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, inst, phi, phi_prev=None, psi=None):
+        keep = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None for a in (phi, phi_prev, psi)]
+        _check(self.lib.mpfc_batch_set_state(self.h, inst, *[a.ctypes.data if a is not None else None for a in keep]),
+               "mpfc_batch_set_state")
+        self.stream.synchronize()
+
+    def get_state(self, inst):
+        p = self.params[inst]
+        outs = [np.empty((p.n, p.m)) for _ in range(3)]
+        _check(self.lib.mpfc_batch_get_state(self.h, inst, *[o.ctypes.data for o in outs]), "mpfc_batch_get_state")
+        return outs
+
+    def step(self, scheme, nsteps=1, raise_on_error=True):
+        st = (ctypes.c_int * self.count)()
+        cy = (ctypes.c_int * self.count)()
+        rc = self.lib.mpfc_batch_step(self.h, scheme, nsteps, st, cy)
+        if rc != MPFC_OK and raise_on_error:
+            raise MPFCError(rc, "mpfc_batch_step")
+        return rc, list(st), list(cy)
+
+    def step_cycles(self, scheme, ncycles):
+        st = (ctypes.c_int * self.count)()
+        rc = self.lib.mpfc_batch_step_cycles(self.h, scheme, ncycles, st)
+        return rc, list(st)
+
+    def set_tile(self, level, tx, ty):
+        _check(self.lib.mpfc_batch_set_tile(self.h, level, tx, ty), "mpfc_batch_set_tile")
+
+    def time_smooth(self, scheme, level, reps=5):
+        ms = ctypes.c_float()
+        _check(self.lib.mpfc_batch_time_smooth(self.h, scheme, level, reps, ctypes.byref(ms)), "mpfc_batch_time_smooth")
+        return ms.value
