@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--profile", action="store_true", help="steps only, no flush and no extras (ncu launch list)")
     ap.add_argument("--profile-smooth", action="store_true",
                     help="only the finest-level sweep kernel, two sweeps (ncu capture of the top kernel)")
@@ -263,6 +264,7 @@ def run_ours(args):
     rc, recs, count = solver.records(max(K, 1))
     if rc != mpfc.MPFC_OK:
         raise mpfc.MPFCError(rc, "timed steps")
+    recs_main = recs
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -398,6 +400,38 @@ def run_ours(args):
                             "tiles": {str(k): v[:2] for k, v in tiles.items()},
                             "steps": Kb}
         b.close()
+
+    # learned initial guess (model trained by paper_1208_2643_gb300.guess on solver data at 256^2)
+    if not args.no_learned:
+        from paper_1208_2643_gb300 import guess as gmod
+        blob = gmod.load()
+        if blob is not None:
+            pl = mpfc.default_params(m=size, n=size, h=w["h"], M=w["M"], epsilon=w["epsilon"], beta=w["beta"],
+                                     dt=w["dt"], tol=w["tol"], omega=w["omega"], guess=mpfc.MPFC_GUESS_LEARNED)
+            sl = mpfc.Solver(pl, stream=stream)
+            gmod.attach(sl, blob)
+            sl.set_state(phi0)
+            msl, recl = timed_steps(sl, K, max(args.warmup, 0))
+            if world > 1:
+                t = torch.tensor([msl], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                msl = float(t.item())
+            # the network's own cost: the five convolutions and the features, timed alone
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(10):
+                sl.lib.mpfc_op_learned_guess(sl.h)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            forms["learned"] = {"steps_per_s": world * K / (msl * 1e-3),
+                                "vcycles_per_step": float(np.mean([r["cycles"] for r in recl])),
+                                "res0_mean": float(np.mean([r["res0"] for r in recl])),
+                                "res0_mean_extrapolated": float(np.mean([r["res0"] for r in recs_main])),
+                                "network_ms_per_step": ev0.elapsed_time(ev1) / 10,
+                                "speedup_vs_fp64": (world * K / (msl * 1e-3)) / steps_per_s,
+                                "model": "5 x conv3x3 (3-32-32-32-32-1), GELU, bf16/fp32-acc, mma.sync tensor cores; "
+                                         "trained on 20k solver steps at 256^2"}
+            sl.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -138,6 +138,14 @@ int mpfc_set_launch_mode(mpfc_t* h, int mode);
  * comparisons.  Same state update and synchronisation as mpfc_step. */
 int mpfc_step_cycles(mpfc_t* h, int scheme, int ncycles, mpfc_step_info* info);
 
+/* Loads the learned initial guess model (host or device pointer to
+ * MPFC_CNN_PARAM_COUNT fp32 values, layout in mpfc_cnn.h) into the handle's workspace.
+ * The handle must have been created with guess = MPFC_GUESS_LEARNED (its workspace
+ * then holds the network's weights and activations).  The guess uses phi^{k-2}, which
+ * the handle keeps from mpfc_set_state on (phi^{-2} = phi^{-1} at the start).
+ * Synchronises. */
+int mpfc_set_guess_model(mpfc_t* h, const float* params, size_t count);
+
 /* Mass h^2 sum phi^k (conserved, Sec. 3.3, first theorem).  Synchronises. */
 int mpfc_mass(mpfc_t* h, double* out);
 
@@ -245,6 +253,11 @@ int mpfc_op_restrict(mpfc_t* h, int scheme, int level, const double* phi, const 
 int mpfc_op_prolong(mpfc_t* h, int level, const double* phi_c_new, const double* mu_c_new,
                     const double* kappa_c_new, const double* phi_c_old, const double* mu_c_old,
                     const double* kappa_c_old, double* phi, double* mu, double* kappa);
+
+/* Runs the learned guess alone on the current state: the network's correction is
+ * added to the finest level's phi array (handle created with MPFC_GUESS_LEARNED and a
+ * model loaded).  For timing the network; asynchronous. */
+int mpfc_op_learned_guess(mpfc_t* h);
 
 /* Exact solve of N(u) = S on the coarsest level (Newton on the eliminated
  * equation for phi; mu, kappa recovered from the second and third rows). */

@@ -591,8 +591,8 @@ __device__ __forceinline__ int step_status(const Ctl* ctl) {
 // (scheme 2, (3.15)); then phi^{k-1} <- phi^k, phi^k <- phi.  Skipped for a
 // failed or skipped step, which also halts the remaining steps of the call.
 template <int SCH>
-__global__ void k_commit(const double* __restrict__ phinew, double* phik, double* phikm1, double* psik, int G,
-                         double inv_s, Ctl* ctl, StepRecord* info) {
+__global__ void k_commit(const double* __restrict__ phinew, double* phik, double* phikm1, double* psik,
+                         double* phikm2, int G, double inv_s, Ctl* ctl, StepRecord* info) {
   int st = step_status(ctl);
   int skip = ctl->skip;
   if (blockIdx.x == 0 && threadIdx.x == 0 && !skip) {
@@ -610,6 +610,7 @@ __global__ void k_commit(const double* __restrict__ phinew, double* phik, double
     double pn = phinew[t], p0 = phik[t];
     double ps = (SCH == 1) ? (pn - p0) * inv_s : 2.0 * inv_s * (pn - p0) - psik[t];
     psik[t] = ps;
+    if (phikm2) phikm2[t] = phikm1[t];
     phikm1[t] = p0;
     phik[t] = pn;
   }

@@ -176,8 +176,8 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
   int Gc = lev[L - 1].m * lev[L - 1].n;
   double* K3a = c.take<double>((size_t)Gc * Gc);
   double* K3b = c.take<double>((size_t)Gc * Gc);
-  size_t extra = mpfc_fp32_carve(H, p, &c.off, base, L);
-  (void)extra;
+  mpfc_fp32_carve(H, p, &c.off, base, L);
+  mpfc_guess_carve(H, p, &c.off, base);
   if (H && base) {
     H->nlev = L;
     H->ctl = ctl;
@@ -289,11 +289,18 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
   return MPFC_OK;
 }
 
-extern "C" void mpfc_destroy(mpfc_t* H) {
-  if (!H) return;
+void mpfc_drop_graphs(mpfc_s* H) {
   for (int s = 0; s < 2; ++s)
     for (int v = 0; v < 2; ++v)
-      if (H->exec[s][v]) cudaGraphExecDestroy(H->exec[s][v]);
+      if (H->exec[s][v]) {
+        cudaGraphExecDestroy(H->exec[s][v]);
+        H->exec[s][v] = nullptr;
+      }
+}
+
+extern "C" void mpfc_destroy(mpfc_t* H) {
+  if (!H) return;
+  mpfc_drop_graphs(H);
   mpfc_fp32_destroy(H);
   if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   if (H->body_stream) cudaStreamDestroy(H->body_stream);
@@ -374,7 +381,7 @@ static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
   A.psik = H->psik;
   A.psi_coef = (SCH == 1) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
   A.half_alpha = 0.5 * (1.0 - p.epsilon);
-  A.guess = (p.guess == MPFC_GUESS_PREV) ? 0 : (p.guess == MPFC_GUESS_EXTRAP ? 1 : 2);
+  A.guess = (p.guess == MPFC_GUESS_PREV) ? 0 : 1;   // the learned guess corrects the extrapolation
   dim3 g0 = grid_for(L0.m, L0.n, kBlk2d);
   k_source_guess<SCH><<<g0, kBlk2d, 0, s>>>(L0, A);
   if (p.guess == MPFC_GUESS_LEARNED) mpfc_enqueue_learned_guess(H, s);
@@ -392,8 +399,8 @@ static void enqueue_commit(mpfc_s* H, cudaStream_t s) {
   size_t G = (size_t)H->p.m * H->p.n;
   int blocks = (int)((G + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_commit<SCH><<<blocks, 256, 0, s>>>(H->lev[0].phi, H->phik, H->phikm1, H->psik, (int)G, 1.0 / H->p.dt, H->ctl,
-                                       H->info);
+  k_commit<SCH><<<blocks, 256, 0, s>>>(H->lev[0].phi, H->phik, H->phikm1, H->psik, H->guess.phikm2, (int)G,
+                                       1.0 / H->p.dt, H->ctl, H->info);
 }
 
 template <int SCH>
@@ -554,6 +561,8 @@ extern "C" int mpfc_set_state(mpfc_t* H, const double* phi, const double* phi_pr
   CK(cudaMemcpyAsync(H->phikm1, phi_prev ? phi_prev : phi, bytes, cudaMemcpyDefault, H->stream));
   if (psi) CK(cudaMemcpyAsync(H->psik, psi, bytes, cudaMemcpyDefault, H->stream));
   else CK(cudaMemsetAsync(H->psik, 0, bytes, H->stream));
+  if (H->guess.phikm2)
+    CK(cudaMemcpyAsync(H->guess.phikm2, phi_prev ? phi_prev : phi, bytes, cudaMemcpyDefault, H->stream));
   k_ctl_reset<<<1, 32, 0, H->stream>>>(H->ctl, 0);
   CK(cudaGetLastError());
   return MPFC_OK;

@@ -18,6 +18,18 @@ struct Lev32 {
   float* q;                  // gam + g'(phi) of the FP64 iterate, restricted
 };
 
+// Learned-guess buffers in the workspace (MPFC_GUESS_LEARNED).
+struct MpfcGuess {
+  float* params = nullptr;     // fp32 model blob (normalisation, weights, biases)
+  void* wk[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // packed bf16 weights
+  void* x = nullptr;           // network input, bf16 [m*n][4]
+  void* act[2] = {nullptr, nullptr};   // activations, bf16 [m*n][32]
+  double* phikm2 = nullptr;    // phi^{k-2}
+  double* mean = nullptr;
+  float norms_host[4] = {1.f, 1.f, 1.f, 1.f};   // host copy of the normalisation scales
+  bool loaded = false;
+};
+
 struct mpfc_s {
   mpfc_params p;
   cudaStream_t stream = nullptr;
@@ -45,10 +57,11 @@ struct mpfc_s {
   float* K3f[2] = {nullptr, nullptr};
   int outer_max = 0;
   // learned initial guess
-  void* guess_model = nullptr;
+  MpfcGuess guess;
 };
 
 void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void mpfc_drop_graphs(mpfc_s* H);
 int mpfc_num_levels(int m, int n, int coarsest);
 mpfc::Coef mpfc_coef(const mpfc_params* p, int scheme, double h);
 void mpfc_build_K3(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<double>& K3);
@@ -67,5 +80,6 @@ int mpfc_fp32_step_stream(mpfc_s* H, int scheme);
 int mpfc_host_continue(const mpfc::Ctl* c);
 
 // learned initial guess (guess_cnn.cu)
+size_t mpfc_guess_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base);
 bool mpfc_has_guess_model(const mpfc_s* H);
 void mpfc_enqueue_learned_guess(mpfc_s* H, cudaStream_t s);

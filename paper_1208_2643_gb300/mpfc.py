@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_probe_fp64_fma.argtypes = [_VP, _VP, P(ctypes.c_double)]
     lib.mpfc_probe_rcp.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.mpfc_set_launch_mode.argtypes = [_VP, ctypes.c_int]
+    lib.mpfc_op_learned_guess.argtypes = [_VP]
     lib.mpfc_batch_workspace_bytes.argtypes = [ctypes.c_int, P(mpfc_params)]
     lib.mpfc_batch_workspace_bytes.restype = ctypes.c_size_t
     lib.mpfc_batch_create.argtypes = [ctypes.c_int, P(mpfc_params), _VP, ctypes.c_size_t, _VP, P(_VP)]

@@ -1,0 +1,168 @@
+"""The learned guess's kernels against the FP64 numpy oracle (oracle/cnn.py), fed the
+same BF16-rounded inputs and weights, and the gain of a trained network.
+
+Tolerances: FP32 outputs 1e-4 relative to their maximum (FP32 accumulation of exact
+BF16 products); BF16 outputs 1e-2 (one BF16 rounding)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_2643_gb300 import guess
+    guess._lib()
+    return guess
+
+
+def bf16(a):
+    """BF16-rounded copy (torch on the CPU) as float64 numpy, and the device bf16 tensor."""
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+    return t.float().double().numpy(), t.cuda()
+
+
+def pad_ch(a, cp):
+    out = np.zeros(a.shape[:-1] + (cp,))
+    out[..., :a.shape[-1]] = a
+    return out
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+@pytest.mark.parametrize("ci,co,cip,cop,H,W", [(32, 32, 32, 32, 8, 40), (3, 32, 4, 32, 12, 32), (32, 1, 32, 8, 5, 70)])
+def test_conv_forward_linear(G, oracle_mod, ci, co, cip, cop, H, W):
+    from oracle import cnn
+    lib = G._lib()
+    rng = np.random.default_rng(0)
+    B = 2
+    xr, xd = bf16(pad_ch(rng.normal(size=(B, H, W, ci)), cip))
+    w = rng.normal(scale=0.2, size=(9, ci, co)).astype(np.float32)
+    wr = torch.from_numpy(w).bfloat16().float().double().numpy()
+    bias = rng.normal(size=co).astype(np.float32)
+    wd = torch.from_numpy(w).cuda()
+    K = (9 * cip + 15) // 16 * 16
+    wk = torch.empty(cop * K, dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.mpfc_cnn_pack_weights(wd.data_ptr(), ci, co, cip, cop, 0, wk.data_ptr(), s) == 0
+    y = torch.empty((B, H, W, cop), dtype=torch.float32, device="cuda")
+    bd = torch.from_numpy(bias).cuda()
+    assert lib.mpfc_cnn_conv_forward(xd.data_ptr(), B, H, W, cip, wk.data_ptr(), bd.data_ptr(), co, cop, 1, None,
+                                     y.data_ptr(), None, s) == 0
+    torch.cuda.synchronize()
+    ref = cnn.conv3x3(xr[..., :ci], wr, bias.astype(np.float64))
+    got = y.cpu().numpy()
+    assert rel(got[..., :co], ref) < 1e-4
+    assert np.all(got[..., co:] == 0)
+
+
+def test_conv_forward_gelu_and_saved_preactivation(G):
+    from oracle import cnn
+    lib = G._lib()
+    rng = np.random.default_rng(1)
+    B, H, W, ci, co = 1, 8, 64, 32, 32
+    xr, xd = bf16(rng.normal(size=(B, H, W, ci)))
+    w = rng.normal(scale=0.2, size=(9, ci, co)).astype(np.float32)
+    wr = torch.from_numpy(w).bfloat16().float().double().numpy()
+    wk = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.mpfc_cnn_pack_weights(torch.from_numpy(w).cuda().data_ptr(), ci, co, 32, 32, 0, wk.data_ptr(), s) == 0
+    yb = torch.empty((B, H, W, 32), dtype=torch.bfloat16, device="cuda")
+    z = torch.empty((B, H, W, 32), dtype=torch.float32, device="cuda")
+    assert lib.mpfc_cnn_conv_forward(xd.data_ptr(), B, H, W, 32, wk.data_ptr(), None, co, 32, 0, yb.data_ptr(), None,
+                                     z.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    zr = cnn.conv3x3(xr, wr)
+    assert rel(z.cpu().numpy(), zr) < 1e-4
+    assert rel(yb.float().cpu().numpy(), cnn.gelu(zr)) < 1e-2
+
+
+@pytest.mark.parametrize("cin,cout_p,H,W", [(32, 32, 8, 40), (32, 4, 6, 32)])
+def test_conv_backward_data(G, cin, cout_p, H, W):
+    from oracle import cnn
+    lib = G._lib()
+    rng = np.random.default_rng(2)
+    B = 2
+    cout = 1 if cout_p == 4 else 32
+    dzr, dzd = bf16(pad_ch(rng.normal(size=(B, H, W, cout)), cout_p))
+    w = rng.normal(scale=0.2, size=(9, cin, cout)).astype(np.float32)
+    wr = torch.from_numpy(w).bfloat16().float().double().numpy()
+    K = (9 * cout_p + 15) // 16 * 16
+    wkt = torch.empty(32 * K, dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.mpfc_cnn_pack_weights(torch.from_numpy(w).cuda().data_ptr(), cin, cout, 32, cout_p, 1,
+                                     wkt.data_ptr(), s) == 0
+    zp = rng.normal(size=(B, H, W, 32)).astype(np.float32)
+    zpd = torch.from_numpy(zp).cuda()
+    ob = torch.empty((B, H, W, 32), dtype=torch.bfloat16, device="cuda")
+    of = torch.empty((B, H, W, 32), dtype=torch.float32, device="cuda")
+    assert lib.mpfc_cnn_conv_backward_data(dzd.data_ptr(), B, H, W, cout_p, wkt.data_ptr(), cin, 32, zpd.data_ptr(),
+                                           ob.data_ptr(), of.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    ref = cnn.conv3x3_grad_input(dzr[..., :cout], wr) * cnn.gelu_grad(zp.astype(np.float64))
+    assert rel(of.cpu().numpy(), ref) < 1e-4
+
+
+@pytest.mark.parametrize("cin,cin_p,cout,cout_p", [(32, 32, 32, 32), (3, 4, 32, 32), (32, 32, 1, 4)])
+def test_conv_backward_weight(G, cin, cin_p, cout, cout_p):
+    from oracle import cnn
+    lib = G._lib()
+    rng = np.random.default_rng(3)
+    B, H, W = 2, 24, 40
+    xr, xd = bf16(pad_ch(rng.normal(size=(B, H, W, cin)), cin_p))
+    dz = pad_ch(rng.normal(size=(B, H, W, cout)), cout_p).astype(np.float32)
+    dzd = torch.from_numpy(dz).cuda()
+    dw = torch.empty(9 * cin * cout, dtype=torch.float32, device="cuda")
+    db = torch.empty(cout, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(int(lib.mpfc_cnn_wgrad_scratch_bytes(B, H, W)), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.mpfc_cnn_conv_backward_weight(xd.data_ptr(), B, H, W, cin, cin_p, dzd.data_ptr(), cout, cout_p,
+                                             dw.data_ptr(), db.data_ptr(), scratch.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    gw, gb = cnn.conv3x3_grad_weight(xr[..., :cin], dz[..., :cout].astype(np.float64))
+    assert rel(dw.cpu().numpy().reshape(9, cin, cout), gw) < 1e-4
+    assert rel(db.cpu().numpy(), gb) < 1e-4
+
+
+def test_adam_matches_oracle(G):
+    from oracle import cnn
+    lib = G._lib()
+    rng = np.random.default_rng(4)
+    p, g = rng.normal(size=1000), rng.normal(size=1000)
+    m, v = np.zeros(1000), np.zeros(1000)
+    pd, gd = torch.tensor(p, dtype=torch.float32, device="cuda"), torch.tensor(g, dtype=torch.float32, device="cuda")
+    md, vd = torch.zeros_like(pd), torch.zeros_like(pd)
+    s = torch.cuda.current_stream().cuda_stream
+    for t in (1, 2, 3):
+        assert lib.mpfc_cnn_adam(pd.data_ptr(), gd.data_ptr(), md.data_ptr(), vd.data_ptr(), 1000, 1e-2, 0.9, 0.999,
+                                 1e-8, t, s) == 0
+        p, m, v = cnn.adam(p, g, m, v, t, lr=1e-2)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(pd.cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+
+
+def test_learned_guess_gain(G):
+    """A network trained briefly on solver trajectories lowers the residual of the
+    initial guess against the linear extrapolation on a held-out trajectory, and the
+    solver still converges to the same tolerance."""
+    from paper_1208_2643_gb300 import inputs, mpfc
+    trajs = G.generate_trajectories(n_traj=2, steps=300, size=64, seed=11)
+    blob = G.train(trajs, epochs=3, batch=8, lr=3e-3, seed=0)
+    m = 64
+    phi0 = inputs.noise_field(m, m, 0.08, 0.05, 99)
+    res = {}
+    for gs in (mpfc.MPFC_GUESS_EXTRAP, mpfc.MPFC_GUESS_LEARNED):
+        g = mpfc.Solver(mpfc.default_params(m=m, n=m, guess=gs))
+        if gs == mpfc.MPFC_GUESS_LEARNED:
+            G.attach(g, blob)
+        g.set_state(phi0)
+        g.step(1, 20)
+        infos = g.step(1, 40)
+        assert all(i["status"] == 0 and i["res"] <= 1e-10 for i in infos)
+        res[gs] = (np.mean([i["res0"] for i in infos]), np.mean([i["cycles"] for i in infos]))
+    assert res[mpfc.MPFC_GUESS_LEARNED][0] < 0.8 * res[mpfc.MPFC_GUESS_EXTRAP][0], res
