@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--profile", action="store_true", help="steps only, no flush and no extras (ncu launch list)")
+    ap.add_argument("--form", choices=["fp64", "fp32"], default="fp64",
+                    help="with --profile: which solver form the launch list runs")
     ap.add_argument("--profile-smooth", action="store_true",
                     help="only the finest-level sweep kernel, two sweeps (ncu capture of the top kernel)")
     return ap.parse_args()
@@ -198,9 +200,8 @@ def run_ours(args):
     import torch.distributed as dist
     from paper_1208_2643_gb300 import inputs, mpfc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1208_2643_gb300 import replicas
+    rank, world, local = replicas.rank_info()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -208,10 +209,12 @@ def run_ours(args):
     w = workload(size, scheme)
     p = mpfc.default_params(m=size, n=size, h=w["h"], M=w["M"], epsilon=w["epsilon"], beta=w["beta"], dt=w["dt"],
                             tol=w["tol"], omega=w["omega"], guess=mpfc.MPFC_GUESS_EXTRAP)
+    if args.profile and args.form == "fp32":
+        p.precision = mpfc.MPFC_FP32_INNER
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     solver = mpfc.Solver(p, stream=stream)
-    phi0 = inputs.noise_field(size, size, 0.07, 0.05, 1 + rank)
+    phi0 = inputs.noise_field(size, size, 0.07, 0.05, replicas.instance_seed(1, rank))
     solver.set_state(phi0)
     if args.profile_smooth:
         phik, _, _ = solver.get_state(device=True)
@@ -265,14 +268,11 @@ def run_ours(args):
     if rc != mpfc.MPFC_OK:
         raise mpfc.MPFCError(rc, "timed steps")
     recs_main = recs
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms = replicas.job_time_ms(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device="cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     cycles = [r["cycles"] for r in recs]
-    steps_per_s = world * K / (ms * 1e-3)
+    steps_per_s = replicas.throughput(K, world, ms)
     launches = sum(kernel_launches_per_step(solver.levels, p.nu1, p.nu2, c, scheme) for c in cycles)
 
     if args.profile:
@@ -329,10 +329,7 @@ def run_ours(args):
     s32 = mpfc.Solver(p32, stream=stream)
     s32.set_state(phi0)
     ms32, recs32 = timed_steps(s32, K, max(args.warmup, 0))
-    if world > 1:
-        t = torch.tensor([ms32], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms32 = float(t.item())
+    ms32 = replicas.job_time_ms(ms32, device="cuda")
     # error of the mixed-precision steps against the FP64 path, 5 steps from phi^0
     a64 = mpfc.Solver(p, stream=stream)
     a32 = mpfc.Solver(p32, stream=stream)
@@ -412,10 +409,7 @@ def run_ours(args):
             gmod.attach(sl, blob)
             sl.set_state(phi0)
             msl, recl = timed_steps(sl, K, max(args.warmup, 0))
-            if world > 1:
-                t = torch.tensor([msl], device="cuda", dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                msl = float(t.item())
+            msl = replicas.job_time_ms(msl, device="cuda")
             # the network's own cost: the five convolutions and the features, timed alone
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)

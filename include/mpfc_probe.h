@@ -23,6 +23,12 @@ int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* tflops);
  * of its error bound.  Asynchronous on `cuda_stream`. */
 int mpfc_probe_rcp(const double* d_x, double* d_out, int n, void* cuda_stream);
 
+/* Applies the library's integer-pipe binary64 <-> binary32 conversions to n device
+ * doubles: d_rn = rounded to nearest even, d_trunc = truncated, d_back = d_rn widened
+ * back to binary64.  Inputs must lie in the normal binary32 magnitude range (or be 0).
+ * For tests against the hardware conversions.  Asynchronous on `cuda_stream`. */
+int mpfc_probe_convert(const double* d_x, float* d_rn, float* d_trunc, double* d_back, int n, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

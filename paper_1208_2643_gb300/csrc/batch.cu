@@ -129,7 +129,7 @@ __global__ void kb_restrict_pk(const BItem* __restrict__ items, int n, const Lev
 
 template <int SCH>
 __global__ void kb_coarse(const Lev* __restrict__ levs, const Coef* __restrict__ coefs, const int* __restrict__ nlev,
-                          const double* __restrict__ K3, const long long* __restrict__ K3off,
+                          const float* __restrict__ K3, const long long* __restrict__ K3off,
                           const BCtl* __restrict__ ctl) {
   int inst = blockIdx.x;
   if (!ctl[inst].active) return;
@@ -327,7 +327,7 @@ struct mpfc_batch_s {
   Coef* d_coef[2] = {nullptr, nullptr};
   SourceArgs* d_src[2] = {nullptr, nullptr};
   int* d_nlev = nullptr;
-  double* d_K3[2] = {nullptr, nullptr};
+  float* d_K3[2] = {nullptr, nullptr};
   long long* d_K3off = nullptr;
   double* d_inv_s = nullptr;
   double** d_state = nullptr;
@@ -472,8 +472,8 @@ size_t carve_batch(mpfc_batch_s* B, int count, const mpfc_params* each, char* ba
     k3off[i] = (long long)k3tot;
     k3tot += (size_t)mc * nc * mc * nc;
   }
-  double* d_K3a = c.take<double>(k3tot);
-  double* d_K3b = c.take<double>(k3tot);
+  float* d_K3a = c.take<float>(k3tot);
+  float* d_K3b = c.take<float>(k3tot);
   if (B && base) {
     B->d_lev = d_lev;
     B->d_coef[0] = d_c1;
@@ -570,8 +570,8 @@ void enqueue_batch_vcycle(mpfc_batch_s* B, cudaStream_t s) {
     const Lev& C = B->lev[i * kMaxLevels + B->nlev[i] - 1];
     Gc = std::max(Gc, C.m * C.n);
   }
-  size_t smem = sizeof(double) * ((size_t)Gc * (Gc + 1) + 8 * (size_t)Gc);
-  kb_coarse<SCH><<<B->count, 256, smem, s>>>(B->d_lev, B->d_coef[S], B->d_nlev, B->d_K3[S], B->d_K3off, B->d_ctl);
+  size_t smem = sizeof(double) * 7 * (size_t)Gc + sizeof(float) * ((size_t)Gc * (Gc + 1) + (size_t)Gc);
+  kb_coarse<SCH><<<B->count, 32, smem, s>>>(B->d_lev, B->d_coef[S], B->d_nlev, B->d_K3[S], B->d_K3off, B->d_ctl);
   for (int gl = B->GL - 2; gl >= 0; --gl) {
     int n = B->full_cnt[gl + 1];
     if (n) kb_prolong<<<grid_for_items(n), blk2, 0, s>>>(B->d_items + B->full_off[gl + 1], n, B->d_lev, B->d_ctl);
@@ -701,7 +701,7 @@ extern "C" int mpfc_batch_create(int count, const mpfc_params* each, void* d_wor
     }
     std::vector<long long> k3off(count);
     std::vector<double> inv_s(count);
-    std::vector<double> K3all[2];
+    std::vector<float> K3all[2];
     long long k3tot = 0;
     for (int i = 0; i < count; ++i) {
       const mpfc_params& p = each[i];
@@ -747,9 +747,9 @@ extern "C" int mpfc_batch_create(int count, const mpfc_params* each, void* d_wor
         (e = cudaMemcpyAsync(B->d_state, B->state.data(), sizeof(double*) * 3 * count, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(B->d_ctl, c0.data(), sizeof(BCtl) * count, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(B->d_glob, &g0, sizeof(g0), cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(B->d_K3[0], K3all[0].data(), sizeof(double) * K3all[0].size(), cudaMemcpyHostToDevice,
+        (e = cudaMemcpyAsync(B->d_K3[0], K3all[0].data(), sizeof(float) * K3all[0].size(), cudaMemcpyHostToDevice,
                              s)) ||
-        (e = cudaMemcpyAsync(B->d_K3[1], K3all[1].data(), sizeof(double) * K3all[1].size(), cudaMemcpyHostToDevice,
+        (e = cudaMemcpyAsync(B->d_K3[1], K3all[1].data(), sizeof(float) * K3all[1].size(), cudaMemcpyHostToDevice,
                              s)) ||
         (e = cudaStreamSynchronize(s))) {
       mpfc_set_cuda_error(e, "batch tables", __FILE__, __LINE__);

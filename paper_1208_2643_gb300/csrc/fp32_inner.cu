@@ -64,10 +64,12 @@ __global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl
     v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));
     double p = L.phi[t];
     double pk = (SCH == 2) ? L.pk[t] : 0.0;
-    E.r1[t] = (float)a;
-    E.r2[t] = (float)b;
-    E.r3[t] = (float)c;
-    E.q[t] = (float)(k.gam + dg_of<SCH>(p, pk));
+    // defect and linearisation handed to the FP32 solve (zero stays zero; values below
+    // 2^-126 in magnitude are far under the FP32 solve's resolution of the defect)
+    E.r1[t] = fabs(a) < 1.2e-38 ? 0.f : f64_to_f32_rn(a);
+    E.r2[t] = fabs(b) < 1.2e-38 ? 0.f : f64_to_f32_rn(b);
+    E.r3[t] = fabs(c) < 1.2e-38 ? 0.f : f64_to_f32_rn(c);
+    E.q[t] = f64_to_f32_rn(k.gam + dg_of<SCH>(p, pk));
     E.ephi[t] = 0.f;
     E.emu[t] = 0.f;
     E.eka[t] = 0.f;
@@ -96,9 +98,10 @@ __global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl
 __global__ void k_update(Lev L, Lev32 E) {
   int G = L.m * L.n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
-    L.phi[t] += (double)E.ephi[t];
-    L.mu[t] += (double)E.emu[t];
-    L.ka[t] += (double)E.eka[t];
+    float a = E.ephi[t], b = E.emu[t], c = E.eka[t];
+    L.phi[t] += fabsf(a) < 1.2e-38f ? 0.0 : f32_to_f64(a);
+    L.mu[t] += fabsf(b) < 1.2e-38f ? 0.0 : f32_to_f64(b);
+    L.ka[t] += fabsf(c) < 1.2e-38f ? 0.0 : f32_to_f64(c);
   }
 }
 
@@ -310,14 +313,20 @@ __global__ void k_coarse32(Lev32 C, Coef32 k, const float* __restrict__ K3f) {
   }
 }
 
-__global__ void k_k3_to_float(const double* __restrict__ a, float* __restrict__ b, int count) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) b[i] = (float)a[i];
-}
-
 size_t coarse32_smem(const Lev32& C) {
   int G = C.m * C.n;
   return sizeof(float) * ((size_t)G * (G + 1) + 4 * (size_t)G);
+}
+
+// `sweeps` red-black sweeps of one level, one launch per colour.  (A single-launch
+// sweep over shared-memory tiles with a 2-cell halo halves the DRAM reads at 2048^2 but
+// was slower on GB300 at every level size measured: its staging is latency bound.)
+void sweeps32(const Lev32& F, const Coef32& kf, int sweeps, cudaStream_t s) {
+  dim3 g = grid_of(F.m / 2, F.n);
+  for (int sw = 0; sw < sweeps; ++sw) {
+    k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 0);
+    k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 1);
+  }
 }
 
 int inner_cycles_of(const mpfc_s* H) { return H->p.inner_cycles > 0 ? H->p.inner_cycles : 2; }
@@ -330,11 +339,7 @@ void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
-    dim3 g = grid_of(F.m / 2, F.n);
-    for (int sw = 0; sw < p.nu1; ++sw) {
-      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 0);
-      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 1);
-    }
+    sweeps32(F, kf, p.nu1, s);
     k_restrict_defect32<<<grid_of(C.m, C.n), kBlk, 0, s>>>(F, C, kf);
   }
   const Lev32& Cc = H->lev32[L - 1];
@@ -344,11 +349,7 @@ void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
     k_prolong32<<<grid_of(C.m, C.n), kBlk, 0, s>>>(F, C);
-    dim3 g = grid_of(F.m / 2, F.n);
-    for (int sw = 0; sw < p.nu2; ++sw) {
-      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 0);
-      k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 1);
-    }
+    sweeps32(F, kf, p.nu2, s);
   }
 }
 
@@ -407,28 +408,13 @@ size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base,
     n /= 2;
     h *= 2.0;
   }
-  int mc = p->m >> (nlev - 1), nc = p->n >> (nlev - 1);
-  size_t Gc = (size_t)mc * nc;
-  float* k3a = take(Gc * Gc);
-  float* k3b = take(Gc * Gc);
-  if (H && base) {
-    H->K3f[0] = k3a;
-    H->K3f[1] = k3b;
-  }
   return *off - start;
 }
 
 int mpfc_fp32_init(mpfc_s* H) {
   if (H->p.precision != MPFC_FP32_INNER) return MPFC_OK;
-  const Lev& C = H->lev[H->nlev - 1];
-  int count = C.m * C.n * C.m * C.n;
-  for (int s = 0; s < 2; ++s) k_k3_to_float<<<(count + 255) / 256, 256, 0, H->stream>>>(H->K3[s], H->K3f[s], count);
-  cudaError_t e = cudaStreamSynchronize(H->stream);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    mpfc_set_cuda_error(e, "fp32 init", __FILE__, __LINE__);
-    return MPFC_ERR_CUDA;
-  }
+  H->K3f[0] = H->K3[0];
+  H->K3f[1] = H->K3[1];
   return MPFC_OK;
 }
 

@@ -357,7 +357,7 @@ static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
 //   F(phi) = phi - c L (S2 + g(phi) + gam phi + L (S3 + theta L phi)) - S1 = 0,
 // with Jacobian J = K3 - c L diag(gam + g'(phi)), K3 = I - c theta L^3 built on the
 // host.  Dense Gaussian elimination with partial pivoting in shared memory, one
-// CTA.  Stops one iteration after the update falls below 1e-15 (1 + |phi|_inf);
+// warp.  Stops one iteration after the update falls below 1e-15 (1 + |phi|_inf);
 // at most 40 iterations.  mu and kappa are then recovered from rows 3 and 2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t) {
@@ -366,106 +366,117 @@ __device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t) 
 }
 
 template <int SCH>
-__device__ void coarse_solve_block(const Lev& C, const Coef& k, const double* __restrict__ K3) {
+__device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __restrict__ K3f) {
+  // One warp.  Newton's method for F(phi) = 0 with F evaluated in FP64; the
+  // Jacobian is assembled, factorised (Gaussian elimination, partial pivoting) and
+  // solved in FP32, i.e. Newton with iterative refinement: every update is computed
+  // from the FP64 residual, so the iteration converges to the FP64 root.  FP32 keeps
+  // the serial elimination off the slow FP64 pipe (on GB300 one warp-wide FP64
+  // instruction occupies a sub-partition's FP64 unit for about 80 cycles).
   extern __shared__ double sm[];
   const int m = C.m, n = C.n, G = m * n, W = G + 1;
-  double* Jm = sm;              // G x (G+1), last column = right-hand side
-  double* ph = Jm + G * W;
+  double* ph = sm;
   double* s1 = ph + G;
   double* s2 = s1 + G;
   double* s3 = s2 + G;
   double* pk = s3 + G;
   double* kap = pk + G;
   double* muv = kap + G;
-  double* d = muv + G;
-  __shared__ int s_piv, s_stop, s_extra;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = tid; t < G; t += nt) {
+  float* Jm = reinterpret_cast<float*>(muv + G);   // G x (G+1), last column = right-hand side
+  float* d = Jm + G * W;
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  if (threadIdx.x >= 32) return;
+  for (int t = lane; t < G; t += 32) {
     ph[t] = C.phi[t];
     s1[t] = C.S1[t];
     s2[t] = C.S2[t];
     s3[t] = C.S3[t];
     pk[t] = (SCH == 2) ? C.pk[t] : 0.0;
   }
-  if (tid == 0) { s_stop = 0; s_extra = 0; }
-  __syncthreads();
+  __syncwarp();
+  const float cf = (float)k.c, ih2f = (float)k.ih2, gamf = (float)k.gam;
+  bool extra = false;
   for (int it = 0; it < 40; ++it) {
-    for (int t = tid; t < G; t += nt) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
-    __syncthreads();
-    for (int t = tid; t < G; t += nt)
+    for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
+    __syncwarp();
+    for (int t = lane; t < G; t += 32)
       muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t) - 4.0 * kap[t]);
-    __syncthreads();
-    for (int t = tid; t < G; t += nt) Jm[t * W + G] = s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t) - 4.0 * muv[t]);
-    for (int idx = tid; idx < G * G; idx += nt) {
+    __syncwarp();
+    for (int t = lane; t < G; t += 32)
+      Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t) - 4.0 * muv[t]));
+    for (int idx = lane; idx < G * G; idx += 32) {
       int r = idx / G, col = idx % G;
       int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
       int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
                 (ci == ri && cj == wrapm(rj - 1, n)) + (ci == ri && cj == wrapm(rj + 1, n));
-      double Lrc = k.ih2 * ((double)cnt - (r == col ? 4.0 : 0.0));
-      Jm[r * W + col] = K3[idx] - k.c * Lrc * (k.gam + dg_of<SCH>(ph[col], pk[col]));
+      float Lrc = ih2f * ((float)cnt - (r == col ? 4.f : 0.f));
+      Jm[r * W + col] = K3f[idx] - cf * Lrc * (gamf + (float)dg_of<SCH>(ph[col], pk[col]));
     }
-    __syncthreads();
+    __syncwarp();
     for (int col = 0; col < G; ++col) {
-      if (tid == 0) {
-        int piv = col;
-        double best = fabs(Jm[col * W + col]);
-        for (int r = col + 1; r < G; ++r) {
-          double v = fabs(Jm[r * W + col]);
-          if (v > best) { best = v; piv = r; }
-        }
-        s_piv = piv;
+      float best = -1.f;
+      int piv = col;
+      for (int r = col + lane; r < G; r += 32) {
+        float v = fabsf(Jm[r * W + col]);
+        if (v > best) { best = v; piv = r; }
       }
-      __syncthreads();
-      int piv = s_piv;
+      for (int o = 16; o > 0; o >>= 1) {
+        float ob = __shfl_down_sync(FULL, best, o);
+        int op = __shfl_down_sync(FULL, piv, o);
+        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+      }
+      piv = __shfl_sync(FULL, piv, 0);
       if (piv != col)
-        for (int c2 = col + tid; c2 <= G; c2 += nt) {
-          double t = Jm[col * W + c2];
+        for (int c2 = col + lane; c2 <= G; c2 += 32) {
+          float t = Jm[col * W + c2];
           Jm[col * W + c2] = Jm[piv * W + c2];
           Jm[piv * W + c2] = t;
         }
-      __syncthreads();
-      for (int r = col + 1 + tid; r < G; r += nt) d[r] = Jm[r * W + col] / Jm[col * W + col];
-      __syncthreads();
-      int rows = G - col - 1, cols = G - col;   // columns col+1 .. G
-      for (int idx = tid; idx < rows * cols; idx += nt) {
-        int r = col + 1 + idx / cols, c2 = col + 1 + idx % cols;
-        Jm[r * W + c2] -= d[r] * Jm[col * W + c2];
+      __syncwarp();
+      float rp = 1.f / Jm[col * W + col];
+      for (int r = col + 1 + lane; r < G; r += 32) {
+        float f = Jm[r * W + col] * rp;
+        for (int c2 = col + 1; c2 <= G; ++c2) Jm[r * W + c2] = fmaf(-f, Jm[col * W + c2], Jm[r * W + c2]);
       }
-      __syncthreads();
+      __syncwarp();
     }
-    if (tid == 0) {
-      for (int r = G - 1; r >= 0; --r) {
-        double acc = Jm[r * W + G];
-        for (int c2 = r + 1; c2 < G; ++c2) acc -= Jm[r * W + c2] * d[c2];
-        d[r] = acc / Jm[r * W + r];
-      }
-      double dmax = 0.0, umax = 0.0;
-      for (int t = 0; t < G; ++t) {
-        ph[t] += d[t];
-        dmax = fmax(dmax, fabs(d[t]));
-        umax = fmax(umax, fabs(ph[t]));
-      }
-      if (s_extra) s_stop = 1;
-      else if (dmax <= 1e-15 * (1.0 + umax)) s_extra = 1;
-      if (!(dmax == dmax)) s_stop = 1;
+    for (int r = G - 1; r >= 0; --r) {
+      float acc = 0.f;
+      for (int c2 = r + 1 + lane; c2 < G; c2 += 32) acc = fmaf(Jm[r * W + c2], d[c2], acc);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+      if (lane == 0) d[r] = (Jm[r * W + G] - acc) / Jm[r * W + r];
+      __syncwarp();
     }
-    __syncthreads();
-    if (s_stop) break;
+    float dmax = 0.f;
+    double umax = 0.0;
+    for (int t = lane; t < G; t += 32) {
+      double pn = ph[t] + (double)d[t];
+      ph[t] = pn;
+      dmax = fmaxf(dmax, fabsf(d[t]));
+      umax = fmax(umax, fabs(pn));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
+      umax = fmax(umax, __shfl_xor_sync(FULL, umax, o));
+    }
+    __syncwarp();
+    if (extra || !(dmax == dmax)) break;
+    if ((double)dmax <= 1e-15 * (1.0 + umax)) extra = true;
   }
-  for (int t = tid; t < G; t += nt) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
-  __syncthreads();
-  for (int t = tid; t < G; t += nt) {
+  for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
+  __syncwarp();
+  for (int t = lane; t < G; t += 32) {
     muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t) - 4.0 * kap[t]);
     C.phi[t] = ph[t];
     C.ka[t] = kap[t];
+    C.mu[t] = muv[t];
   }
-  __syncthreads();
-  for (int t = tid; t < G; t += nt) C.mu[t] = muv[t];
 }
 
 template <int SCH>
-__global__ void k_coarse_solve(Lev C, Coef k, const double* __restrict__ K3) {
-  coarse_solve_block<SCH>(C, k, K3);
+__global__ void k_coarse_solve(Lev C, Coef k, const float* __restrict__ K3f) {
+  coarse_solve_block<SCH>(C, k, K3f);
 }
 
 // ---------------------------------------------------------------------------

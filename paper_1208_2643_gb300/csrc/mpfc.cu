@@ -174,8 +174,8 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
     h *= 2.0;
   }
   int Gc = lev[L - 1].m * lev[L - 1].n;
-  double* K3a = c.take<double>((size_t)Gc * Gc);
-  double* K3b = c.take<double>((size_t)Gc * Gc);
+  float* K3a = c.take<float>((size_t)Gc * Gc);
+  float* K3b = c.take<float>((size_t)Gc * Gc);
   mpfc_fp32_carve(H, p, &c.off, base, L);
   mpfc_guess_carve(H, p, &c.off, base);
   if (H && base) {
@@ -272,7 +272,8 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
     }
     for (int s = 0; s < 2 && rc == MPFC_OK; ++s) {
       mpfc_build_K3(C, H->coef[s][H->nlev - 1], K3);
-      if ((e = cudaMemcpyAsync(H->K3[s], K3.data(), K3.size() * sizeof(double), cudaMemcpyHostToDevice, H->stream)) !=
+      std::vector<float> K3f(K3.begin(), K3.end());
+      if ((e = cudaMemcpyAsync(H->K3[s], K3f.data(), K3f.size() * sizeof(float), cudaMemcpyHostToDevice, H->stream)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(H->stream)) != cudaSuccess) {
         mpfc_set_cuda_error(e, "upload coarse matrix", __FILE__, __LINE__);
@@ -341,12 +342,12 @@ static void launch_smooth(const Lev& L, const Coef& k, int sweeps, cudaStream_t 
 
 static size_t coarse_smem(const Lev& C) {
   int G = C.m * C.n;
-  return sizeof(double) * ((size_t)G * (G + 1) + 8 * (size_t)G);
+  return sizeof(double) * 7 * (size_t)G + sizeof(float) * ((size_t)G * (G + 1) + (size_t)G);
 }
 
 template <int SCH>
 static void launch_coarse(mpfc_s* H, const Lev& C, const Coef& k, cudaStream_t s) {
-  k_coarse_solve<SCH><<<1, 256, coarse_smem(C), s>>>(C, k, H->K3[SCH - 1]);
+  k_coarse_solve<SCH><<<1, 32, coarse_smem(C), s>>>(C, k, H->K3[SCH - 1]);
 }
 
 template <int SCH>

@@ -42,14 +42,52 @@ struct Coef {
   int pad;
 };
 
+// Conversions between binary64 and binary32 done with integer operations on the IEEE
+// 754 bit fields (sign, biased exponent, significand), so that they run on the integer
+// pipes instead of GB300's narrow FP64 pipe.  Valid for values whose magnitude lies in
+// the normal binary32 range [2^-126, 2^128); the callers use them only there (the
+// tests check them against the hardware conversions on that range).
+//   f64_to_f32_trunc: significand truncated to 23 bits (relative error < 2^-23);
+//   f64_to_f32_rn:    rounded to nearest, ties to even (equal to the IEEE conversion);
+//   f32_to_f64:       exact.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned int hi = (unsigned int)(b >> 32);
+  unsigned int e = ((hi >> 20) & 0x7FFu) - 1023u + 127u;
+  unsigned int f = (hi & 0x80000000u) | (e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFull);
+  return __uint_as_float(f);
+}
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  if (mag == 0ull) return __uint_as_float(sign);
+  // binary32 magnitude bits with the exponent re-biased and the significand cut to 23
+  // bits, then round to nearest even on the 29 dropped bits (a carry into the exponent
+  // field is the correct result of rounding up a significand of all ones)
+  unsigned long long keep = (mag >> 29) - ((unsigned long long)(1023 - 127) << 23);
+  unsigned long long rest = mag & 0x1FFFFFFFull;
+  unsigned long long half = 0x10000000ull;
+  if (rest > half || (rest == half && (keep & 1ull))) keep += 1ull;
+  return __uint_as_float(sign | (unsigned int)keep);
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+  unsigned int u = __float_as_uint(f);
+  unsigned int mag = u & 0x7FFFFFFFu;
+  if (mag == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+  unsigned long long e = (unsigned long long)(((mag >> 23) & 0xFFu) - 127u + 1023u);
+  unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) | (e << 52) |
+                         ((unsigned long long)(mag & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
 // Reciprocal by one Newton-Raphson step (r <- r + r (1 - x r), Newton's method for
-// f(r) = 1/r - x) from the correctly rounded single-precision reciprocal of x.  The
-// seed's relative error is below 2^-23 (including the rounding of x to single), and
-// one step squares it: |r x - 1| < 2^-45 for x in the normal single range.  The
-// smoother's cell solve needs no more: its error only perturbs an iterate, not the
-// fixed point.
+// f(r) = 1/r - x) from the correctly rounded single-precision reciprocal of x rounded
+// down to single.  The seed's relative error is below 2^-22.4; one step squares it:
+// |r x - 1| < 2^-44 for x in the normal single range.  The smoother's cell solve needs
+// no more: its error only perturbs an iterate, not the fixed point.
 __device__ __forceinline__ double rcp_nr(double x) {
-  double r = (double)__frcp_rn(__double2float_rn(x));
+  double r = f32_to_f64(__frcp_rn(f64_to_f32_trunc(x)));
   return fma(r, fma(-x, r, 1.0), r);
 }
 

@@ -46,7 +46,7 @@ struct mpfc_s {
   mpfc::Ctl* ctl = nullptr;
   double* partials = nullptr;
   mpfc::StepRecord* info = nullptr;
-  double* K3[2] = {nullptr, nullptr};
+  float* K3[2] = {nullptr, nullptr};    // I - c theta L^3 on the coarsest grid (FP32), per scheme
   double* px[mpfc::kMaxLevels];
   double* pf[mpfc::kMaxLevels];
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};

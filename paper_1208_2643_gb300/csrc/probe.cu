@@ -57,3 +57,23 @@ extern "C" int mpfc_probe_rcp(const double* d_x, double* d_out, int n, void* cud
   k_rcp<<<(n + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(d_x, d_out, n);
   return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
 }
+
+namespace {
+__global__ void k_convert(const double* __restrict__ x, float* __restrict__ rn, float* __restrict__ tr,
+                          double* __restrict__ back, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    rn[i] = mpfc::f64_to_f32_rn(x[i]);
+    tr[i] = mpfc::f64_to_f32_trunc(x[i]);
+    back[i] = mpfc::f32_to_f64(rn[i]);
+  }
+}
+}  // namespace
+
+extern "C" int mpfc_probe_convert(const double* d_x, float* d_rn, float* d_trunc, double* d_back, int n,
+                                  void* cuda_stream) {
+  if (!d_x || !d_rn || !d_trunc || !d_back || n < 0) return MPFC_ERR_INVALID;
+  if (n == 0) return MPFC_OK;
+  k_convert<<<(n + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(d_x, d_rn, d_trunc, d_back, n);
+  return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
+}

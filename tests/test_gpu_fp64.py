@@ -347,3 +347,32 @@ def test_smoother_reciprocal_error_bound(mp):
     assert lib.mpfc_probe_rcp(xd.data_ptr(), y.data_ptr(), x.size, None) == 0
     rel = np.abs(host(y) * x - 1.0)
     assert rel.max() < 2.0 ** -44, rel.max()
+
+
+def test_integer_pipe_conversions_match_ieee(mp):
+    """binary64 -> binary32 round-to-nearest-even, truncation and exact widening, done on
+    the integer pipes, against the IEEE conversions (numpy) over the normal range."""
+    import ctypes
+    lib = mp.load()
+    lib.mpfc_probe_convert.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_void_p]
+    rng = np.random.default_rng(5)
+    mags = 2.0 ** rng.uniform(-120, 120, 20000)
+    x = np.concatenate([mags * rng.choice([-1, 1], mags.size), [0.0, -0.0, 1.0, -1.5, 3.4e38, 1.2e-38],
+                        np.nextafter(np.float32(1.0), np.float32(2.0)).astype(np.float64) + np.array([1e-12, -1e-12, 0])])
+    # exact ties: binary32 midpoints
+    f = rng.uniform(1, 2, 1000).astype(np.float32).astype(np.float64)
+    x = np.concatenate([x, f + 2.0 ** -24, f - 2.0 ** -24])
+    xd = dev(x)
+    rn = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    tr = torch.empty_like(rn)
+    back = torch.empty_like(xd)
+    assert lib.mpfc_probe_convert(xd.data_ptr(), rn.data_ptr(), tr.data_ptr(), back.data_ptr(), x.size, None) == 0
+    torch.cuda.synchronize()
+    ref = x.astype(np.float32)
+    got = rn.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert np.array_equal(back.cpu().numpy(), ref.astype(np.float64))
+    t = tr.cpu().numpy().astype(np.float64)
+    nz = x != 0
+    assert np.all(np.abs(t[nz] - x[nz]) <= np.abs(x[nz]) * 2.0 ** -23)
+    assert np.all(np.abs(t[nz]) <= np.abs(x[nz]))
