@@ -138,11 +138,14 @@ def traffic_for(kernel, size):
     ent = data.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, ent["source"])
+    srcs = ent["source"] if isinstance(ent["source"], list) else [ent["source"]]
+    h = hashlib.sha256()
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        for src in srcs:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
     except Exception:
         return None
+    digest = h.hexdigest()
     if digest != ent.get("sha256"):
         return None
     return ent["bytes_per_launch_per_cell"] * size * size

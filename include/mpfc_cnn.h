@@ -78,6 +78,17 @@ int mpfc_cnn_mse(const float* yhat, int yhat_stride, const float* y, long long n
 int mpfc_cnn_adam(float* param, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
                   float eps, int t, void* stream);
 
+/* Chooses the tensor-core path of the 32 -> 32 channel convolutions (forward and data
+ * gradient, image width a multiple of 128): 1 = tcgen05 MMAs with the accumulator in
+ * tensor memory (default), 0 = warp-level mma.sync.  Other shapes always use mma.sync.
+ * Process-wide; applies to convolutions launched, and step graphs captured, afterwards. */
+int mpfc_cnn_set_tensor_path(int use_tcgen05);
+
+/* Reports (and clears) whether a tcgen05 convolution gave up waiting for its MMAs
+ * since the last call: MPFC_OK if none did, MPFC_ERR_NOT_CONVERGED if one did (its
+ * output is then incomplete), MPFC_ERR_CUDA on a CUDA error.  Synchronous. */
+int mpfc_cnn_tensor_path_status(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,11 @@
 #include "../../include/mpfc_cnn.h"
 #include "mpfc_internal.h"
 
+bool mpfc_cnn_tc_eligible(int cin_p, int cout_p, int W, int mode);
+int mpfc_cnn_conv_tc(const void* x, int B, int H, int W, const void* wk, const float* bias, int cout, int cout_p,
+                     int mode, void* y_bf16, float* y_f32, float* z_f32, double* phi0, double scale,
+                     cudaStream_t s);
+
 namespace {
 
 constexpr int kTW = 32, kTH = 4;          // output tile: 32 x 4 pixels, 4 warps (one row each)
@@ -299,6 +304,9 @@ size_t conv_smem(int cin_p, int cout_p, int kpad) {
 }
 
 int launch_conv(const ConvArgs& A, cudaStream_t s) {
+  if (mpfc_cnn_tc_eligible(A.cin_p, A.cout_p, A.W, A.mode))
+    return mpfc_cnn_conv_tc(A.x, A.B, A.H, A.W, A.wk, A.bias, A.cout, A.cout_p, A.mode, A.y_bf16, A.y_f32, A.z_f32,
+                            A.phi0, A.scale, s);
   long long ntiles = (long long)((A.W + kTW - 1) / kTW) * ((A.H + kTH - 1) / kTH) * A.B;
   int grid = (int)(ntiles < 152 * 6 ? ntiles : 152 * 6);
   size_t sm = conv_smem(A.cin_p, A.cout_p, A.kpad);

@@ -44,6 +44,8 @@ def _lib():
     lib.mpfc_cnn_adam.argtypes = [V, V, V, V, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                   ctypes.c_float, ctypes.c_int, V]
     lib.mpfc_set_guess_model.argtypes = [V, V, ctypes.c_size_t]
+    lib.mpfc_cnn_set_tensor_path.argtypes = [ctypes.c_int]
+    lib.mpfc_cnn_tensor_path_status.argtypes = []
     return lib
 
 

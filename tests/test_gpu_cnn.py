@@ -166,3 +166,89 @@ def test_learned_guess_gain(G):
         assert all(i["status"] == 0 and i["res"] <= 1e-10 for i in infos)
         res[gs] = (np.mean([i["res0"] for i in infos]), np.mean([i["cycles"] for i in infos]))
     assert res[mpfc.MPFC_GUESS_LEARNED][0] < 0.8 * res[mpfc.MPFC_GUESS_EXTRAP][0], res
+
+
+@pytest.fixture
+def tensor_path(G):
+    """Yields a setter of the 32 -> 32 convolutions' tensor-core path; restores tcgen05."""
+    lib = G._lib()
+    yield lambda use_tc: lib.mpfc_cnn_set_tensor_path(use_tc)
+    lib.mpfc_cnn_set_tensor_path(1)
+
+
+@pytest.mark.parametrize("H,W", [(3, 128), (5, 256)])
+@pytest.mark.parametrize("use_tc", [1, 0])
+def test_conv32_both_tensor_paths_match_oracle(G, tensor_path, use_tc, H, W):
+    """Forward (linear, and GELU with the saved pre-activation) and data gradient of a
+    32 -> 32 layer on widths that take the tcgen05 kernel, on both tensor-core paths;
+    fewer real output channels (cout 20) than padded ones check the zero fill."""
+    from oracle import cnn
+    lib = G._lib()
+    tensor_path(use_tc)
+    rng = np.random.default_rng(7)
+    B = 2
+    s = torch.cuda.current_stream().cuda_stream
+    xr, xd = bf16(rng.normal(size=(B, H, W, 32)))
+    for co in (32, 20):
+        w = rng.normal(scale=0.2, size=(9, 32, co)).astype(np.float32)
+        wr = torch.from_numpy(w).bfloat16().float().double().numpy()
+        bias = rng.normal(size=co).astype(np.float32)
+        wk = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+        assert lib.mpfc_cnn_pack_weights(torch.from_numpy(w).cuda().data_ptr(), 32, co, 32, 32, 0, wk.data_ptr(),
+                                         s) == 0
+        bd = torch.from_numpy(bias).cuda()
+        y = torch.full((B, H, W, 32), 7.0, dtype=torch.float32, device="cuda")
+        assert lib.mpfc_cnn_conv_forward(xd.data_ptr(), B, H, W, 32, wk.data_ptr(), bd.data_ptr(), co, 32, 1, None,
+                                         y.data_ptr(), None, s) == 0
+        yb = torch.empty((B, H, W, 32), dtype=torch.bfloat16, device="cuda")
+        z = torch.empty((B, H, W, 32), dtype=torch.float32, device="cuda")
+        assert lib.mpfc_cnn_conv_forward(xd.data_ptr(), B, H, W, 32, wk.data_ptr(), bd.data_ptr(), co, 32, 0,
+                                         yb.data_ptr(), None, z.data_ptr(), s) == 0
+        torch.cuda.synchronize()
+        assert lib.mpfc_cnn_tensor_path_status() == 0
+        ref = cnn.conv3x3(xr, wr, bias.astype(np.float64))
+        got = y.cpu().numpy()
+        assert rel(got[..., :co], ref) < 1e-4
+        assert np.all(got[..., co:] == 0)
+        assert rel(z.cpu().numpy()[..., :co], ref) < 1e-4
+        gb = yb.float().cpu().numpy()
+        assert rel(gb[..., :co], cnn.gelu(ref)) < 1e-2
+        assert np.all(gb[..., co:] == 0)
+    # data gradient through a 32 -> 32 layer
+    dzr, dzd = bf16(rng.normal(size=(B, H, W, 32)))
+    w = rng.normal(scale=0.2, size=(9, 32, 32)).astype(np.float32)
+    wr = torch.from_numpy(w).bfloat16().float().double().numpy()
+    wkt = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+    assert lib.mpfc_cnn_pack_weights(torch.from_numpy(w).cuda().data_ptr(), 32, 32, 32, 32, 1, wkt.data_ptr(),
+                                     s) == 0
+    zp = rng.normal(size=(B, H, W, 32)).astype(np.float32)
+    zpd = torch.from_numpy(zp).cuda()
+    ob = torch.empty((B, H, W, 32), dtype=torch.bfloat16, device="cuda")
+    of = torch.empty((B, H, W, 32), dtype=torch.float32, device="cuda")
+    assert lib.mpfc_cnn_conv_backward_data(dzd.data_ptr(), B, H, W, 32, wkt.data_ptr(), 32, 32, zpd.data_ptr(),
+                                           ob.data_ptr(), of.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    assert lib.mpfc_cnn_tensor_path_status() == 0
+    ref = cnn.conv3x3_grad_input(dzr, wr) * cnn.gelu_grad(zp.astype(np.float64))
+    assert rel(of.cpu().numpy(), ref) < 1e-4
+    assert rel(ob.float().cpu().numpy(), ref) < 1e-2
+
+
+def test_learned_guess_same_on_both_tensor_paths(G, tensor_path):
+    """The packaged 256 x 256 model gives the same initial residual (to FP32 accumulation
+    order) whichever tensor-core path runs its 32 -> 32 layers."""
+    from paper_1208_2643_gb300 import inputs, mpfc
+    m = 256
+    phi0 = inputs.noise_field(m, m, 0.08, 0.05, 5)
+    out = {}
+    for use_tc in (1, 0):
+        tensor_path(use_tc)
+        g = mpfc.Solver(mpfc.default_params(m=m, n=m, guess=mpfc.MPFC_GUESS_LEARNED))
+        G.attach(g, G.load())
+        g.set_state(phi0)
+        g.step(1, 3)
+        infos = g.step(1, 3)
+        assert all(i["status"] == 0 for i in infos)
+        out[use_tc] = np.array([i["res0"] for i in infos])
+        assert G._lib().mpfc_cnn_tensor_path_status() == 0
+    np.testing.assert_allclose(out[1], out[0], rtol=1e-3)
