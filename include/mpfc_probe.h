@@ -29,6 +29,17 @@ int mpfc_probe_rcp(const double* d_x, double* d_out, int n, void* cuda_stream);
  * For tests against the hardware conversions.  Asynchronous on `cuda_stream`. */
 int mpfc_probe_convert(const double* d_x, float* d_rn, float* d_trunc, double* d_back, int n, void* cuda_stream);
 
+/* Evaluates the convolution kernels' GELU and its derivative (erf by the rational
+ * approximation of Abramowitz & Stegun 7.1.26, absolute error <= 1.5e-7) on n device
+ * floats: d_g = GELU(z), d_dg = GELU'(z).  For tests against the exact functions.
+ * Asynchronous on `cuda_stream`. */
+int mpfc_probe_gelu(const float* d_z, float* d_g, float* d_dg, int n, void* cuda_stream);
+
+/* The same GELU in the 8-wide form the tcgen05 convolution uses (one reciprocal shared
+ * by eight values): d_g[i] = GELU(d_z[i]) for n device floats, evaluated in groups of
+ * eight consecutive values.  Asynchronous on `cuda_stream`. */
+int mpfc_probe_gelu8(const float* d_z, float* d_g, int n, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@
 
 #include "../../include/mpfc.h"
 #include "../../include/mpfc_cnn.h"
+#include "cnn_math.cuh"
 #include "mpfc_internal.h"
 
 bool mpfc_cnn_tc_eligible(int cin_p, int cout_p, int W, int mode);
@@ -27,11 +28,8 @@ constexpr int kMaxCin = 32, kMaxCout = 32;
 
 __device__ __forceinline__ int wrapi(int i, int n) { return ((i % n) + n) % n; }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-  // d/dz [z Phi(z)] = Phi(z) + z phi(z)
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
+__device__ __forceinline__ float gelu_f(float z) { return mpfc_cnn_math::gelu(z); }
+__device__ __forceinline__ float gelu_grad(float z) { return mpfc_cnn_math::gelu_grad(z); }
 
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
   asm volatile(

@@ -1,41 +1,93 @@
 // Periodic 3x3 convolutions with 32 input channels on the 5th-generation tensor cores
-// (tcgen05): implicit GEMM with M = 128 output pixels (one row segment of one image),
-// N = 32 (or 16) output channels, K = 9 taps x 32 input channels; BF16 operands in
-// shared memory, FP32 accumulator in tensor memory (TMEM).
+// (tcgen05): implicit GEMM over M = 128 output pixels (one row segment of one image)
+// and K = 9 taps x 32 input channels, BF16 operands in shared memory, FP32
+// accumulators in tensor memory (TMEM).
 //
-// Shared-memory operands use the canonical K-major layout without swizzle: a "core
-// matrix" is 8 rows x 16 bytes (8 bf16 along K), rows 16 bytes apart, so the rows of a
-// whole operand sit at a uniform 16-byte stride and a tap's pixel shift dx is just a
-// 16*dx-byte offset of the descriptor's start address.  Input rows y-1, y, y+1 of the
-// tile (pixels x0-1 .. x0+128, periodic) are staged as [row][8-channel chunk][pixel]
-// 16-byte units; weights as [tap][chunk][out channel] 16-byte units.  One thread
-// issues the 18 MMAs (9 taps x 2 K-steps of 16) and commits them to an mbarrier.
+// Row-stacked weights: input row r contributes to output rows r+1, r, r-1 through the
+// weight taps dy = 0, 1, 2.  The B operand stacks, for each dx and 16-channel K-step,
+// the three dy blocks of NB output channels (NB = 32, or 16 for the one-channel guess
+// layer) along N, so one MMA of N = 3 NB applies an input plane to all three output
+// rows at once: 6 MMAs per input row instead of 18 per output row, each reading the
+// 128-row A window once for three times the work.  Output rows accumulate in a ring
+// of kBlocks TMEM blocks of NB columns; the epilogue zeroes a block after reading it,
+// so every MMA accumulates.  An MMA whose output rows would wrap the ring is split in
+// two, and at the ends of a run only the rows inside the run are computed.
 //
-// Per tile the CTA overlaps the MMAs with the global loads of the next tile's input
-// (held in registers), then reads the accumulator (tcgen05.ld, one pixel per thread),
-// applies the epilogue, and writes the tile's outputs through a swizzled shared-memory
-// stage (the A operand's space, free once the MMAs completed) so that the global
-// stores are contiguous: a tile's outputs are one contiguous block of NHWC memory.
+// A operand: the K-major layout with 64-byte swizzle.  A pixel (32 channels, 64 bytes)
+// is one row; 16-byte chunk c of the row at shared address a is stored at chunk
+// c ^ ((a >> 7) & 3), the pattern TMA applies when it writes a 64-byte-swizzled box
+// (the MMA unit derives the pattern from the same absolute address bits).  An input
+// row segment (pixels x0-1 .. x0+128 of one image row, periodic) is one "plane" of 130
+// consecutive pixel rows; a tap (dy, dx) is the 128-row window starting at pixel dx of
+// the plane of input row y-1+dy, i.e. a 64*dx-byte change of the descriptor's start
+// address, and the two K-steps of 16 channels are a further 32-byte offset.  The
+// weights (B) are staged once per CTA in the same 64-byte-swizzled K-major form, one
+// row of 32 input channels per (dx, stacked output channel).
+//
+// Work order: the tiles of an image are numbered strip by strip (a strip = the tiles
+// of one 128-pixel column range, y = 0 .. H-1) and each CTA takes one contiguous range
+// of that order.  Consecutive tiles of a run down a strip share two of their three
+// input planes, so the planes live in a ring of kSlots shared-memory slots and each
+// tile after the first of a run loads only its new row y+1: one 8 KB TMA box per tile.
+//
+// Warp roles of the persistent kernel (one CTA per SM):
+//   warp 0      producer: walks the CTA's plane loads in order; per load one TMA
+//               tensor load (the 128 body pixels, 8 KB contiguous in global memory)
+//               and the two periodic halo pixels with cp.async, completing on the
+//               slot's full barrier;
+//   warp 1      one thread walks the input rows: per row the 6 MMAs (3 dx x 2 K-steps)
+//               into the ring blocks of the output rows it touches, then commits them
+//               to the barriers that free the plane and publish the output row the
+//               row completes;
+//   warps 2..17 epilogue, two groups of 8 warps on alternate tiles: warp w reads
+//               TMEM lanes 32 (w % 4) .. +31 (one pixel per thread) and 16 of the
+//               block's columns, zeroes them, applies the epilogue, and stages the
+//               tile's outputs in shared memory in their global (NHWC) order; one
+//               thread of the group writes the tile back with bulk asynchronous
+//               copies (a tile's outputs are one contiguous block).
+// All mbarrier waits are bounded; a wait that gives up raises an abort flag that
+// every role checks, and sets the device flag read by mpfc_cnn_tensor_path_status.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/mpfc.h"
 #include "../../include/mpfc_cnn.h"
+#include "cnn_math.cuh"
 #include "mpfc_internal.h"
 
 namespace {
 
-constexpr int kTM = 128;                 // pixels per tile (TMEM lanes)
+constexpr int kTM = 128;                    // pixels per tile (TMEM lanes)
 constexpr int kCin = 32;
-constexpr int kChunks = kCin / 8;        // 8-channel (16-byte) chunks of a pixel
-constexpr int kNPix = 138;               // staged pixels per (row, chunk); 130 used, the pad spreads banks
-constexpr int kUnits = 3 * 130 * kChunks;             // 16-byte units staged per tile (1560)
-constexpr int kThreads = 128;
-constexpr int kPerThread = (kUnits + kThreads - 1) / kThreads;   // 13
-constexpr int kABytes = 3 * kChunks * kNPix * 16;     // 26496
-constexpr int kBBytesMax = 9 * kChunks * 32 * 16;     // 18432
-constexpr int kSmem = kABytes + kBBytesMax + 32 * 4 + 64;
-static_assert(kTM * 32 * 4 + kTM * 32 * 2 <= kABytes, "output stage must fit in the A operand space");
+constexpr int kChunks = kCin / 8;           // 8-channel (16-byte) chunks of a pixel
+constexpr int kPixBytes = kCin * 2;         // one pixel row of the A operand
+constexpr int kSlotBytes = 9 * 1024;        // one plane slot (130 pixels used)
+constexpr int kPlaneLead = 1024 - kPixBytes;   // pixel p = 1 (first body pixel) lands 1024-byte aligned
+constexpr int kSlots = 12;                  // plane ring: 3 in use by a tile + 9 loads of look-ahead
+constexpr int kTxBytes = kTM * kPixBytes;   // TMA bytes per plane load
+constexpr int kHaloLanes = 2 * kChunks;     // (side, chunk) cp.async copies per plane
+constexpr int kBBytes = 3 * 96 * kPixBytes;     // 3 dx x 96 stacked output rows x 64 bytes
+constexpr int kBlocks = 16;                 // TMEM ring of output-row accumulators
+constexpr int kOutBf16 = kTM * 32 * 2, kOutF32 = kTM * 32 * 4;
+constexpr int kOutBytes = kOutBf16 + kOutF32;
+constexpr int kEpiWarps = 16;               // 4 lane quarters x 4 groups of 8 columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+// shared-memory map (offsets from a 1024-byte aligned base)
+constexpr int kOffA = 0;
+constexpr int kOffB = kOffA + kSlots * kSlotBytes + 1024;   // the last slot's halo pixel spills 64 bytes
+constexpr int kOffOut = kOffB + kBBytes;
+constexpr int kOffBias = kOffOut + 2 * kOutBytes;
+constexpr int kOffBar = kOffBias + 32 * 4;  // full[kSlots], empty[kSlots], accfull[kBlocks], accempty[kBlocks]
+constexpr int kOffMisc = kOffBar + (2 * kSlots + 2 * kBlocks) * 8;   // TMEM address, abort flag
+constexpr int kSmem = kOffMisc + 16 + 1024;
+static_assert(kPlaneLead + 130 * kPixBytes <= kSlotBytes + kPlaneLead, "plane layout");
+static_assert(kSlotBytes % 1024 == 0 && kOffB % 1024 == 0 && kOffOut % 1024 == 0, "alignment");
+static_assert(kSmem <= 227 * 1024, "shared memory");
+constexpr long long kSpinLimit = 200000000ll;   // clock cycles (about 0.1 s) per wait
 
 // Epilogue modes (same meaning as the mma.sync kernel's).
 constexpr int kModeGelu = 0, kModeLinear = 1, kModeGeluGrad = 2, kModeGuess = 3;
@@ -43,26 +95,22 @@ constexpr int kModeGelu = 0, kModeLinear = 1, kModeGeluGrad = 2, kModeGuess = 3;
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor (SM100 format): start address, leading- and
-// stride-dimension byte offsets (all >> 4), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// stride-dimension byte offsets (all >> 4), descriptor version 1, layout type
+// (0 = no swizzle, 4 = 64-byte swizzle).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1u << 46;
+  d |= (uint64_t)(layout & 7u) << 61;
   return d;
 }
 
 // Instruction descriptor of kind::f16: D in F32, A and B in BF16, both K-major,
 // N >> 3 at bit 17, M >> 4 at bit 24.
-template <int N>
-__device__ __forceinline__ uint32_t idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
-}
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+__device__ __forceinline__ uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -70,8 +118,46 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Set to 1 by a CTA whose wait gave up; read and cleared by mpfc_cnn_tensor_path_status.
+__device__ int g_tc_fail = 0;
+
+// Bounded wait on an mbarrier phase; false if the CTA aborts (this wait timed out, or
+// another role's did).
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (true) {
+    if (try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kSpinLimit) {
+      *abort_flag = 1;
+      atomicExch(&g_tc_fail, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 struct TcArgs {
-  const __nv_bfloat16* x;   // [B][H][W][32]
+  const __nv_bfloat16* x;   // [B][H][W][32] (also described by the tensor map)
   const __nv_bfloat16* wk;  // [cout_p][288] packed (k = tap * 32 + c)
   const float* bias;        // [cout] (nullable)
   int B, H, W, cout, cout_p, mode;
@@ -82,233 +168,348 @@ struct TcArgs {
   double scale;
 };
 
-// Set to 1 by a CTA whose MMA-completion wait gave up; read and cleared by
-// mpfc_cnn_tensor_path_status.
-__device__ int g_tc_fail = 0;
-
-// Global loads of one tile's input units into registers (unit t: row r, pixel p, chunk q).
-__device__ __forceinline__ void load_tile(const uint4* __restrict__ xg, const TcArgs& A, long long tile, int tiles_x,
-                                          uint4 (&v)[kPerThread]) {
-  const int b = (int)(tile / ((long long)A.H * tiles_x));
-  const int rem = (int)(tile % ((long long)A.H * tiles_x));
-  const int y = rem / tiles_x, x0 = (rem % tiles_x) * kTM;
-#pragma unroll
-  for (int i = 0; i < kPerThread; ++i) {
-    const int t = threadIdx.x + i * kThreads;
-    if (t < kUnits) {
-      const int q = t & 3, rp = t >> 2, r = rp / 130, p = rp - r * 130;
-      int gy = y + r - 1;
-      gy = gy < 0 ? gy + A.H : (gy >= A.H ? gy - A.H : gy);
-      int gx = x0 + p - 1;
-      gx = gx < 0 ? gx + A.W : (gx >= A.W ? gx - A.W : gx);
-      v[i] = __ldg(&xg[(((size_t)b * A.H + gy) * A.W + gx) * kChunks + q]);
-    }
+// Tile t of the strip-major order -> image b, tile row y, column offset x0.
+struct TileOrder {
+  int H, tiles_x;
+  __device__ __forceinline__ void decode(int t, int& b, int& y, int& x0) const {
+    const int per_img = H * tiles_x;
+    b = t / per_img;
+    const int rem = t - b * per_img;
+    const int strip = rem / H;
+    y = rem - strip * H;
+    x0 = strip * kTM;
   }
-}
+  // whether tile t + 1 continues t's run down the same strip
+  __device__ __forceinline__ bool continues(int t) const { return (t + 1) % H != 0; }
+};
 
-__device__ __forceinline__ void store_tile(unsigned char* As, const uint4 (&v)[kPerThread]) {
-#pragma unroll
-  for (int i = 0; i < kPerThread; ++i) {
-    const int t = threadIdx.x + i * kThreads;
-    if (t < kUnits) {
-      const int q = t & 3, rp = t >> 2, r = rp / 130, p = rp - r * 130;
-      reinterpret_cast<uint4*>(As)[(r * kChunks + q) * kNPix + p] = v[i];
-    }
-  }
-}
-
-// Output stage inside the A space: fp32 [128 px][8 chunks of 4] then bf16 [128 px][4
-// chunks of 8]; chunk j of pixel p sits at position j ^ (p & 7) (fp32) or
-// j ^ ((p >> 1) & 3) (bf16) so that the per-pixel accesses of a warp hit distinct banks.
-constexpr int kStageF32 = 0, kStageBf16 = kTM * 32 * 4;
-__device__ __forceinline__ int f32_slot(int p, int j) { return p * 8 + (j ^ (p & 7)); }
-__device__ __forceinline__ int bf16_slot(int p, int j) { return p * 4 + (j ^ ((p >> 1) & 3)); }
-
-template <int N>
-__global__ void __launch_bounds__(kThreads, 4) k_conv3x3_tc(TcArgs A) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* As = smem;
-  unsigned char* Bs = smem + kABytes;
-  float* bias_s = reinterpret_cast<float*>(smem + kABytes + kBBytesMax);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kABytes + kBBytesMax + 32 * 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kABytes + kBBytesMax + 32 * 4 + 8);
+template <int NB>
+__global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constant__ CUtensorMap tmap, TcArgs A) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const uint32_t sbase = smem_addr(smem);
+  float* bias_s = reinterpret_cast<float*>(smem + kOffBias);
+  const uint32_t bar0 = sbase + kOffBar;
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (kSlots + s); };
+  auto accfull = [&](int j) { return bar0 + 8u * (2 * kSlots + j); };
+  auto accempty = [&](int j) { return bar0 + 8u * (2 * kSlots + kBlocks + j); };
+  auto plane = [&](int slot) { return sbase + kOffA + (uint32_t)(slot * kSlotBytes + kPlaneLead); };   // pixel 0
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffMisc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kOffMisc + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // TMEM: 32 columns (the FP32 accumulator of 128 x N, N <= 32)
-  if (warp == 0) {
+  if (warp == 1) {   // TMEM: the ring of kBlocks output-row blocks of NB columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                 "r"(32));
+                 "r"(kBlocks * NB));   // the same count is freed at the end
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(1));
+    for (int s = 0; s < kSlots; ++s) {
+      bar_init(full(s), 1 + kHaloLanes);   // lane 0's expect_tx arrival + the halo cp.async arrivals
+      bar_init(empty(s), 1);
+    }
+    for (int j = 0; j < kBlocks; ++j) {
+      bar_init(accfull(j), 1);
+      bar_init(accempty(j), kEpiWarps / 2);   // the 8 warps of the group that reads the block
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
   }
   if (tid < 32) bias_s[tid] = (A.bias && tid < A.cout) ? A.bias[tid] : 0.f;
-  // weights: unit (tap, q, n) = 8 channels of output row n; rows past cout_p are zero
+  // stacked weights, K-major with 64-byte swizzle like A: row (dx, n), n = sb NB + co,
+  // holds the 32 input channels of tap (dy = 2 - sb, dx) for output channel co (zero
+  // past cout_p); its 16-byte chunk cc sits at chunk cc ^ ((row address >> 7) & 3)
   const uint4* wg = reinterpret_cast<const uint4*>(A.wk);
-  for (int t = tid; t < 9 * kChunks * N; t += kThreads) {
-    const int n = t % N, tq = t / N, tap = tq / kChunks, q = tq % kChunks;
+  for (int t = tid; t < 3 * 3 * NB * kChunks; t += kThreads) {
+    const int cc = t & 3, row = t >> 2, dx = row / (3 * NB), n = row % (3 * NB);
+    const int sb = n / NB, co = n % NB, tap = (2 - sb) * 3 + dx;
     uint4 w = make_uint4(0u, 0u, 0u, 0u);
-    if (n < A.cout_p) w = wg[(size_t)n * (9 * kCin / 8) + tap * kChunks + q];
-    reinterpret_cast<uint4*>(Bs)[t] = w;
+    if (co < A.cout_p) w = wg[(size_t)co * (9 * kCin / 8) + tap * kChunks + cc];
+    const uint32_t ra = (uint32_t)(kOffB + row * kPixBytes);   // kOffB is 1024-byte aligned, as is sbase
+    *reinterpret_cast<uint4*>(smem + ra + ((cc ^ ((ra >> 7) & 3)) << 4)) = w;
   }
+  asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
+  if (warp >= 2 && warp < 10 && ((warp - 2) >> 2) * 16 < NB) {
+    // zero the ring: warp w of the first epilogue group owns lanes 32 (w % 4).. and the
+    // 16 columns of half (w - 2) / 4 of every block
+    const uint32_t zero = 0u;
+    for (int j = 0; j < kBlocks; ++j) {
+      const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(j * NB + ((warp - 2) >> 2) * 16);
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+          "r"(zero)
+          : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
 
-  const int tiles_x = A.W / kTM;
-  const long long ntiles = (long long)A.B * A.H * tiles_x;
-  const uint4* xg = reinterpret_cast<const uint4*>(A.x);
-  uint4 v[kPerThread];
-  if (blockIdx.x < ntiles) load_tile(xg, A, blockIdx.x, tiles_x, v);
-  uint32_t phase = 0;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int b = (int)(tile / ((long long)A.H * tiles_x));
-    const int rem = (int)(tile % ((long long)A.H * tiles_x));
-    const int y = rem / tiles_x, x0 = (rem % tiles_x) * kTM;
-    const size_t pix0 = ((size_t)b * A.H + y) * A.W + x0;
-    store_tile(As, v);
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
-      int accum = 0;
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const uint64_t ad = make_desc(a0 + (uint32_t)(((dy * kChunks + 2 * kk) * kNPix + dx) * 16), kNPix * 16, 128);
-          const uint64_t bd = make_desc(b0 + (uint32_t)(((tap * kChunks + 2 * kk) * N) * 16), N * 16, 128);
+  const TileOrder order{A.H, A.W / kTM};
+  const int ntiles = A.B * A.H * order.tiles_x;   // the host keeps this below 2^30
+  const int t_begin = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+  const int t_end = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    // Plane loads in order: a run's first tile loads rows y-1, y, y+1, every later tile
+    // of the run row y+1; load k goes to slot k % kSlots once the load kSlots earlier
+    // has been released.  Lanes 0..7 copy the two periodic halo pixels (side, chunk)
+    // with cp.async, completing on the slot's full barrier; lane 0 adds the TMA box.
+    // Nothing here waits on memory, so the producer runs ahead by the whole ring.
+    const char* xg = reinterpret_cast<const char*>(A.x);
+    const int hside = lane >> 2, hq = lane & 3;
+    int k = 0;
+    for (int t = t_begin; t < t_end; ++t) {
+      int b, y, x0;
+      order.decode(t, b, y, x0);
+      const bool first = t == t_begin || !order.continues(t - 1);
+      for (int r = first ? 0 : 2; r < 3; ++r, ++k) {
+        const int s = k % kSlots, use = k / kSlots;
+        bool ok = use == 0 || wait_bar(empty(s), (uint32_t)((use - 1) & 1), abort_flag);
+        if (!__all_sync(0xffffffffu, ok)) break;
+        int gy = y + r - 1;
+        gy = gy < 0 ? gy + A.H : (gy >= A.H ? gy - A.H : gy);
+        const uint32_t pl = plane(s);
+        if (lane < kHaloLanes) {
+          const int gx = hside ? (x0 + kTM == A.W ? 0 : x0 + kTM) : (x0 == 0 ? A.W - 1 : x0 - 1);
+          const char* src = xg + ((((size_t)b * A.H + gy) * A.W + gx) * kChunks + hq) * 16;
+          const uint32_t px = pl + (uint32_t)((hside ? 129 : 0) * kPixBytes);
+          const uint32_t dst = px + (uint32_t)((hq ^ ((px >> 7) & 3)) << 4);   // 64-byte swizzle
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full(s)) : "memory");
+        }
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTxBytes)
+                       : "memory");
           asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc<N>()), "r"(accum));
-          accum = 1;
+              "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(pl + kPixBytes),   // 1024-byte aligned
+              "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(x0), "r"(b * A.H + gy), "r"(full(s))
+              : "memory");
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(mbar)));
+      if (*abort_flag) break;
     }
-    // the next tile's input travels while the MMAs run
-    if (tile + gridDim.x < ntiles) load_tile(xg, A, tile + gridDim.x, tiles_x, v);
-    // bounded wait for the MMAs (about 50 ms of polling at most)
-    uint32_t done = 0;
-    const long long t0 = clock64();
-    while (!done) {
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-          : "=r"(done)
-          : "r"(smem_addr(mbar)), "r"(phase));
-      if (!done && clock64() - t0 > 100000000ll) break;
-    }
-    // all threads take the same decision (a thread that gave up makes the block stop)
-    if (__syncthreads_or(done ? 0 : 1)) {
-      if (tid == 0) atomicExch(&g_tc_fail, 1);
-      break;
-    }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int p = warp * 32 + lane;                    // this thread's pixel (TMEM lane)
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    if (A.mode == kModeGuess) {
-      uint32_t r0;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(r0) : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      A.phi0[pix0 + p] += A.scale * (double)(__uint_as_float(r0) + bias_s[0]);
-    } else {
-      if (A.mode == kModeGeluGrad) {
-        // stage the tile's z (a contiguous block) with coalesced loads
-        const uint4* zg = reinterpret_cast<const uint4*>(A.z_f32 + pix0 * 32);
-        uint4* st = reinterpret_cast<uint4*>(As + kStageF32);
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t b0 = sbase + kOffB;
+      int k = 0;   // plane loads consumed
+      bool ok = true;
+      for (int ts = t_begin; ts < t_end && ok;) {
+        int te = ts;   // the run ts .. te down one strip
+        while (te + 1 < t_end && order.continues(te)) ++te;
+        const int n = te - ts + 1, i_s = ts - t_begin;
+        for (int rr = -1; rr <= n; ++rr, ++k) {   // input row y0 + rr (output rows rr-1, rr, rr+1 of the run)
+          const int s = k % kSlots;
+          ok = wait_bar(full(s), (uint32_t)((k / kSlots) & 1), abort_flag);
+          if (ok && rr + 1 <= n - 1) {   // first contribution to output row rr + 1: its block must be free
+            const int i = i_s + rr + 1;
+            if (i >= kBlocks) ok = wait_bar(accempty(i % kBlocks), (uint32_t)(((i / kBlocks) - 1) & 1), abort_flag);
+          }
+          if (!ok) break;
+          // the halo chunks arrived through cp.async (generic proxy); the MMAs read
+          // through the async proxy
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int qa = rr - 1 > 0 ? rr - 1 : 0, qb = rr + 1 < n - 1 ? rr + 1 : n - 1;
+          const int cnt = qb - qa + 1;                 // 1 .. 3 output rows
+          const int ja = (i_s + qa) % kBlocks;         // ring block of output row qa
+          const int sba = qa - rr + 1;                 // its block in the weight stack (dy = 2 - sba)
+          const int c1 = cnt < kBlocks - ja ? cnt : kBlocks - ja;
+          const uint32_t pl = plane(s);
 #pragma unroll
-        for (int i = 0; i < kTM * 8 / kThreads; ++i) {
-          const int u = tid + i * kThreads, pp = u >> 3, j = u & 7;
-          st[f32_slot(pp, j)] = zg[u];
+          for (int dx = 0; dx < 3; ++dx) {
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t ad = make_desc(pl + (uint32_t)(dx * kPixBytes + kk * 32), 16, 8 * kPixBytes, 4);
+              const uint32_t bb = b0 + (uint32_t)(dx * 3 * NB * kPixBytes + kk * 32);
+              const uint64_t bd = make_desc(bb + (uint32_t)(sba * NB * kPixBytes), 16, 8 * kPixBytes, 4);
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(ja * NB)),
+                  "l"(ad), "l"(bd), "r"(idesc(c1 * NB)));
+              if (c1 < cnt) {   // the rows past the ring's end continue at block 0
+                const uint64_t bd2 = make_desc(bb + (uint32_t)((sba + c1) * NB * kPixBytes), 16, 8 * kPixBytes, 4);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd2), "r"(idesc((cnt - c1) * NB)));
+              }
+            }
+          }
+          mma_commit(empty(s));                                            // the plane is used once
+          if (rr - 1 >= 0) mma_commit(accfull((i_s + rr - 1) % kBlocks));  // output row rr - 1 is complete
         }
-        __syncthreads();
+        ts = te + 1;
       }
-      uint32_t r[32];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-          "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      float4* sf = reinterpret_cast<float4*>(As + kStageF32);
-      uint4* sb = reinterpret_cast<uint4*>(As + kStageBf16);
-      float o[32];
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    // Two groups of 8 warps take alternate tiles (group G the tiles i = G mod 2), so one
+    // group's GELU math overlaps the other's stores and barriers.  Within a group, warp w
+    // reads lane quarter w % 4 and the 16 columns of half h of the block.
+    const int e = warp - 2, grp = e >> 3, qd = warp & 3, h = (e >> 2) & 1;
+    const bool owns_cols = h * 16 < NB;
+    const bool leader = (e & 7) == 0 && lane == 0;        // issues the group's bulk copies
+    const int p = qd * 32 + lane;                         // this thread's pixel in the tile
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    const float* bias_h = bias_s + (16 * h & 31);   // this half's 16 biases (shared-memory broadcast)
+    const bool f32_out = A.mode == kModeLinear || A.mode == kModeGeluGrad || A.z_f32 != nullptr;
+    unsigned char* ob = smem + kOffOut + grp * kOutBytes;  // this group's stage buffer
+    for (int i = grp, t = t_begin + grp; t < t_end; t += 2, i += 2) {
+      const int blk = i % kBlocks;
+      int b, y, x0;
+      order.decode(t, b, y, x0);
+      const size_t pix0 = ((size_t)b * A.H + y) * A.W + x0;
+      float4 zin[4];
       if (A.mode == kModeGeluGrad) {
+        const float4* zg = reinterpret_cast<const float4*>(A.z_f32 + (pix0 + p) * 32 + h * 16);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4 z = sf[f32_slot(p, j)];
-          o[4 * j + 0] = 4 * j + 0 < A.cout ? __uint_as_float(r[4 * j + 0]) * gelu_grad(z.x) : 0.f;
-          o[4 * j + 1] = 4 * j + 1 < A.cout ? __uint_as_float(r[4 * j + 1]) * gelu_grad(z.y) : 0.f;
-          o[4 * j + 2] = 4 * j + 2 < A.cout ? __uint_as_float(r[4 * j + 2]) * gelu_grad(z.z) : 0.f;
-          o[4 * j + 3] = 4 * j + 3 < A.cout ? __uint_as_float(r[4 * j + 3]) * gelu_grad(z.w) : 0.f;
+        for (int v = 0; v < 4; ++v) zin[v] = zg[v];
+      }
+      bool ok = wait_bar(accfull(blk), (uint32_t)((i / kBlocks) & 1), abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t r[16];
+      if (ok && owns_cols) {
+        // read this warp's 16 columns of the block, then zero them for the block's next row
+        const uint32_t taddr = tmem + lane_base + (uint32_t)(blk * NB + h * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const uint32_t zero = 0u;
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+                taddr),
+            "r"(zero)
+            : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) bar_arrive(accempty(blk));   // this warp's share of the block is read and zeroed
+      if (A.mode == kModeGuess) {
+        if (ok && h == 0) A.phi0[pix0 + p] += A.scale * (double)(__uint_as_float(r[0]) + bias_h[0]);
+        continue;
+      }
+      float o[16];
+      if (A.mode == kModeGeluGrad) {
+        const float* zz = reinterpret_cast<const float*>(zin);
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          o[c] = 16 * h + c < A.cout ? __uint_as_float(r[c]) * mpfc_cnn_math::gelu_grad(zz[c]) : 0.f;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) o[c] = 16 * h + c < A.cout ? __uint_as_float(r[c]) + bias_h[c] : 0.f;
+      }
+      float q[16];
+      if (A.mode == kModeGelu) {
+        float zb[8], gb[8];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) zb[c] = o[8 * half + c];
+          mpfc_cnn_math::gelu8(zb, gb);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) q[8 * half + c] = 16 * h + 8 * half + c < A.cout ? gb[c] : 0.f;
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < 32; ++c) o[c] = c < A.cout ? __uint_as_float(r[c]) + bias_s[c] : 0.f;
+        for (int c = 0; c < 16; ++c) q[c] = o[c];
       }
-      const bool f32_out = A.mode == kModeLinear || A.mode == kModeGeluGrad || A.z_f32 != nullptr;
-      if (f32_out) {
+      // this group's stage buffer must have been read by its previous bulk copy
+      if (leader) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      asm volatile("bar.sync %0, 256;" ::"r"(1 + grp) : "memory");
+      if (ok) {
+        if (f32_out) {
+          uint4* d = reinterpret_cast<uint4*>(ob + kOutBf16 + p * 128 + h * 64);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          sf[f32_slot(p, j)] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
-      }
-      if (A.mode != kModeLinear) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float g[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            g[e] = A.mode == kModeGelu ? (8 * j + e < A.cout ? gelu_f(o[8 * j + e]) : 0.f) : o[8 * j + e];
-          sb[bf16_slot(p, j)] = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]),
-                                           pack_bf16(g[6], g[7]));
+          for (int v = 0; v < 4; ++v)
+            d[v] = make_uint4(__float_as_uint(o[4 * v]), __float_as_uint(o[4 * v + 1]), __float_as_uint(o[4 * v + 2]),
+                              __float_as_uint(o[4 * v + 3]));
+        }
+        if (A.mode != kModeLinear) {
+          uint4* d = reinterpret_cast<uint4*>(ob + p * 64 + h * 32);
+          d[0] = make_uint4(pack_bf16(q[0], q[1]), pack_bf16(q[2], q[3]), pack_bf16(q[4], q[5]), pack_bf16(q[6], q[7]));
+          d[1] = make_uint4(pack_bf16(q[8], q[9]), pack_bf16(q[10], q[11]), pack_bf16(q[12], q[13]),
+                            pack_bf16(q[14], q[15]));
         }
       }
-      __syncthreads();
-      // contiguous copy-out of the tile
-      if (f32_out) {
-        uint4* dst = reinterpret_cast<uint4*>((A.mode == kModeGelu ? A.z_f32 : A.y_f32) + pix0 * 32);
-        const uint4* src = reinterpret_cast<const uint4*>(As + kStageF32);
-#pragma unroll
-        for (int i = 0; i < kTM * 8 / kThreads; ++i) {
-          const int u = tid + i * kThreads, pp = u >> 3, j = u & 7;
-          dst[u] = src[f32_slot(pp, j)];
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync %0, 256;" ::"r"(1 + grp) : "memory");
+      if (leader && !*abort_flag) {
+        if (f32_out) {
+          float* dst = (A.mode == kModeGelu ? A.z_f32 : A.y_f32) + pix0 * 32;
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                       "r"(smem_addr(ob + kOutBf16)), "r"(kOutF32)
+                       : "memory");
         }
-      }
-      if (A.mode != kModeLinear) {
-        uint4* dst = reinterpret_cast<uint4*>(A.y_bf16 + pix0 * 32);
-        const uint4* src = reinterpret_cast<const uint4*>(As + kStageBf16);
-#pragma unroll
-        for (int i = 0; i < kTM * 4 / kThreads; ++i) {
-          const int u = tid + i * kThreads, pp = u >> 2, j = u & 3;
-          dst[u] = src[bf16_slot(pp, j)];
+        if (A.mode != kModeLinear) {
+          __nv_bfloat16* dst = A.y_bf16 + pix0 * 32;
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(ob)),
+                       "r"(kOutBf16)
+                       : "memory");
         }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();   // TMEM and the A space are free for the next tile
+    if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
+  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBlocks * NB));
 }
 
 int g_use_tc = 1;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
 
-template <int N>
-int launch_tc(const TcArgs& A, cudaStream_t s) {
+// Tensor map of the input activations viewed as [B*H rows][W pixels][32 channels]
+// bf16, box = 32 channels x 128 pixels x 1 row (8 KB contiguous), 64-byte swizzle.
+int make_tmap(CUtensorMap* map, const void* x, int B, int H, int W) {
+  {
+    std::lock_guard<std::mutex> lk(g_encode_mu);
+    if (!g_encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        mpfc_set_cuda_error(e != cudaSuccess ? e : cudaErrorSymbolNotFound, "cuTensorMapEncodeTiled", __FILE__,
+                            __LINE__);
+        return MPFC_ERR_CUDA;
+      }
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)kCin, (cuuint64_t)W, (cuuint64_t)B * H};
+  cuuint64_t strides[2] = {(cuuint64_t)kCin * 2, (cuuint64_t)W * kCin * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kCin, (cuuint32_t)kTM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(x), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? MPFC_OK : MPFC_ERR_INVALID;
+}
+
+template <int NB>
+int launch_tc(const CUtensorMap& map, const TcArgs& A, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) {
       mpfc_set_cuda_error(e, "tc conv smem", __FILE__, __LINE__);
       return MPFC_ERR_CUDA;
@@ -316,8 +517,8 @@ int launch_tc(const TcArgs& A, cudaStream_t s) {
     attr = true;
   }
   const long long ntiles = (long long)A.B * A.H * (A.W / kTM);
-  const int grid = (int)(ntiles < 152 * 4 ? ntiles : 152 * 4);   // 4 CTAs per SM fit in shared memory
-  k_conv3x3_tc<N><<<grid, kThreads, kSmem, s>>>(A);
+  const int grid = (int)(ntiles < 152 ? ntiles : 152);   // persistent: one CTA per SM
+  k_conv3x3_tc<NB><<<grid, kThreads, kSmem, s>>>(map, A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     mpfc_set_cuda_error(e, "k_conv3x3_tc", __FILE__, __LINE__);
@@ -338,6 +539,14 @@ bool mpfc_cnn_tc_eligible(int cin_p, int cout_p, int W, int mode) {
 int mpfc_cnn_conv_tc(const void* x, int B, int H, int W, const void* wk, const float* bias, int cout, int cout_p,
                      int mode, void* y_bf16, float* y_f32, float* z_f32, double* phi0, double scale,
                      cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(wk) & 15) ||
+      (reinterpret_cast<uintptr_t>(y_bf16) & 15) || (reinterpret_cast<uintptr_t>(y_f32) & 15) ||
+      (reinterpret_cast<uintptr_t>(z_f32) & 15))
+    return MPFC_ERR_INVALID;   // 16-byte vector and bulk copies
+  if ((long long)B * H * (W / kTM) >= (1ll << 30)) return MPFC_ERR_INVALID;   // tile indices stay 32-bit
+  CUtensorMap map;
+  int rc = make_tmap(&map, x, B, H, W);
+  if (rc != MPFC_OK) return rc;
   TcArgs A;
   A.x = (const __nv_bfloat16*)x;
   A.wk = (const __nv_bfloat16*)wk;
@@ -353,7 +562,7 @@ int mpfc_cnn_conv_tc(const void* x, int B, int H, int W, const void* wk, const f
   A.z_f32 = z_f32;
   A.phi0 = phi0;
   A.scale = scale;
-  return mode == kModeGuess ? launch_tc<16>(A, s) : launch_tc<32>(A, s);
+  return mode == kModeGuess ? launch_tc<16>(map, A, s) : launch_tc<32>(map, A, s);
 }
 
 extern "C" int mpfc_cnn_set_tensor_path(int use_tcgen05) {

@@ -1,8 +1,11 @@
-// FP64 FMA-rate probe used for the roofline of the FP64 kernels (see include/mpfc_probe.h).
+// Measurement and test helpers (see include/mpfc_probe.h): the FP64 FMA-rate probe used
+// for the roofline of the FP64 kernels, and device evaluations of the library's own
+// reciprocal, precision conversions and GELU for tests against their error bounds.
 #include <cuda_runtime.h>
 
 #include "../../include/mpfc.h"
 #include "../../include/mpfc_probe.h"
+#include "cnn_math.cuh"
 #include "mpfc_common.cuh"
 
 namespace {
@@ -75,5 +78,44 @@ extern "C" int mpfc_probe_convert(const double* d_x, float* d_rn, float* d_trunc
   if (!d_x || !d_rn || !d_trunc || !d_back || n < 0) return MPFC_ERR_INVALID;
   if (n == 0) return MPFC_OK;
   k_convert<<<(n + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(d_x, d_rn, d_trunc, d_back, n);
+  return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
+}
+
+namespace {
+__global__ void k_gelu(const float* __restrict__ z, float* __restrict__ g, float* __restrict__ dg, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    g[i] = mpfc_cnn_math::gelu(z[i]);
+    dg[i] = mpfc_cnn_math::gelu_grad(z[i]);
+  }
+}
+
+// the 8-wide form: thread i evaluates z[8i .. 8i+7] (zero-padded past n)
+__global__ void k_gelu8(const float* __restrict__ z, float* __restrict__ g, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (8 * i < n) {
+    float zz[8], gg[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) zz[j] = 8 * i + j < n ? z[8 * i + j] : 0.0f;
+    mpfc_cnn_math::gelu8(zz, gg);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (8 * i + j < n) g[8 * i + j] = gg[j];
+  }
+}
+}  // namespace
+
+extern "C" int mpfc_probe_gelu(const float* d_z, float* d_g, float* d_dg, int n, void* cuda_stream) {
+  if (!d_z || !d_g || !d_dg || n < 0) return MPFC_ERR_INVALID;
+  if (n == 0) return MPFC_OK;
+  k_gelu<<<(n + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(d_z, d_g, d_dg, n);
+  return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
+}
+
+extern "C" int mpfc_probe_gelu8(const float* d_z, float* d_g, int n, void* cuda_stream) {
+  if (!d_z || !d_g || n < 0) return MPFC_ERR_INVALID;
+  if (n == 0) return MPFC_OK;
+  const int threads = (n + 7) / 8;
+  k_gelu8<<<(threads + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(d_z, d_g, n);
   return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
 }

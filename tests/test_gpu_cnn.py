@@ -252,3 +252,36 @@ def test_learned_guess_same_on_both_tensor_paths(G, tensor_path):
         out[use_tc] = np.array([i["res0"] for i in infos])
         assert G._lib().mpfc_cnn_tensor_path_status() == 0
     np.testing.assert_allclose(out[1], out[0], rtol=1e-3)
+
+
+def test_gelu_matches_exact_erf(G):
+    """The kernels' GELU and GELU' (erf after Abramowitz & Stegun 7.1.26) against the
+    exact functions in float64, over the range activations take and far tails."""
+    import ctypes
+    import math
+    lib = G._lib()
+    lib.mpfc_probe_gelu.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]
+    z = np.concatenate([np.linspace(-12, 12, 200001), [0.0, -0.0, 1e-30, -1e-30, 50.0, -50.0, 1e4, -1e4]])
+    z = z.astype(np.float32)
+    zd = torch.from_numpy(z).cuda()
+    g, dg = torch.empty_like(zd), torch.empty_like(zd)
+    assert lib.mpfc_probe_gelu(zd.data_ptr(), g.data_ptr(), dg.data_ptr(), z.size, None) == 0
+    torch.cuda.synchronize()
+    zz = z.astype(np.float64)
+    erf = np.array([math.erf(v / math.sqrt(2.0)) for v in zz])
+    g_ref = 0.5 * zz * (1.0 + erf)
+    dg_ref = 0.5 * (1.0 + erf) + zz * np.exp(-0.5 * zz * zz) / math.sqrt(2.0 * math.pi)
+    gg, dd = g.cpu().numpy().astype(np.float64), dg.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gg - g_ref) <= 4e-7 * np.abs(zz) + 4e-7 * np.abs(g_ref) + 1e-37)
+    assert np.all(np.abs(dd - dg_ref) <= 1e-6 * (1.0 + np.abs(zz)))
+    # the 8-wide form (shared reciprocal), with mixed magnitudes inside each group of 8
+    lib.mpfc_probe_gelu8.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int, ctypes.c_void_p]
+    perm = np.random.default_rng(3).permutation(z.size)
+    zp = np.ascontiguousarray(z[perm])
+    zpd = torch.from_numpy(zp).cuda()
+    g8 = torch.empty_like(zpd)
+    assert lib.mpfc_probe_gelu8(zpd.data_ptr(), g8.data_ptr(), zp.size, None) == 0
+    torch.cuda.synchronize()
+    gr = g_ref[perm]
+    got8 = g8.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got8 - gr) <= 4e-7 * np.abs(zz[perm]) + 4e-7 * np.abs(gr) + 1e-37)
