@@ -54,8 +54,11 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--profile", action="store_true", help="steps only, no flush and no extras (ncu launch list)")
-    ap.add_argument("--form", choices=["fp64", "fp32"], default="fp64",
+    ap.add_argument("--form", choices=["fp64", "fp32", "learned"], default="fp64",
                     help="with --profile: which solver form the launch list runs")
+    ap.add_argument("--profile-conv", action="store_true",
+                    help="only the 32 -> 32 channel convolution of the learned guess (GELU, bf16 out), four "
+                         "launches at --size^2 (ncu capture of the network's top kernel)")
     ap.add_argument("--profile-smooth", action="store_true",
                     help="only the finest-level sweep kernel, two sweeps (ncu capture of the top kernel)")
     return ap.parse_args()
@@ -176,6 +179,60 @@ def cpu_oracle_rate(size, scheme, max_steps, budget_s, warmup=0):
 
 
 # ----------------------------------------------------------------------------- reference arm
+def conv32_timing(size, launches=10, flush_between=True):
+    """The learned guess's 32 -> 32 channel convolution (GELU, bf16 out, the solver's
+    inference form) on a size^2 image, timed alone with CUDA events on its stream, with
+    and without an L2 flush before each launch; roofline against the measured peaks."""
+    import numpy as np
+    import torch
+    from paper_1208_2643_gb300 import guess as gmod
+    lib = gmod._lib()
+    st = torch.cuda.current_stream()
+    s = st.cuda_stream
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(1, size, size, 32, device="cuda", generator=g).bfloat16()
+    wt = torch.randn(9, 32, 32, device="cuda", generator=g) * 0.1
+    bias = torch.zeros(32, device="cuda")
+    wk = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+    y = torch.empty(1, size, size, 32, dtype=torch.bfloat16, device="cuda")
+    if lib.mpfc_cnn_pack_weights(wt.data_ptr(), 32, 32, 32, 32, 0, wk.data_ptr(), s) != 0:
+        raise RuntimeError("mpfc_cnn_pack_weights failed")
+
+    def one():
+        if lib.mpfc_cnn_conv_forward(x.data_ptr(), 1, size, size, 32, wk.data_ptr(), bias.data_ptr(), 32, 32, 0,
+                                     y.data_ptr(), None, None, s) != 0:
+            raise RuntimeError("mpfc_cnn_conv_forward failed")
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush_between else None
+    out = {}
+    for label, use_flush in (("us_flushed", True), ("us_no_flush", False)):
+        if use_flush and flush is None:
+            continue
+        for _ in range(3):
+            one()
+        ts = []
+        for _ in range(launches):
+            if use_flush:
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            one()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        out[label] = float(np.median(ts))
+    px = size * size
+    flops = 2.0 * 9 * 32 * 32 * px
+    bytes_ = (32 * 2 + 32 * 2) * px                 # read the bf16 input once, write the bf16 output
+    peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    t = out.get("us_flushed", out["us_no_flush"]) * 1e-6
+    out.update({"image": f"1 x {size} x {size} x 32 bf16", "tflops": flops / t / 1e12,
+                "frac_of_measured_bf16": flops / t / 1e12 / peaks["bf16_tflops"],
+                "gbs_algorithmic": bytes_ / t / 1e9, "frac_of_measured_hbm": bytes_ / t / 1e9 / peaks["hbm_gbs"],
+                "bound": "neither: the epilogue (GELU on the MUFU pipe) and the TMA/MMA handoff set the rate"})
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -214,9 +271,19 @@ def run_ours(args):
                             tol=w["tol"], omega=w["omega"], guess=mpfc.MPFC_GUESS_EXTRAP)
     if args.profile and args.form == "fp32":
         p.precision = mpfc.MPFC_FP32_INNER
+    if args.profile and args.form == "learned":
+        p.guess = mpfc.MPFC_GUESS_LEARNED
+    if args.profile_conv:
+        r = conv32_timing(size, launches=4, flush_between=False)
+        if rank == 0:
+            print(json.dumps({"profile_conv": True, "us": r["us_no_flush"]}), flush=True)
+        return
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     solver = mpfc.Solver(p, stream=stream)
+    if args.profile and args.form == "learned":
+        from paper_1208_2643_gb300 import guess as gmod
+        gmod.attach(solver, gmod.load())
     phi0 = inputs.noise_field(size, size, 0.07, 0.05, replicas.instance_seed(1, rank))
     solver.set_state(phi0)
     if args.profile_smooth:
@@ -426,8 +493,10 @@ def run_ours(args):
                                 "res0_mean_extrapolated": float(np.mean([r["res0"] for r in recs_main])),
                                 "network_ms_per_step": ev0.elapsed_time(ev1) / 10,
                                 "speedup_vs_fp64": (world * K / (msl * 1e-3)) / steps_per_s,
-                                "model": "5 x conv3x3 (3-32-32-32-32-1), GELU, bf16/fp32-acc, mma.sync tensor cores; "
-                                         "trained on 20k solver steps at 256^2"}
+                                "conv32": conv32_timing(size),
+                                "model": "5 x conv3x3 (3-32-32-32-32-1), GELU, bf16/fp32-acc; the 32-input-channel "
+                                         "layers on tcgen05 (TMEM accumulators, TMA), the first on mma.sync; "
+                                         "trained on solver trajectories at 256^2"}
             sl.close()
 
     cpu = None

@@ -360,17 +360,19 @@ __global__ void k_mean_final(const double* __restrict__ part, long long G, doubl
 //   x0 = (phi^k - mean)/s0, x1 = (phi^k - phi^{k-1})/s1, x2 = (phi^k - 2 phi^{k-1} + phi^{k-2})/s2, x3 = 0,
 //   y  = (phi^{k+1} - 2 phi^k + phi^{k-1})/sy   (the error of the linear extrapolation).
 __global__ void k_features(const double* __restrict__ p0, const double* __restrict__ p1, const double* __restrict__ p2,
-                           const double* __restrict__ pn, long long G, int B, const float* __restrict__ norms,
+                           const double* __restrict__ pn, long long G, const float* __restrict__ norms,
                            const double* __restrict__ means, __nv_bfloat16* __restrict__ x, float* __restrict__ y) {
-  long long total = (long long)B * G;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    int b = (int)(t / G);
-    double a = p0[t], c1 = p1[t], c2 = p2[t];
-    x[4 * t + 0] = __float2bfloat16_rn((float)((a - means[b]) / norms[0]));
-    x[4 * t + 1] = __float2bfloat16_rn((float)((a - c1) / norms[1]));
-    x[4 * t + 2] = __float2bfloat16_rn((float)((a - 2.0 * c1 + c2) / norms[2]));
-    x[4 * t + 3] = __float2bfloat16_rn(0.f);
-    if (y && pn) y[t] = (float)((pn[t] - 2.0 * a + c1) / norms[3]);
+  const int b = blockIdx.y;   // sample
+  const double inv0 = 1.0 / (double)norms[0], inv1 = 1.0 / (double)norms[1], inv2 = 1.0 / (double)norms[2];
+  const double inv3 = 1.0 / (double)norms[3], mean = means[b];
+  const size_t off = (size_t)b * G;
+  uint2* xo = reinterpret_cast<uint2*>(x) + off;   // 4 bf16 channels = 8 bytes per pixel
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < G; i += (long long)gridDim.x * blockDim.x) {
+    const double a = p0[off + i], c1 = p1[off + i], c2 = p2[off + i];
+    __nv_bfloat162 lo = __floats2bfloat162_rn((float)((a - mean) * inv0), (float)((a - c1) * inv1));
+    __nv_bfloat162 hi = __floats2bfloat162_rn((float)((a - 2.0 * c1 + c2) * inv2), 0.f);
+    xo[i] = make_uint2(*reinterpret_cast<unsigned*>(&lo), *reinterpret_cast<unsigned*>(&hi));
+    if (y && pn) y[off + i] = (float)((pn[off + i] - 2.0 * a + c1) * inv3);
   }
 }
 
@@ -386,9 +388,9 @@ extern "C" int mpfc_cnn_features(const double* phik, const double* phikm1, const
   double* part = means + B;
   k_mean_partial<<<dim3(kMeanBlocks, B), 256, 0, s>>>(phik, G, part);
   k_mean_final<<<B, 32, 0, s>>>(part, G, means);
-  long long total = (long long)B * G;
-  int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
-  k_features<<<blocks, 256, 0, s>>>(phik, phikm1, phikm2, phikp1, G, B, norms, means, (__nv_bfloat16*)x_bf16, y_f32);
+  const long long per = (G + 255) / 256, cap = (152 * 16 + B - 1) / B;
+  const dim3 grid((unsigned)(per < cap ? per : cap), (unsigned)B);
+  k_features<<<grid, 256, 0, s>>>(phik, phikm1, phikm2, phikp1, G, norms, means, (__nv_bfloat16*)x_bf16, y_f32);
   return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
 }
 

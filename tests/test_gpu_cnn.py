@@ -285,3 +285,31 @@ def test_gelu_matches_exact_erf(G):
     gr = g_ref[perm]
     got8 = g8.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(got8 - gr) <= 4e-7 * np.abs(zz[perm]) + 4e-7 * np.abs(gr) + 1e-37)
+
+
+def test_features_match_oracle(G):
+    """Network input and training target of mpfc_cnn_features against the oracle's
+    features() (and the extrapolation error for the target), on two samples."""
+    from oracle import cnn
+    lib = G._lib()
+    rng = np.random.default_rng(8)
+    B, H, W = 2, 24, 40
+    f = [rng.normal(0.07, 0.05, size=(B, H, W)) for _ in range(4)]   # phi^k, phi^{k-1}, phi^{k-2}, phi^{k+1}
+    norms = np.array([0.05, 2e-3, 3e-4, 1e-4], dtype=np.float32)
+    fd = [torch.from_numpy(a).cuda() for a in f]
+    nd = torch.from_numpy(norms).cuda()
+    means = torch.empty(B * 129, dtype=torch.float64, device="cuda")
+    x = torch.empty((B, H, W, 4), dtype=torch.bfloat16, device="cuda")
+    y = torch.empty((B, H, W), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.mpfc_cnn_features(fd[0].data_ptr(), fd[1].data_ptr(), fd[2].data_ptr(), fd[3].data_ptr(), B, H, W,
+                                 nd.data_ptr(), means.data_ptr(), x.data_ptr(), y.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    got = x.float().cpu().numpy().astype(np.float64)
+    for b in range(B):
+        ref = cnn.features(f[0][b], f[1][b], f[2][b], norms.astype(np.float64))
+        # one bf16 rounding (8 significant bits) of each feature
+        assert np.all(np.abs(got[b, ..., :3] - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-30)
+        assert np.all(got[b, ..., 3] == 0)
+        tgt = (f[3][b] - 2 * f[0][b] + f[1][b]) / float(norms[3])
+        np.testing.assert_allclose(y.cpu().numpy()[b], tgt, rtol=1e-6, atol=1e-6 * np.abs(tgt).max())
