@@ -90,6 +90,7 @@ def _load():
                                           ctypes.c_int, ctypes.c_int, ctypes.c_double] + [_D] * 7
         lib.orc_scheme_consts.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, _D, _D, _D]
         lib.orc_num_levels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.orc_set_boundary.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -104,6 +105,27 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_boundary(ny_neumann: bool) -> None:
+    """Boundary rule of every following call: periodic (App. A, (A.8)-(A.9)), or with
+    ny_neumann periodic in x and homogeneous Neumann in y ((A.7), Sec. 4.5)."""
+    _load().orc_set_boundary(1 if ny_neumann else 0)
+
+
+class boundary:
+    """Context manager: the given boundary rule inside, periodic again on exit."""
+
+    def __init__(self, ny_neumann: bool):
+        self.ny = ny_neumann
+
+    def __enter__(self):
+        set_boundary(self.ny)
+        return self
+
+    def __exit__(self, *exc):
+        set_boundary(False)
+        return False
 
 
 @dataclass
@@ -121,6 +143,7 @@ class Params:
     newton: int = 1
     coarse_cells: int = 4
     omega: float = 0.8
+    ny_neumann: int = 0   # 1: homogeneous Neumann in y (Sec. 4.5); applied by Solver around each call
 
     def c_struct(self) -> _Params:
         return _Params(self.m, self.n, self.h, self.M, self.eps, self.beta, self.s, self.nu1, self.nu2,
@@ -140,7 +163,7 @@ def num_levels(m: int, n: int, coarse_cells: int = 4) -> int:
 
 
 def laplacian(f, h):
-    """Five-point Delta_h with periodic ghost rule (App. A)."""
+    """Five-point Delta_h with the current ghost rule (App. A; see set_boundary)."""
     f = _f64(f)
     out = np.empty_like(f)
     _load().orc_laplacian(f.shape[1], f.shape[0], h, _p(f), _p(out))
@@ -263,8 +286,9 @@ class Solver:
         info = _Info()
         hist = np.zeros(max(max_cycles, fixed_cycles, 1))
         ph0 = _f64(phi0) if phi0 is not None else None
-        st = self._lib.orc_step(self._ctx, scheme, guess, _p(ph0), tol, max_cycles, fixed_cycles,
-                                ctypes.byref(info), _p(hist))
+        with boundary(self.p.ny_neumann):
+            st = self._lib.orc_step(self._ctx, scheme, guess, _p(ph0), tol, max_cycles, fixed_cycles,
+                                    ctypes.byref(info), _p(hist))
         return dict(cycles=info.cycles, status=info.status, res0=info.res0, res=info.res,
                     hist=hist[:info.cycles].copy(), rc=st)
 
@@ -275,6 +299,7 @@ class Solver:
         hist = np.zeros(max(max_cycles, 1))
         res = ctypes.c_double()
         pk = _f64(phik) if phik is not None else None
-        cyc = self._lib.orc_solve(self._ctx, scheme, _p(phi), _p(mu), _p(kappa), _p(S1), _p(S2), _p(S3), _p(pk),
-                                  tol, max_cycles, _p(hist), ctypes.byref(res))
+        with boundary(self.p.ny_neumann):
+            cyc = self._lib.orc_solve(self._ctx, scheme, _p(phi), _p(mu), _p(kappa), _p(S1), _p(S2), _p(S3),
+                                      _p(pk), tol, max_cycles, _p(hist), ctypes.byref(res))
         return (phi, mu, kappa), cyc, res.value, hist[:cyc].copy()

@@ -14,8 +14,10 @@ from __future__ import annotations
 import numpy as np
 
 
-def lap_matrix(m, n, h):
-    """Matrix of the periodic five-point Delta_h on (n, m) arrays flattened row-major."""
+def lap_matrix(m, n, h, ny_neumann=False):
+    """Matrix of the five-point Delta_h on (n, m) arrays flattened row-major: periodic,
+    or (ny_neumann) periodic in x and homogeneous Neumann in y, where a ghost row takes
+    the value of the boundary row next to it (App. A, (A.7))."""
     G = m * n
     L = np.zeros((G, G))
     for j in range(n):
@@ -23,6 +25,8 @@ def lap_matrix(m, n, h):
             r = j * m + i
             L[r, r] -= 4.0 / h**2
             for (ii, jj) in ((i - 1, j), (i + 1, j), (i, j - 1), (i, j + 1)):
+                if ny_neumann:
+                    jj = min(max(jj, 0), n - 1)
                 L[r, (jj % n) * m + (ii % m)] += 1.0 / h**2
     return L
 
@@ -39,14 +43,14 @@ def _dg(scheme, phi, phik):
     return 0.25 * (3.0 * phi**2 + 2.0 * phi * phik + phik**2)
 
 
-def newton_solve(scheme, consts, h, S, phik=None, u0=None, tol=1e-14, max_iter=50):
+def newton_solve(scheme, consts, h, S, phik=None, u0=None, tol=1e-14, max_iter=50, ny_neumann=False):
     """Solves N(u) = S (App. B.1/B.2) by Newton's method with the exact Jacobian.
     Returns (phi, mu, kappa) as (n, m) arrays and the final max-norm residual."""
     c, gam, theta = consts
     S1, S2, S3 = [np.asarray(x, dtype=np.float64).ravel() for x in S]
     n, m = np.asarray(S[0]).shape
     G = m * n
-    L = lap_matrix(m, n, h)
+    L = lap_matrix(m, n, h, ny_neumann)
     pk = np.zeros(G) if phik is None else np.asarray(phik, dtype=np.float64).ravel()
     if u0 is None:
         phi, mu, kappa = np.zeros(G), np.zeros(G), np.zeros(G)

@@ -13,7 +13,10 @@
  * Grid functions are m x n cell-centred arrays stored row-major, f[j*m + i], with
  * i the x index (0..m-1) and j the y index (0..n-1).  The ghost ring of App. A is
  * not stored: periodic boundary conditions (App. A, (A.8)-(A.9)) are applied by
- * wrapping indices.
+ * wrapping indices.  orc_set_boundary(1) switches every following call to the mixed
+ * conditions of Sec. 4.5: periodic in x, homogeneous Neumann in y with the ghost rule
+ * of App. A, (A.7): phi_{i,0} = phi_{i,1}, phi_{i,n+1} = phi_{i,n}, i.e. a ghost row
+ * holds the value of the boundary row next to it.
  *
  * Readings of points the paper leaves open (each also listed in the design doc):
  *  - smoother: red-black ordering, red = (i+j) even first; one local Newton
@@ -31,7 +34,12 @@
  *    coarse source S_c = N_c(R u) + R(S - N(u)); scheme 2 uses phi^k_c = R phi^k;
  *  - coarsest level (a few cells per side): dense Newton on all 3*m*n unknowns,
  *    Gaussian elimination with partial pivoting;
- *  - stopping rule: scaled residual sqrt(sum_{c,i,j} r_c^2 / (3mn)) <= tol.
+ *  - stopping rule: scaled residual sqrt(sum_{c,i,j} r_c^2 / (3mn)) <= tol;
+ *  - Neumann rows (Sec. 4.5 says only that the solver is easily adapted): explicit
+ *    stencils read the ghost row as the boundary row (A.7); in the smoother's cell
+ *    system the ghost is the unknown itself, so it leaves the neighbour sum and the
+ *    diagonal count drops from 4 to 3 (exact elimination of the ghost); the
+ *    transfers and the coarsest solve use the same ghost rule on every level.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -82,19 +90,42 @@ static orc_consts consts_of(const orc_params* p, int scheme) {
 /* ------------------------------------------------------------------------ */
 /* Grid helpers (App. A)                                                    */
 /* ------------------------------------------------------------------------ */
+static int g_ny_neumann = 0;   /* 0: periodic in y (A.9); 1: homogeneous Neumann in y (A.7) */
+
+void orc_set_boundary(int ny_neumann) { g_ny_neumann = ny_neumann ? 1 : 0; }
+
 static int wrap(int i, int m) { return (i % m + m) % m; }
 
-static double at(const double* f, int m, int n, int i, int j) {
-  return f[wrap(j, n) * m + wrap(i, m)];
+/* Stored row that holds row j (j = -1 and j = n are the ghost rows). */
+static int yrow(int j, int n) {
+  if (!g_ny_neumann) return wrap(j, n);
+  return j < 0 ? 0 : (j >= n ? n - 1 : j);
 }
 
-/* Sum of the four face neighbours with periodic wrap. */
+/* Whether row j is a ghost row under the Neumann rule. */
+static int y_is_ghost(int j, int n) { return g_ny_neumann && (j < 0 || j >= n); }
+
+static double at(const double* f, int m, int n, int i, int j) {
+  return f[yrow(j, n) * m + wrap(i, m)];
+}
+
+/* Sum of the four face neighbours, ghost values by the boundary rule. */
 static double nb_sum(const double* f, int m, int n, int i, int j) {
   return at(f, m, n, i - 1, j) + at(f, m, n, i + 1, j) + at(f, m, n, i, j - 1) + at(f, m, n, i, j + 1);
 }
 
-/* Standard five-point discrete Laplacian Delta_h (App. A) with periodic
- * ghost values (A.8)-(A.9). */
+/* Sum over the face neighbours that are not ghost cells, and their number. */
+static double real_nb_sum(const double* f, int m, int n, int i, int j, int* count) {
+  double s = at(f, m, n, i - 1, j) + at(f, m, n, i + 1, j);
+  int c = 2;
+  if (!y_is_ghost(j - 1, n)) { s += at(f, m, n, i, j - 1); ++c; }
+  if (!y_is_ghost(j + 1, n)) { s += at(f, m, n, i, j + 1); ++c; }
+  *count = c;
+  return s;
+}
+
+/* Standard five-point discrete Laplacian Delta_h (App. A) with the ghost
+ * values of the boundary rule (periodic (A.8)-(A.9), or (A.7) in y). */
 void orc_laplacian(int m, int n, double h, const double* f, double* out) {
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < m; ++i)
@@ -195,9 +226,11 @@ void orc_cramer3(const double* A, const double* r, double* x) {
 
 /* One visit of cell (i,j): builds the cell's 3x3 linearised system from the
  * smoothing scheme of App. B and replaces (phi, mu, kappa) at that cell.
- *   eq 1: phi + (4c/h^2) mu                    = S1 + (c/h^2) sum_nb mu
- *   eq 2: -(gam + q) phi + mu + (4/h^2) kappa  = S2 + e + (1/h^2) sum_nb kappa
- *   eq 3: (4 theta/h^2) phi + kappa            = S3 + (theta/h^2) sum_nb phi
+ *   eq 1: phi + (d c/h^2) mu                    = S1 + (c/h^2) sum_nb mu
+ *   eq 2: -(gam + q) phi + mu + (d/h^2) kappa   = S2 + e + (1/h^2) sum_nb kappa
+ *   eq 3: (d theta/h^2) phi + kappa             = S3 + (theta/h^2) sum_nb phi
+ * where sum_nb runs over the d face neighbours that are not ghost cells (d = 4,
+ * or 3 next to a Neumann boundary, whose ghost is the cell's own unknown)
  * with the cubic linearised about the current value p = phi_ij:
  *   Newton: g(phi) ~ g(p) + g'(p)(phi - p)  ->  q = g'(p),  e = g(p) - g'(p) p
  *   Picard, scheme 1: phi^3 ~ p^2 phi        ->  q = p^2,    e = 0
@@ -222,12 +255,16 @@ static void visit_cell(const orc_consts* k, int newton, int m, int n, double h, 
     q = 0.5 * chi;
     e = 0.5 * chi * pk;
   }
-  double A[9] = {1.0, 4.0 * k->c / h2, 0.0,
-                 -(k->gam + q), 1.0, 4.0 / h2,
-                 4.0 * k->theta / h2, 0.0, 1.0};
-  double r[3] = {S1[id] + k->c / h2 * nb_sum(mu, m, n, i, j),
-                 S2[id] + e + nb_sum(kappa, m, n, i, j) / h2,
-                 S3[id] + k->theta / h2 * nb_sum(phi, m, n, i, j)};
+  int d;
+  double smu = real_nb_sum(mu, m, n, i, j, &d);
+  double ska = real_nb_sum(kappa, m, n, i, j, &d);
+  double sph = real_nb_sum(phi, m, n, i, j, &d);
+  double A[9] = {1.0, d * k->c / h2, 0.0,
+                 -(k->gam + q), 1.0, d / h2,
+                 d * k->theta / h2, 0.0, 1.0};
+  double r[3] = {S1[id] + k->c / h2 * smu,
+                 S2[id] + e + ska / h2,
+                 S3[id] + k->theta / h2 * sph};
   double x[3];
   orc_cramer3(A, r, x);
   /* relaxed update u <- u + omega (x - u); omega = 1 is the plain update */
@@ -340,8 +377,9 @@ int orc_coarse_newton(int scheme, double c, double gam, double theta, int m, int
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < m; ++i) {
         int r = j * m + i;
-        int nbr[4] = {j * m + wrap(i - 1, m), j * m + wrap(i + 1, m), wrap(j - 1, n) * m + i,
-                      wrap(j + 1, n) * m + i};
+        /* a ghost neighbour is the boundary cell itself (yrow), which folds it into the diagonal */
+        int nbr[4] = {j * m + wrap(i - 1, m), j * m + wrap(i + 1, m), yrow(j - 1, n) * m + i,
+                      yrow(j + 1, n) * m + i};
         double pk = (scheme == 2) ? phik[r] : 0.0;
         /* row block 1: phi - c Lap mu */
         A[r * N + r] += 1.0;
