@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-polycrystal", action="store_true")
     ap.add_argument("--profile", action="store_true", help="steps only, no flush and no extras (ncu launch list)")
     ap.add_argument("--form", choices=["fp64", "fp32", "learned"], default="fp64",
                     help="with --profile: which solver form the launch list runs")
@@ -301,16 +302,17 @@ def run_ours(args):
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def timed_steps(slv, K, warm):
+    def timed_steps(slv, K, warm, sch=None):
         """K steps of slv, each between events on the stream, L2 flushed in between."""
-        slv.step(scheme, warm)
+        sch = scheme if sch is None else sch
+        slv.step(sch, warm)
         st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         torch.cuda.synchronize()
         for k in range(K):
             flush.fill_(float(k))
             st[k].record(stream)
-            slv.step_async(scheme, 1)
+            slv.step_async(sch, 1)
             en[k].record(stream)
         torch.cuda.synchronize()
         rc_, recs_, _ = slv.records(max(K, 1))
@@ -498,6 +500,25 @@ def run_ours(args):
                                          "layers on tcgen05 (TMEM accumulators, TMA), the first on mma.sync; "
                                          "trained on solver trajectories at 256^2"}
             sl.close()
+
+    # mixed boundary conditions: the polycrystal run of Sec. 4.5 (periodic in x,
+    # homogeneous Neumann in y), 2048^2, scheme 2, s = 1
+    if not args.no_polycrystal:
+        Np = 2048
+        pp = mpfc.default_params(m=Np, n=Np, h=804.0 / 2048, M=1.0, epsilon=0.25, beta=0.9, dt=1.0, tol=w["tol"],
+                                 omega=w["omega"], guess=mpfc.MPFC_GUESS_EXTRAP, bc=mpfc.MPFC_BC_NEUMANN_Y)
+        sp = mpfc.Solver(pp, stream=stream)
+        sp.set_state(inputs.polycrystal_seeds(Np, Np, 0.285, 3, 16, 0.3, replicas.instance_seed(2, rank)))
+        Kp = 10
+        msp, recp = timed_steps(sp, Kp, 3, sch=2)
+        msp = replicas.job_time_ms(msp, device="cuda")
+        cyc_p = float(np.mean([r["cycles"] for r in recp]))
+        forms["neumann_polycrystal"] = {
+            "workload": "2048^2, h = 804/2048, scheme 2, M = 1, eps = 0.25, beta = 0.9, s = 1, mean 0.285 with "
+                        "three 16-cell seeds on y = 0, periodic x / homogeneous Neumann y, FP64, tol 1e-10",
+            "steps_per_s": world * Kp / (msp * 1e-3), "vcycles_per_step": cyc_p,
+            "cell_updates_per_s": world * Kp * Np * Np / (msp * 1e-3), "steps": Kp}
+        sp.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -46,6 +46,14 @@ extern "C" {
 #define MPFC_GUESS_EXTRAP 1  /* phi^(0) = 2 phi^k - phi^{k-1}                              */
 #define MPFC_GUESS_LEARNED 2 /* extrapolation plus the learned correction (mpfc_set_guess_model) */
 
+/* Boundary conditions (App. A): periodic in both directions, (A.8)-(A.9); or, as in the
+ * polycrystal run of Sec. 4.5, periodic in x and homogeneous Neumann in y with the ghost
+ * rule (A.7), phi_{i,0} = phi_{i,1}, phi_{i,n+1} = phi_{i,n}, applied to phi, mu, kappa
+ * on every multigrid level.  The Neumann rule is available for MPFC_FP64 handles with
+ * the PREV or EXTRAP guess (not in batches). */
+#define MPFC_BC_PERIODIC 0
+#define MPFC_BC_NEUMANN_Y 1
+
 typedef struct {
   int m, n;          /* cells in x and y; the hierarchy halves both while they stay even
                         and at least `coarsest` cells per side remain                    */
@@ -62,6 +70,7 @@ typedef struct {
   int precision;     /* MPFC_FP64 or MPFC_FP32_INNER                                      */
   int guess;         /* MPFC_GUESS_*                                                      */
   int inner_cycles;  /* MPFC_FP32_INNER: FP32 V-cycles per FP64 outer iteration (0 = 2)   */
+  int bc;            /* MPFC_BC_PERIODIC (default) or MPFC_BC_NEUMANN_Y                   */
 } mpfc_params;
 
 typedef struct {

@@ -68,7 +68,7 @@ __global__ void kb_smooth(const BItem* __restrict__ items, int n, const Lev* __r
     const int id = w.inst * kMaxLevels + w.level;
     Lev L = levs[id];
     int x = w.x0 + threadIdx.x, j = w.y0 + threadIdx.y;
-    if (x < (L.m >> 1) && j < L.n) smooth_cell<SCH>(L, coefs[id], 2 * x + ((j + color) & 1), j);
+    if (x < (L.m >> 1) && j < L.n) smooth_cell<SCH>(L, coefs[id], coefs[id], 2 * x + ((j + color) & 1), j);
   }
 }
 
@@ -511,6 +511,7 @@ size_t carve_batch(mpfc_batch_s* B, int count, const mpfc_params* each, char* ba
       Lev v;
       v.m = m;
       v.n = n;
+      v.nyn = 0;   // batches are periodic
       v.h = h;
       v.phi = c.take<double>(G);
       v.mu = c.take<double>(G);
@@ -663,7 +664,7 @@ extern "C" size_t mpfc_batch_workspace_bytes(int count, const mpfc_params* each)
   for (int i = 0; i < count; ++i) {
     if (mpfc_workspace_bytes(&each[i]) == 0) return 0;
     if (!same_solver_settings(each[i], each[0]) || each[i].precision != MPFC_FP64 ||
-        each[i].guess == MPFC_GUESS_LEARNED)
+        each[i].guess == MPFC_GUESS_LEARNED || each[i].bc != MPFC_BC_PERIODIC)
       return 0;
   }
   return carve_batch(nullptr, count, each, nullptr);
@@ -707,7 +708,7 @@ extern "C" int mpfc_batch_create(int count, const mpfc_params* each, void* d_wor
       const mpfc_params& p = each[i];
       for (int s = 0; s < 2; ++s)
         for (int l = 0; l < B->nlev[i]; ++l)
-          B->coef[s][(size_t)i * kMaxLevels + l] = mpfc_coef(&p, s + 1, B->lev[(size_t)i * kMaxLevels + l].h);
+          B->coef[s][(size_t)i * kMaxLevels + l] = mpfc_coef(&p, s + 1, B->lev[(size_t)i * kMaxLevels + l].h, 4);
       for (int s = 0; s < 2; ++s) {
         SourceArgs& A = B->src[s][i];
         A.phik = B->state[3 * i];

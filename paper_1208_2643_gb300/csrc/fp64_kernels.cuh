@@ -28,7 +28,7 @@ struct SourceArgs {
 template <int SCH>
 __device__ __forceinline__ void source_cell(const Lev& L, const SourceArgs& A, int i, int j) {
   int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
   double ih2 = 1.0 / (L.h * L.h);
@@ -66,7 +66,7 @@ __global__ void k_source_guess(Lev L, SourceArgs A) {
 // kappa0 = S3 + theta Delta_h phi0
 __device__ __forceinline__ void guess_kappa_cell(const Lev& L, const Coef& k, int i, int j) {
   int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
   const double* f = L.phi;
   double sum = (f[(size_t)j * m + im] + f[(size_t)j * m + ip]) + (f[(size_t)jm * m + i] + f[(size_t)jp * m + i]);
@@ -84,7 +84,7 @@ static __global__ void k_guess_kappa(Lev L, Coef k) {
 template <int SCH>
 __device__ __forceinline__ void guess_mu_cell(const Lev& L, const Coef& k, int i, int j) {
   int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
   const double* f = L.ka;
   double sum = (f[(size_t)j * m + im] + f[(size_t)j * m + ip]) + (f[(size_t)jm * m + i] + f[(size_t)jp * m + i]);
@@ -107,10 +107,14 @@ __global__ void k_guess_mu(Lev L, Coef k) {
 // `color` (0 = red, (i+j) even).  Cells of one colour only read the other colour,
 // so a half sweep is exactly parallel.
 // ---------------------------------------------------------------------------
+// Next to a Neumann boundary (L.nyn, rows 0 and n-1) the ghost neighbour is the cell's
+// own unknown (App. A, (A.7)): it leaves the neighbour sums and the cell system uses
+// the coefficients of three neighbours, kb.  Rows are warp-uniform, so the branch
+// does not diverge, and periodic levels never take it.
 template <int SCH>
-__device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k, int i, int j) {
+__device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const Coef& kb, int i, int j) {
   int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
   double* __restrict__ phi = L.phi;
@@ -121,6 +125,13 @@ __device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k, int i, 
   double ska = (__ldg(ka + w) + __ldg(ka + e)) + (__ldg(ka + s) + __ldg(ka + nn));
   double sph = (__ldg(phi + w) + __ldg(phi + e)) + (__ldg(phi + s) + __ldg(phi + nn));
   double p = phi[c];
+  const bool edge = L.nyn && (j == 0 || j == L.n - 1);
+  if (edge) {   // the ghost was read as the cell's current value: take it out again
+    smu -= mu[c];
+    ska -= ka[c];
+    sph -= p;
+  }
+  const Coef& k = edge ? kb : k0;
   double R1 = fma(k.cmu, smu, __ldg(L.S1 + c));
   double R3 = fma(k.th2, sph, __ldg(L.S3 + c));
   // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
@@ -161,11 +172,11 @@ __device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k, int i, 
 }
 
 template <int SCH>
-__global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, int color) {
+__global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, Coef kb, int color) {
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= (L.m >> 1) || j >= L.n) return;
-  smooth_cell<SCH>(L, k, 2 * x + ((j + color) & 1), j);
+  smooth_cell<SCH>(L, k, kb, 2 * x + ((j + color) & 1), j);
 }
 
 // ---------------------------------------------------------------------------
@@ -175,7 +186,7 @@ template <int SCH>
 __device__ __forceinline__ void resid_at(const Lev& L, const Coef& k, int i, int j, double& r1, double& r2,
                                          double& r3) {
   int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
   const double* phi = L.phi;
@@ -257,7 +268,7 @@ __global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
 template <int SCH>
 __device__ __forceinline__ void tau_cell(const Lev& C, const Coef& k, int i, int j) {
   int m = C.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, C.n), jp = wrapm(j + 1, C.n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, C.n, C.nyn), jp = ywrap(j + 1, C.n, C.nyn);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
   const double* phi = C.phi;
@@ -303,6 +314,7 @@ struct ProlongArgs {
   const double *ophi, *omu, *oka;   // coarse R u_f before it
   double *fphi, *fmu, *fka;         // fine u (in/out)
   int mc, nc;
+  int nyn;                          // Neumann rule in y (ghost coarse row = boundary row)
 };
 
 // One thread per coarse cell; the block first stages e = u_c - b_c on its
@@ -310,11 +322,11 @@ struct ProlongArgs {
 // is formed once, then writes the bilinear correction into its 2x2 fine children.
 constexpr int kPTX = 32, kPTY = 8;
 __device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, const double* __restrict__ co,
-                                              double* __restrict__ f, int mc, int nc, double (*E)[kPTX + 2], int I0,
-                                              int J0) {
+                                              double* __restrict__ f, int mc, int nc, int nyn, double (*E)[kPTX + 2],
+                                              int I0, int J0) {
   for (int t = threadIdx.y * kPTX + threadIdx.x; t < (kPTX + 2) * (kPTY + 2); t += kPTX * kPTY) {
     int ty = t / (kPTX + 2), tx = t % (kPTX + 2);
-    int I = wrapm(I0 + tx - 1, mc), J = wrapm(J0 + ty - 1, nc);
+    int I = wrapm(I0 + tx - 1, mc), J = ywrap(J0 + ty - 1, nc, nyn);
     if (I0 + tx - 1 < mc + 1 && J0 + ty - 1 < nc + 1) {
       size_t id = (size_t)J * mc + I;
       E[ty][tx] = __ldg(cn + id) - __ldg(co + id);
@@ -342,9 +354,9 @@ __device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, con
 
 // The block's (kPTX x kPTY) coarse tile at (I0, J0): all three components.
 __device__ __forceinline__ void prolong_tile(const ProlongArgs& A, double (*E)[kPTX + 2], int I0, int J0) {
-  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, E, I0, J0);
-  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, E, I0, J0);
-  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, E, I0, J0);
+  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, A.nyn, E, I0, J0);
+  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, A.nyn, E, I0, J0);
+  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, A.nyn, E, I0, J0);
 }
 
 static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
@@ -360,9 +372,10 @@ static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
 // warp.  Stops one iteration after the update falls below 1e-15 (1 + |phi|_inf);
 // at most 40 iterations.  mu and kappa are then recovered from rows 3 and 2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t) {
+__device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t, int nyn) {
   int i = t % m, j = t / m;
-  return (f[j * m + wrapm(i - 1, m)] + f[j * m + wrapm(i + 1, m)]) + (f[wrapm(j - 1, n) * m + i] + f[wrapm(j + 1, n) * m + i]);
+  return (f[j * m + wrapm(i - 1, m)] + f[j * m + wrapm(i + 1, m)]) +
+         (f[ywrap(j - 1, n, nyn) * m + i] + f[ywrap(j + 1, n, nyn) * m + i]);
 }
 
 template <int SCH>
@@ -398,18 +411,20 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
   const float cf = (float)k.c, ih2f = (float)k.ih2, gamf = (float)k.gam;
   bool extra = false;
   for (int it = 0; it < 40; ++it) {
-    for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
+    const int nyn = C.nyn;
+    for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t, nyn) - 4.0 * ph[t]);
     __syncwarp();
     for (int t = lane; t < G; t += 32)
-      muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t) - 4.0 * kap[t]);
+      muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t, nyn) - 4.0 * kap[t]);
     __syncwarp();
     for (int t = lane; t < G; t += 32)
-      Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t) - 4.0 * muv[t]));
+      Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t, nyn) - 4.0 * muv[t]));
     for (int idx = lane; idx < G * G; idx += 32) {
       int r = idx / G, col = idx % G;
       int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
+      // a Neumann ghost is the cell itself, so it lands on the diagonal (count 3 - 4)
       int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
-                (ci == ri && cj == wrapm(rj - 1, n)) + (ci == ri && cj == wrapm(rj + 1, n));
+                (ci == ri && cj == ywrap(rj - 1, n, nyn)) + (ci == ri && cj == ywrap(rj + 1, n, nyn));
       float Lrc = ih2f * ((float)cnt - (r == col ? 4.f : 0.f));
       Jm[r * W + col] = K3f[idx] - cf * Lrc * (gamf + (float)dg_of<SCH>(ph[col], pk[col]));
     }
@@ -464,10 +479,10 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
     if (extra || !(dmax == dmax)) break;
     if ((double)dmax <= 1e-15 * (1.0 + umax)) extra = true;
   }
-  for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t) - 4.0 * ph[t]);
+  for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t, C.nyn) - 4.0 * ph[t]);
   __syncwarp();
   for (int t = lane; t < G; t += 32) {
-    muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t) - 4.0 * kap[t]);
+    muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t, C.nyn) - 4.0 * kap[t]);
     C.phi[t] = ph[t];
     C.ka[t] = kap[t];
     C.mu[t] = muv[t];
@@ -628,7 +643,7 @@ __global__ void k_commit(const double* __restrict__ phinew, double* phik, double
 }
 
 // ---------------------------------------------------------------------------
-// Diagnostics: mass and energy sums, periodic Poisson multigrid for the -1 norm.
+// Diagnostics: mass and energy sums, Poisson multigrid for the -1 norm.
 // ---------------------------------------------------------------------------
 static __global__ void k_sum1(const double* __restrict__ f, int G, Ctl* ctl, double* partials) {
   double v[1] = {0.0};
@@ -638,14 +653,17 @@ static __global__ void k_sum1(const double* __restrict__ f, int G, Ctl* ctl, dou
 
 // sums: 0 phi^4, 1 phi^2, 2 |grad phi|^2 (edge differences), 3 (Delta_h phi)^2 h^4,
 // 4 psi * xi, 5 |grad (phi - phi_prev)|^2
+// With the Neumann rule the north edge of the top row has zero difference (ghost =
+// boundary row) and the bottom row's south edge is never counted, as App. A's
+// Neumann grid has only the n - 1 interior north-south edges.
 static __global__ void k_energy_sums(const double* __restrict__ phi, const double* __restrict__ phip,
-                              const double* __restrict__ psi, const double* __restrict__ xi, int m, int n, Ctl* ctl,
-                              double* partials) {
+                              const double* __restrict__ psi, const double* __restrict__ xi, int m, int n, int nyn,
+                              Ctl* ctl, double* partials) {
   double v[6] = {0, 0, 0, 0, 0, 0};
   int G = m * n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
     int i = t % m, j = t / m;
-    int ip = wrapm(i + 1, m), im = wrapm(i - 1, m), jp = wrapm(j + 1, n), jm = wrapm(j - 1, n);
+    int ip = wrapm(i + 1, m), im = wrapm(i - 1, m), jp = ywrap(j + 1, n, nyn), jm = ywrap(j - 1, n, nyn);
     double p = phi[t];
     double pe = phi[j * m + ip], pw = phi[j * m + im], pn = phi[jp * m + i], ps = phi[jm * m + i];
     double p2 = p * p;
@@ -670,21 +688,27 @@ static __global__ void k_sub_mean(const double* __restrict__ f, double* __restri
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) out[t] = f[t] - mean;
 }
 
-// Red-black Gauss-Seidel half sweep for -Delta_h x = f (periodic).
-static __global__ void k_pois_smooth(double* __restrict__ x, const double* __restrict__ f, int m, int n, double h2,
-                              int color) {
+// Red-black Gauss-Seidel half sweep for -Delta_h x = f (periodic, or Neumann in y:
+// a boundary row's ghost is its own unknown, so it has three neighbours).
+static __global__ void k_pois_smooth(double* __restrict__ x, const double* __restrict__ f, int m, int n, int nyn,
+                                     double h2, int color) {
   int xi = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (xi >= (m >> 1) || j >= n) return;
   int i = 2 * xi + ((j + color) & 1);
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, n), jp = wrapm(j + 1, n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, n, nyn), jp = ywrap(j + 1, n, nyn);
   double s = (x[j * m + im] + x[j * m + ip]) + (x[jm * m + i] + x[jp * m + i]);
-  x[j * m + i] = 0.25 * (s + h2 * f[j * m + i]);
+  if (nyn && (j == 0 || j == n - 1)) {
+    s -= x[j * m + i];
+    x[j * m + i] = (s + h2 * f[j * m + i]) / 3.0;
+  } else {
+    x[j * m + i] = 0.25 * (s + h2 * f[j * m + i]);
+  }
 }
 
 // coarse f = R (f + Delta_h x), coarse x = 0; also the sum of squared fine residuals
 static __global__ void k_pois_restrict(const double* __restrict__ x, const double* __restrict__ f, double* __restrict__ fc,
-                                double* __restrict__ xc, int mc, int nc, double ih2) {
+                                double* __restrict__ xc, int mc, int nc, int nyn, double ih2) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mc || J >= nc) return;
@@ -693,7 +717,7 @@ static __global__ void k_pois_restrict(const double* __restrict__ x, const doubl
   for (int dj = 0; dj < 2; ++dj)
     for (int di = 0; di < 2; ++di) {
       int i = 2 * I + di, j = 2 * J + dj;
-      int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, n), jp = wrapm(j + 1, n);
+      int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, n, nyn), jp = ywrap(j + 1, n, nyn);
       double lap = ((x[j * m + im] + x[j * m + ip]) + (x[jm * m + i] + x[jp * m + i]) - 4.0 * x[j * m + i]) * ih2;
       acc += f[j * m + i] + lap;
     }
@@ -701,11 +725,11 @@ static __global__ void k_pois_restrict(const double* __restrict__ x, const doubl
   xc[J * mc + I] = 0.0;
 }
 
-static __global__ void k_pois_prolong(const double* __restrict__ xc, double* __restrict__ x, int mc, int nc) {
+static __global__ void k_pois_prolong(const double* __restrict__ xc, double* __restrict__ x, int mc, int nc, int nyn) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mc || J >= nc) return;
-  int Im = wrapm(I - 1, mc), Ip = wrapm(I + 1, mc), Jm = wrapm(J - 1, nc), Jp = wrapm(J + 1, nc);
+  int Im = wrapm(I - 1, mc), Ip = wrapm(I + 1, mc), Jm = ywrap(J - 1, nc, nyn), Jp = ywrap(J + 1, nc, nyn);
   auto X = [&](int a, int b) { return xc[b * mc + a]; };
   double e00 = X(I, J), eW = X(Im, J), eE = X(Ip, J), eS = X(I, Jm), eN = X(I, Jp);
   double eSW = X(Im, Jm), eSE = X(Ip, Jm), eNW = X(Im, Jp), eNE = X(Ip, Jp);
@@ -719,7 +743,7 @@ static __global__ void k_pois_prolong(const double* __restrict__ xc, double* __r
 }
 
 // Coarsest Poisson level: `sweeps` red-black sweeps in one CTA, then the mean removed.
-static __global__ void k_pois_coarse(double* x, const double* f, int m, int n, double h2, int sweeps) {
+static __global__ void k_pois_coarse(double* x, const double* f, int m, int n, int nyn, double h2, int sweeps) {
   extern __shared__ double xs[];
   int G = m * n;
   for (int t = threadIdx.x; t < G; t += blockDim.x) xs[t] = x[t];
@@ -729,7 +753,8 @@ static __global__ void k_pois_coarse(double* x, const double* f, int m, int n, d
       for (int t = threadIdx.x; t < G; t += blockDim.x) {
         int i = t % m, j = t / m;
         if (((i + j) & 1) != color) continue;
-        xs[t] = 0.25 * (nbsum_s(xs, m, n, t) + h2 * f[t]);
+        if (nyn && (j == 0 || j == n - 1)) xs[t] = (nbsum_s(xs, m, n, t, nyn) - xs[t] + h2 * f[t]) / 3.0;
+        else xs[t] = 0.25 * (nbsum_s(xs, m, n, t, nyn) + h2 * f[t]);
       }
       __syncthreads();
     }
@@ -743,13 +768,13 @@ static __global__ void k_pois_coarse(double* x, const double* f, int m, int n, d
 }
 
 // sum of squared residuals of -Delta_h x = f, and sum of f^2
-static __global__ void k_pois_resnorm(const double* __restrict__ x, const double* __restrict__ f, int m, int n, double ih2,
-                               Ctl* ctl, double* partials) {
+static __global__ void k_pois_resnorm(const double* __restrict__ x, const double* __restrict__ f, int m, int n, int nyn,
+                               double ih2, Ctl* ctl, double* partials) {
   double v[2] = {0.0, 0.0};
   int G = m * n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
     int i = t % m, j = t / m;
-    int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, n), jp = wrapm(j + 1, n);
+    int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, n, nyn), jp = ywrap(j + 1, n, nyn);
     double lap = ((x[j * m + im] + x[j * m + ip]) + (x[jm * m + i] + x[jp * m + i]) - 4.0 * x[t]) * ih2;
     double r = f[t] + lap;
     v[0] += r * r;

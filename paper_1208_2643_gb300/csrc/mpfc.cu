@@ -79,6 +79,9 @@ static bool params_valid(const mpfc_params* p) {
   if (p->precision != MPFC_FP64 && p->precision != MPFC_FP32_INNER) return false;
   if (p->guess < MPFC_GUESS_PREV || p->guess > MPFC_GUESS_LEARNED) return false;
   if (p->inner_cycles < 0 || p->inner_cycles > 64) return false;
+  if (p->bc != MPFC_BC_PERIODIC && p->bc != MPFC_BC_NEUMANN_Y) return false;
+  // the mixed conditions are built for the FP64 path with the analytic guesses
+  if (p->bc == MPFC_BC_NEUMANN_Y && (p->precision != MPFC_FP64 || p->guess == MPFC_GUESS_LEARNED)) return false;
   int L = mpfc_num_levels(p->m, p->n, p->coarsest);
   int mc = p->m >> (L - 1), nc = p->n >> (L - 1);
   if (mc * nc > kMaxCoarseCells) return false;
@@ -86,7 +89,9 @@ static bool params_valid(const mpfc_params* p) {
   return true;
 }
 
-Coef mpfc_coef(const mpfc_params* p, int scheme, double h) {
+// nb: face neighbours that are not ghosts (4, or 3 next to a Neumann boundary, whose
+// ghost is the cell's own unknown and so joins the diagonal).
+Coef mpfc_coef(const mpfc_params* p, int scheme, double h, int nb) {
   Coef k;
   double alpha = 1.0 - p->epsilon;
   if (scheme == 1) {
@@ -101,10 +106,10 @@ Coef mpfc_coef(const mpfc_params* p, int scheme, double h) {
   k.omega = p->omega;
   double h2 = h * h;
   k.cmu = k.c / h2;
-  k.a = 4.0 * k.c / h2;
+  k.a = nb * k.c / h2;
   k.ih2 = 1.0 / h2;
-  k.b = 4.0 / h2;
-  k.b3 = 4.0 * k.theta / h2;
+  k.b = nb / h2;
+  k.b3 = nb * k.theta / h2;
   k.th2 = k.theta / h2;
   k.D0 = 1.0 + k.a * k.gam + k.a * k.b * k.b3;
   k.Q0 = k.gam + k.b * k.b3;
@@ -151,6 +156,7 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
     Lev& v = lev[l];
     v.m = m;
     v.n = n;
+    v.nyn = p->bc == MPFC_BC_NEUMANN_Y;
     v.h = h;
     v.phi = c.take<double>(G);
     v.mu = c.take<double>(G);
@@ -211,7 +217,9 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
     for (int i = 0; i < m; ++i) {
       int r = j * m + i;
       Lm[(size_t)r * G + r] -= 4.0 * ih2;
-      int nb[4] = {j * m + (i + m - 1) % m, j * m + (i + 1) % m, ((j + n - 1) % n) * m + i, ((j + 1) % n) * m + i};
+      // a Neumann ghost row is the boundary row itself, which folds it into the diagonal
+      int js = C.nyn ? (j > 0 ? j - 1 : 0) : (j + n - 1) % n, jn = C.nyn ? (j < n - 1 ? j + 1 : n - 1) : (j + 1) % n;
+      int nb[4] = {j * m + (i + m - 1) % m, j * m + (i + 1) % m, js * m + i, jn * m + i};
       for (int t = 0; t < 4; ++t) Lm[(size_t)r * G + nb[t]] += ih2;
     }
   for (int r = 0; r < G; ++r)
@@ -245,7 +253,10 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
   H->ws_bytes = bytes;
   carve(H, p, (char*)d_workspace);
   for (int s = 0; s < 2; ++s)
-    for (int l = 0; l < H->nlev; ++l) H->coef[s][l] = mpfc_coef(p, s + 1, H->lev[l].h);
+    for (int l = 0; l < H->nlev; ++l) {
+      H->coef[s][l] = mpfc_coef(p, s + 1, H->lev[l].h, 4);
+      H->coefb[s][l] = mpfc_coef(p, s + 1, H->lev[l].h, 3);
+    }
   int rc = MPFC_OK;
   do {
     cudaError_t e;
@@ -332,11 +343,11 @@ int mpfc_reduce_blocks(size_t G) {
 }
 
 template <int SCH>
-static void launch_smooth(const Lev& L, const Coef& k, int sweeps, cudaStream_t s) {
+static void launch_smooth(const Lev& L, const Coef& k, const Coef& kb, int sweeps, cudaStream_t s) {
   dim3 g = grid_for(L.m / 2, L.n, kBlk2d);
   for (int sw = 0; sw < sweeps; ++sw) {
-    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, 0);
-    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, 1);
+    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, kb, 0);
+    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, kb, 1);
   }
 }
 
@@ -357,7 +368,7 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
   for (int l = 0; l < L - 1; ++l) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
-    launch_smooth<SCH>(F, H->coef[SCH - 1][l], p.nu1, s);
+    launch_smooth<SCH>(F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu1, s);
     k_resid_restrict<SCH><<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(F, C, H->coef[SCH - 1][l], 1);
     k_tau<SCH><<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(C, H->coef[SCH - 1][l + 1]);
   }
@@ -365,9 +376,9 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
   for (int l = L - 2; l >= 0; --l) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
-    ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n};
+    ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n, C.nyn};
     k_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(A);
-    launch_smooth<SCH>(F, H->coef[SCH - 1][l], p.nu2, s);
+    launch_smooth<SCH>(F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu2, s);
   }
 }
 
@@ -705,25 +716,25 @@ static int poisson_solve(mpfc_s* H, const double* rhs) {
       const Lev& F = H->lev[l];
       dim3 g = grid_for(F.m / 2, F.n, kBlk2d);
       for (int sw = 0; sw < 2; ++sw)
-        for (int c = 0; c < 2; ++c) k_pois_smooth<<<g, kBlk2d, 0, s>>>(H->px[l], H->pf[l], F.m, F.n, F.h * F.h, c);
+        for (int c = 0; c < 2; ++c) k_pois_smooth<<<g, kBlk2d, 0, s>>>(H->px[l], H->pf[l], F.m, F.n, F.nyn, F.h * F.h, c);
       const Lev& C = H->lev[l + 1];
       k_pois_restrict<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(H->px[l], H->pf[l], H->pf[l + 1], H->px[l + 1],
-                                                                     C.m, C.n, 1.0 / (F.h * F.h));
+                                                                     C.m, C.n, C.nyn, 1.0 / (F.h * F.h));
     }
     const Lev& Cc = H->lev[L - 1];
     k_pois_coarse<<<1, 128, sizeof(double) * (Cc.m * Cc.n + 1), s>>>(H->px[L - 1], H->pf[L - 1], Cc.m, Cc.n,
-                                                                      Cc.h * Cc.h, 200);
+                                                                      Cc.nyn, Cc.h * Cc.h, 200);
     for (int l = L - 2; l >= 0; --l) {
       const Lev& F = H->lev[l];
       const Lev& C = H->lev[l + 1];
-      k_pois_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(H->px[l + 1], H->px[l], C.m, C.n);
+      k_pois_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(H->px[l + 1], H->px[l], C.m, C.n, C.nyn);
       dim3 g = grid_for(F.m / 2, F.n, kBlk2d);
       for (int sw = 0; sw < 2; ++sw)
-        for (int c = 0; c < 2; ++c) k_pois_smooth<<<g, kBlk2d, 0, s>>>(H->px[l], H->pf[l], F.m, F.n, F.h * F.h, c);
+        for (int c = 0; c < 2; ++c) k_pois_smooth<<<g, kBlk2d, 0, s>>>(H->px[l], H->pf[l], F.m, F.n, F.nyn, F.h * F.h, c);
     }
     const Lev& F0 = H->lev[0];
-    k_pois_resnorm<<<mpfc_reduce_blocks(G0), 256, 0, s>>>(H->px[0], H->pf[0], F0.m, F0.n, 1.0 / (F0.h * F0.h),
-                                                          H->ctl, H->partials);
+    k_pois_resnorm<<<mpfc_reduce_blocks(G0), 256, 0, s>>>(H->px[0], H->pf[0], F0.m, F0.n, F0.nyn,
+                                                          1.0 / (F0.h * F0.h), H->ctl, H->partials);
     CK(cudaGetLastError());
     double v[2];
     int rc = read_sums(H, v, 2);
@@ -740,7 +751,7 @@ extern "C" int mpfc_energy(mpfc_t* H, mpfc_energy_t* out) {
   if (rc) return rc;
   size_t G = (size_t)H->p.m * H->p.n;
   k_energy_sums<<<mpfc_reduce_blocks(G), 256, 0, H->stream>>>(H->phik, H->phikm1, H->psik, H->px[0], H->p.m, H->p.n,
-                                                              H->ctl, H->partials);
+                                                              H->lev[0].nyn, H->ctl, H->partials);
   CK(cudaGetLastError());
   double v[6];
   rc = read_sums(H, v, 6);
@@ -809,8 +820,8 @@ extern "C" int mpfc_op_smooth(mpfc_t* H, int scheme, int level, double* phi, dou
   if (!level_ok(H, level) || (scheme != 1 && scheme != 2) || sweeps < 0 || (scheme == 2 && !phik))
     return MPFC_ERR_INVALID;
   Lev L = user_level(H, level, phi, mu, kappa, S1, S2, S3, phik);
-  if (scheme == 1) launch_smooth<1>(L, H->coef[0][level], sweeps, H->stream);
-  else launch_smooth<2>(L, H->coef[1][level], sweeps, H->stream);
+  if (scheme == 1) launch_smooth<1>(L, H->coef[0][level], H->coefb[0][level], sweeps, H->stream);
+  else launch_smooth<2>(L, H->coef[1][level], H->coefb[1][level], sweeps, H->stream);
   CK(cudaGetLastError());
   return MPFC_OK;
 }
@@ -855,7 +866,7 @@ extern "C" int mpfc_op_prolong(mpfc_t* H, int level, const double* phi_c_new, co
                                const double* kappa_c_old, double* phi, double* mu, double* kappa) {
   if (!level_ok(H, level) || level + 1 >= H->nlev) return MPFC_ERR_INVALID;
   const Lev& C = H->lev[level + 1];
-  ProlongArgs A{phi_c_new, mu_c_new, kappa_c_new, phi_c_old, mu_c_old, kappa_c_old, phi, mu, kappa, C.m, C.n};
+  ProlongArgs A{phi_c_new, mu_c_new, kappa_c_new, phi_c_old, mu_c_old, kappa_c_old, phi, mu, kappa, C.m, C.n, C.nyn};
   k_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, H->stream>>>(A);
   CK(cudaGetLastError());
   return MPFC_OK;

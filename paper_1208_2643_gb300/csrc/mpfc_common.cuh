@@ -15,6 +15,7 @@ constexpr int kInfoCap = 1024;         // per-step records per mpfc_step chunk
 // One grid level: SoA planes, row-major [n][m].
 struct Lev {
   int m, n;
+  int nyn;                  // 1: homogeneous Neumann in y (ghost row = boundary row), 0: periodic
   double h;
   double *phi, *mu, *ka;    // u = (phi, mu, kappa)
   double *S1, *S2, *S3;     // FAS source (tau-corrected below the finest level)
@@ -109,6 +110,11 @@ struct StepRecord {      // mirrors mpfc_step_info
 };
 
 __device__ __forceinline__ int wrapm(int i, int m) { return i < 0 ? i + m : (i >= m ? i - m : i); }
+// Stored row of row j in -1..n: periodic wrap, or with the Neumann rule of App. A
+// ((A.7): phi_{i,0} = phi_{i,1}, phi_{i,n+1} = phi_{i,n}) the boundary row itself.
+__device__ __forceinline__ int ywrap(int j, int n, int nyn) {
+  return nyn ? (j < 0 ? 0 : (j >= n ? n - 1 : j)) : wrapm(j, n);
+}
 
 // Nonlinear term of N^(2) and its derivative (App. B.1: phi^3; App. B.2:
 // chi(phi, phik)(phi + phik)/2 with chi(a, b) = (a^2 + b^2)/2).

@@ -40,6 +40,7 @@ struct mpfc_s {
   int nlev = 0;
   mpfc::Lev lev[mpfc::kMaxLevels];
   mpfc::Coef coef[2][mpfc::kMaxLevels];
+  mpfc::Coef coefb[2][mpfc::kMaxLevels];   // cell systems of Neumann boundary rows (3 neighbours)
   double* phik = nullptr;
   double* phikm1 = nullptr;
   double* psik = nullptr;
@@ -63,7 +64,7 @@ struct mpfc_s {
 void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void mpfc_drop_graphs(mpfc_s* H);
 int mpfc_num_levels(int m, int n, int coarsest);
-mpfc::Coef mpfc_coef(const mpfc_params* p, int scheme, double h);
+mpfc::Coef mpfc_coef(const mpfc_params* p, int scheme, double h, int nb);
 void mpfc_build_K3(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<double>& K3);
 int mpfc_reduce_blocks(size_t G);
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd,

@@ -95,3 +95,17 @@ def crystallite_field(m: int, n: int, h: float, phibar: float, eps: float, count
     if phibar < 0:
         phi = -phi
     return phi + noise * uniform(seed + 1000003, m * n).reshape(n, m)
+
+
+def polycrystal_seeds(m: int, n: int, mean: float, count: int, size_cells: int, amp: float,
+                      seed: int) -> np.ndarray:
+    """Constant density `mean` with `count` small random square perturbations of
+    `size_cells` cells (amplitude amp U(-1, 1)) on the bottom rows y = 0, at seeded
+    random x positions: the nucleation seeds of the polycrystal run, Sec. 4.5."""
+    phi = np.full((n, m), float(mean))
+    xs = uniform(seed, count)
+    noise = uniform(seed + 1, count * size_cells * size_cells).reshape(count, size_cells, size_cells)
+    for k in range(count):
+        x0 = int((xs[k] + 1.0) * 0.5 * (m - size_cells))
+        phi[0:size_cells, x0:x0 + size_cells] += amp * noise[k]
+    return phi

@@ -31,13 +31,17 @@ MPFC_GUESS_PREV = 0
 MPFC_GUESS_EXTRAP = 1
 MPFC_GUESS_LEARNED = 2
 
+MPFC_BC_PERIODIC = 0
+MPFC_BC_NEUMANN_Y = 1
+
 
 class mpfc_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("h", ctypes.c_double), ("M", ctypes.c_double),
                 ("epsilon", ctypes.c_double), ("beta", ctypes.c_double), ("dt", ctypes.c_double),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
-                ("precision", ctypes.c_int), ("guess", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("guess", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("bc", ctypes.c_int)]
 
 
 class mpfc_step_info(ctypes.Structure):
