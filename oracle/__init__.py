@@ -91,6 +91,11 @@ def _load():
         lib.orc_scheme_consts.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, _D, _D, _D]
         lib.orc_num_levels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_set_boundary.argtypes = [ctypes.c_int]
+        lib.orc_set_pinning.argtypes = [ctypes.c_void_p, _D, _D]
+        lib.orc_apply_N_pinned.argtypes = lib.orc_apply_N.argtypes[:11] + [_D, _D, _D, _D]
+        lib.orc_smooth_pinned.argtypes = lib.orc_smooth.argtypes + [_D]
+        lib.orc_coarse_newton_pinned.argtypes = lib.orc_coarse_newton.argtypes + [_D]
+        lib.orc_source_pinned.argtypes = [ctypes.c_int, ctypes.POINTER(_Params), _D, _D, _D, _D, _D, _D, _D, _D]
         _lib = lib
     return _lib
 
@@ -170,19 +175,25 @@ def laplacian(f, h):
     return out
 
 
-def apply_N(scheme, consts, h, phi, mu, kappa, phik=None):
-    """N(u) of App. B.1/B.2 on one grid."""
+def apply_N(scheme, consts, h, phi, mu, kappa, phik=None, W=None):
+    """N(u) of App. B.1/B.2 on one grid; W: pinning weight on the grid (Sec. 4.6)."""
     phi, mu, kappa = _f64(phi), _f64(mu), _f64(kappa)
     phik = _f64(phik) if phik is not None else np.zeros_like(phi)
     out = [np.empty_like(phi) for _ in range(3)]
     c, g, t = consts
-    _load().orc_apply_N(scheme, c, g, t, phi.shape[1], phi.shape[0], h, _p(phi), _p(mu), _p(kappa), _p(phik),
-                        *[_p(o) for o in out])
+    args = (scheme, c, g, t, phi.shape[1], phi.shape[0], h, _p(phi), _p(mu), _p(kappa), _p(phik))
+    if W is None:
+        _load().orc_apply_N(*args, *[_p(o) for o in out])
+    else:
+        _load().orc_apply_N_pinned(*args, _p(_f64(W)), *[_p(o) for o in out])
     return out
 
 
-def residual(scheme, consts, h, u, S, phik=None):
+def residual(scheme, consts, h, u, S, phik=None, W=None):
     """r = S - N(u)."""
+    if W is not None:
+        N = apply_N(scheme, consts, h, *u, phik, W)
+        return [_f64(a) - b for a, b in zip(S, N)]
     phi, mu, kappa = [_f64(x) for x in u]
     S1, S2, S3 = [_f64(x) for x in S]
     phik = _f64(phik) if phik is not None else np.zeros_like(phi)
@@ -193,22 +204,31 @@ def residual(scheme, consts, h, u, S, phik=None):
     return out
 
 
-def source(scheme, p: Params, phik, phikm1, psik):
-    """S of App. B.1 (scheme 1) or App. B.2 (scheme 2)."""
+def source(scheme, p: Params, phik, phikm1, psik, W=None, phihat=None):
+    """S of App. B.1 (scheme 1) or App. B.2 (scheme 2); with a pinning weight W and
+    target phihat, the pinned scheme-2 source of Sec. 4.6."""
     phik, phikm1, psik = _f64(phik), _f64(phikm1), _f64(psik)
     out = [np.empty_like(phik) for _ in range(3)]
-    _load().orc_source(scheme, ctypes.byref(p.c_struct()), _p(phik), _p(phikm1), _p(psik), *[_p(o) for o in out])
+    if W is None:
+        _load().orc_source(scheme, ctypes.byref(p.c_struct()), _p(phik), _p(phikm1), _p(psik), *[_p(o) for o in out])
+    else:
+        _load().orc_source_pinned(scheme, ctypes.byref(p.c_struct()), _p(phik), _p(phikm1), _p(psik), _p(_f64(W)),
+                                  _p(_f64(phihat)), *[_p(o) for o in out])
     return out
 
 
-def smooth(scheme, consts, h, u, S, phik=None, sweeps=1, newton=1, omega=0.8):
+def smooth(scheme, consts, h, u, S, phik=None, sweeps=1, newton=1, omega=0.8, W=None):
     """Red-black nonlinear block Gauss-Seidel sweeps (App. B), relaxed by omega; returns new u."""
     phi, mu, kappa = [_f64(x).copy() for x in u]
     S1, S2, S3 = [_f64(x) for x in S]
     phik = _f64(phik) if phik is not None else np.zeros_like(phi)
     c, g, t = consts
-    _load().orc_smooth(scheme, c, g, t, newton, omega, sweeps, phi.shape[1], phi.shape[0], h, _p(phi), _p(mu),
-                       _p(kappa), _p(S1), _p(S2), _p(S3), _p(phik))
+    args = (scheme, c, g, t, newton, omega, sweeps, phi.shape[1], phi.shape[0], h, _p(phi), _p(mu), _p(kappa), _p(S1),
+            _p(S2), _p(S3), _p(phik))
+    if W is None:
+        _load().orc_smooth(*args)
+    else:
+        _load().orc_smooth_pinned(*args, _p(_f64(W)))
     return phi, mu, kappa
 
 
@@ -235,13 +255,17 @@ def cramer3(A, r):
     return x
 
 
-def coarse_newton(scheme, consts, h, u, S, phik=None):
+def coarse_newton(scheme, consts, h, u, S, phik=None, W=None):
     phi, mu, kappa = [_f64(x).copy() for x in u]
     S1, S2, S3 = [_f64(x) for x in S]
     phik = _f64(phik) if phik is not None else np.zeros_like(phi)
     c, g, t = consts
-    it = _load().orc_coarse_newton(scheme, c, g, t, phi.shape[1], phi.shape[0], h, _p(phi), _p(mu), _p(kappa),
-                                   _p(S1), _p(S2), _p(S3), _p(phik))
+    args = (scheme, c, g, t, phi.shape[1], phi.shape[0], h, _p(phi), _p(mu), _p(kappa), _p(S1), _p(S2), _p(S3),
+            _p(phik))
+    if W is None:
+        it = _load().orc_coarse_newton(*args)
+    else:
+        it = _load().orc_coarse_newton_pinned(*args, _p(_f64(W)))
     return (phi, mu, kappa), it
 
 
@@ -263,6 +287,15 @@ class Solver:
         if getattr(self, "_ctx", None):
             self._lib.orc_destroy(self._ctx)
             self._ctx = None
+
+    def set_pinning(self, weight=None, target=None):
+        """Pinning of Sec. 4.6 (scheme 2): weight W >= 0 and target phihat on the grid;
+        weight None switches it off."""
+        if weight is None:
+            self._lib.orc_set_pinning(self._ctx, None, None)
+        else:
+            self._pin = (_f64(weight), _f64(target))
+            self._lib.orc_set_pinning(self._ctx, _p(self._pin[0]), _p(self._pin[1]))
 
     def set_state(self, phi, phi_prev=None, psi=None):
         phi = _f64(phi)

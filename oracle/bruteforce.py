@@ -43,8 +43,9 @@ def _dg(scheme, phi, phik):
     return 0.25 * (3.0 * phi**2 + 2.0 * phi * phik + phik**2)
 
 
-def newton_solve(scheme, consts, h, S, phik=None, u0=None, tol=1e-14, max_iter=50, ny_neumann=False):
+def newton_solve(scheme, consts, h, S, phik=None, u0=None, tol=1e-14, max_iter=50, ny_neumann=False, W=None):
     """Solves N(u) = S (App. B.1/B.2) by Newton's method with the exact Jacobian.
+    W (optional): pinning weight of Sec. 4.6, which adds -W phi to row 2 of N.
     Returns (phi, mu, kappa) as (n, m) arrays and the final max-norm residual."""
     c, gam, theta = consts
     S1, S2, S3 = [np.asarray(x, dtype=np.float64).ravel() for x in S]
@@ -52,6 +53,7 @@ def newton_solve(scheme, consts, h, S, phik=None, u0=None, tol=1e-14, max_iter=5
     G = m * n
     L = lap_matrix(m, n, h, ny_neumann)
     pk = np.zeros(G) if phik is None else np.asarray(phik, dtype=np.float64).ravel()
+    w = np.zeros(G) if W is None else np.asarray(W, dtype=np.float64).ravel()
     if u0 is None:
         phi, mu, kappa = np.zeros(G), np.zeros(G), np.zeros(G)
     else:
@@ -61,13 +63,13 @@ def newton_solve(scheme, consts, h, S, phik=None, u0=None, tol=1e-14, max_iter=5
     res = np.inf
     for _ in range(max_iter):
         N1 = phi - c * (L @ mu)
-        N2 = mu - _g(scheme, phi, pk) - gam * phi - L @ kappa
+        N2 = mu - _g(scheme, phi, pk) - (gam + w) * phi - L @ kappa
         N3 = kappa - theta * (L @ phi)
         r = np.concatenate([S1 - N1, S2 - N2, S3 - N3])
         res = float(np.max(np.abs(r)))
         if res < tol:
             break
-        D = np.diag(gam + _dg(scheme, phi, pk))
+        D = np.diag(gam + w + _dg(scheme, phi, pk))
         J = np.block([[I, -c * L, Z], [-D, I, -L], [-theta * L, Z, I]])
         du = np.linalg.solve(J, r)
         phi, mu, kappa = phi + du[:G], mu + du[G:2 * G], kappa + du[2 * G:]

@@ -100,7 +100,14 @@ def mass(phi, h):
     return float(h * h * np.sum(phi))
 
 
-def scheme2_identity_terms(phi_new, phi_k, phi_km1, psi_new, psi_k, h, eps, M, beta, s, ny_neumann=False):
+def pin_energy(phi, W, phihat, h):
+    """Pinning energy h^2 sum W (phi - phihat)^2, the discrete form of the term added
+    to E in Sec. 4.6."""
+    return float(h * h * np.sum(W * (phi - phihat) ** 2))
+
+
+def scheme2_identity_terms(phi_new, phi_k, phi_km1, psi_new, psi_k, h, eps, M, beta, s, ny_neumann=False,
+                           W=None, phihat=None):
     """Both sides of the exact energy identity of Sec. 3.4, (3.28):
     tildeF^{k+1} + s beta/M ||psi^{k+1/2}||_{-1}^2 + s^4/2 ||grad_h D_s^2 phi^k||^2 = tildeF^k.
     Returns (lhs, rhs)."""
@@ -109,6 +116,9 @@ def scheme2_identity_terms(phi_new, phi_k, phi_km1, psi_new, psi_k, h, eps, M, b
     tf_old = tilde_F(phi_k, phi_km1, psi_k, h, eps, M, nn)
     psi_half = 0.5 * (psi_new + psi_k)
     diss = s * beta / M * norm_m1_sq(psi_half, h, nn) + 0.5 * grad_sq(phi_new - 2.0 * phi_k + phi_km1, h, nn)
+    if W is not None:   # the pinned energy: the midpoint form makes its change exact (difference of squares)
+        tf_new += pin_energy(phi_new, W, phihat, h)
+        tf_old += pin_energy(phi_k, W, phihat, h)
     return tf_new + diss, tf_old
 
 

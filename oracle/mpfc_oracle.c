@@ -35,6 +35,11 @@
  *  - coarsest level (a few cells per side): dense Newton on all 3*m*n unknowns,
  *    Gaussian elimination with partial pivoting;
  *  - stopping rule: scaled residual sqrt(sum_{c,i,j} r_c^2 / (3mn)) <= tol;
+ *  - pinning (Sec. 4.6, second-order scheme only): the unknown mu is the pinned
+ *    potential mu~ = mu + 2 (phi^{k+1/2} - phihat) W, W the weight; with
+ *    phi^{k+1/2} = (phi + phi^k)/2 this moves W phi into row 2 of N, a pointwise
+ *    linear term (gam -> gam + W_ij), and W (phi^k - 2 phihat) into S2; coarse
+ *    levels use the 2x2 average of W (standard FAS restriction);
  *  - Neumann rows (Sec. 4.5 says only that the solver is easily adapted): explicit
  *    stencils read the ghost row as the boundary row (A.7); in the smoother's cell
  *    system the ghost is the unknown itself, so it leaves the neighbour sum and the
@@ -154,9 +159,11 @@ static double dg_of(int scheme, double phi, double phik) {
  *   N2 = mu    - g(phi) - gam phi - Delta_h kappa
  *   N3 = kappa - theta Delta_h phi
  * phik is only read for scheme 2. */
-void orc_apply_N(int scheme, double c, double gam, double theta, int m, int n, double h,
-                 const double* phi, const double* mu, const double* kappa, const double* phik,
-                 double* N1, double* N2, double* N3) {
+/* W (nullable): pinning weight on this grid (Sec. 4.6); row 2 then reads
+ *   N2 = mu - g(phi) - (gam + W) phi - Delta_h kappa. */
+static void apply_N_w(int scheme, double c, double gam, double theta, int m, int n, double h,
+                      const double* phi, const double* mu, const double* kappa, const double* phik,
+                      const double* W, double* N1, double* N2, double* N3) {
   double* lmu = malloc(sizeof(double) * m * n);
   double* lka = malloc(sizeof(double) * m * n);
   double* lph = malloc(sizeof(double) * m * n);
@@ -167,9 +174,16 @@ void orc_apply_N(int scheme, double c, double gam, double theta, int m, int n, d
     double pk = (scheme == 2) ? phik[k] : 0.0;
     N1[k] = phi[k] - c * lmu[k];
     N2[k] = mu[k] - g_of(scheme, phi[k], pk) - gam * phi[k] - lka[k];
+    if (W) N2[k] -= W[k] * phi[k];
     N3[k] = kappa[k] - theta * lph[k];
   }
   free(lmu); free(lka); free(lph);
+}
+
+void orc_apply_N(int scheme, double c, double gam, double theta, int m, int n, double h,
+                 const double* phi, const double* mu, const double* kappa, const double* phik,
+                 double* N1, double* N2, double* N3) {
+  apply_N_w(scheme, c, gam, theta, m, n, h, phi, mu, kappa, phik, NULL, N1, N2, N3);
 }
 
 /* Source S.
@@ -177,8 +191,20 @@ void orc_apply_N(int scheme, double c, double gam, double theta, int m, int n, d
  * Scheme 2 (App. B.2): S1 = phik + 2 psik/(beta+2/s),
  *   S2 = (alpha/2) phik + 2 Delta_h phitilde, phitilde = (3 phik - phikm1)/2,
  *   S3 = (1/2) Delta_h phik. */
+/* Pinned source (Sec. 4.6, scheme 2): S2 additionally gets W (phi^k - 2 phihat), the
+ * part of 2 W (phi^{k+1/2} - phihat) that does not involve the unknown. */
+static void source_w(int scheme, const orc_params* p, const double* phik, const double* phikm1,
+                     const double* psik, const double* W, const double* phihat, double* S1, double* S2,
+                     double* S3);
+
 void orc_source(int scheme, const orc_params* p, const double* phik, const double* phikm1,
                 const double* psik, double* S1, double* S2, double* S3) {
+  source_w(scheme, p, phik, phikm1, psik, NULL, NULL, S1, S2, S3);
+}
+
+static void source_w(int scheme, const orc_params* p, const double* phik, const double* phikm1,
+                     const double* psik, const double* W, const double* phihat, double* S1, double* S2,
+                     double* S3) {
   int m = p->m, n = p->n, N = m * n;
   double alpha = 1.0 - p->eps;
   double* lap = malloc(sizeof(double) * N);
@@ -198,6 +224,7 @@ void orc_source(int scheme, const orc_params* p, const double* phik, const doubl
     for (int k = 0; k < N; ++k) {
       S1[k] = phik[k] + 2.0 * psik[k] / (p->beta + 2.0 / p->s);
       S2[k] = 0.5 * alpha * phik[k] + 2.0 * lap_t[k];
+      if (W) S2[k] += W[k] * (phik[k] - 2.0 * phihat[k]);
       S3[k] = 0.5 * lap[k];
     }
     free(tl); free(lap_t);
@@ -238,7 +265,7 @@ void orc_cramer3(const double* A, const double* r, double* x) {
  *                                            ->  q = chi/2,  e = chi phik / 2  */
 static void visit_cell(const orc_consts* k, int newton, int m, int n, double h, int i, int j,
                        double* phi, double* mu, double* kappa, const double* S1, const double* S2,
-                       const double* S3, const double* phik) {
+                       const double* S3, const double* phik, const double* W) {
   int id = j * m + i;
   double h2 = h * h;
   double p = phi[id];
@@ -259,8 +286,9 @@ static void visit_cell(const orc_consts* k, int newton, int m, int n, double h, 
   double smu = real_nb_sum(mu, m, n, i, j, &d);
   double ska = real_nb_sum(kappa, m, n, i, j, &d);
   double sph = real_nb_sum(phi, m, n, i, j, &d);
+  double w = W ? W[id] : 0.0;   /* pinning weight: a pointwise linear term of row 2 */
   double A[9] = {1.0, d * k->c / h2, 0.0,
-                 -(k->gam + q), 1.0, d / h2,
+                 -(k->gam + w + q), 1.0, d / h2,
                  d * k->theta / h2, 0.0, 1.0};
   double r[3] = {S1[id] + k->c / h2 * smu,
                  S2[id] + e + ska / h2,
@@ -274,16 +302,22 @@ static void visit_cell(const orc_consts* k, int newton, int m, int n, double h, 
 }
 
 /* sweeps full red-black passes: red cells ((i+j) even) first, then black. */
-void orc_smooth(int scheme, double c, double gam, double theta, int newton, double omega, int sweeps, int m,
-                int n, double h, double* phi, double* mu, double* kappa, const double* S1, const double* S2,
-                const double* S3, const double* phik) {
+static void smooth_w(int scheme, double c, double gam, double theta, int newton, double omega, int sweeps, int m,
+                     int n, double h, double* phi, double* mu, double* kappa, const double* S1, const double* S2,
+                     const double* S3, const double* phik, const double* W) {
   orc_consts k = {c, gam, theta, scheme, omega};
   for (int sw = 0; sw < sweeps; ++sw)
     for (int color = 0; color < 2; ++color)
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < m; ++i)
           if (((i + j) & 1) == color)
-            visit_cell(&k, newton, m, n, h, i, j, phi, mu, kappa, S1, S2, S3, phik);
+            visit_cell(&k, newton, m, n, h, i, j, phi, mu, kappa, S1, S2, S3, phik, W);
+}
+
+void orc_smooth(int scheme, double c, double gam, double theta, int newton, double omega, int sweeps, int m,
+                int n, double h, double* phi, double* mu, double* kappa, const double* S1, const double* S2,
+                const double* S3, const double* phik) {
+  smooth_w(scheme, c, gam, theta, newton, omega, sweeps, m, n, h, phi, mu, kappa, S1, S2, S3, phik, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -354,9 +388,9 @@ int orc_gauss_solve(int N, double* A, double* b, double* x) {
  *   [ -theta L 0     I  ]
  * Iterates until the update is below 1e-15 (1 + |u|_inf), then takes one
  * more iteration; at most 60 iterations.  Returns the iteration count. */
-int orc_coarse_newton(int scheme, double c, double gam, double theta, int m, int n, double h,
-                      double* phi, double* mu, double* kappa, const double* S1, const double* S2,
-                      const double* S3, const double* phik) {
+static int coarse_newton_w(int scheme, double c, double gam, double theta, int m, int n, double h,
+                           double* phi, double* mu, double* kappa, const double* S1, const double* S2,
+                           const double* S3, const double* phik, const double* W) {
   int G = m * n, N = 3 * G;
   double* A = malloc(sizeof(double) * N * N);
   double* b = malloc(sizeof(double) * N);
@@ -367,7 +401,7 @@ int orc_coarse_newton(int scheme, double c, double gam, double theta, int m, int
   double h2 = h * h;
   int it, extra = -1;
   for (it = 0; it < 60; ++it) {
-    orc_apply_N(scheme, c, gam, theta, m, n, h, phi, mu, kappa, phik, N1, N2, N3);
+    apply_N_w(scheme, c, gam, theta, m, n, h, phi, mu, kappa, phik, W, N1, N2, N3);
     for (int k = 0; k < G; ++k) {
       b[k] = S1[k] - N1[k];
       b[G + k] = S2[k] - N2[k];
@@ -386,7 +420,7 @@ int orc_coarse_newton(int scheme, double c, double gam, double theta, int m, int
         A[r * N + G + r] += 4.0 * c / h2;
         for (int t = 0; t < 4; ++t) A[r * N + G + nbr[t]] -= c / h2;
         /* row block 2: mu - g(phi) - gam phi - Lap kappa */
-        A[(G + r) * N + r] += -(gam + dg_of(scheme, phi[r], pk));
+        A[(G + r) * N + r] += -(gam + (W ? W[r] : 0.0) + dg_of(scheme, phi[r], pk));
         A[(G + r) * N + G + r] += 1.0;
         A[(G + r) * N + 2 * G + r] += 4.0 / h2;
         for (int t = 0; t < 4; ++t) A[(G + r) * N + 2 * G + nbr[t]] -= 1.0 / h2;
@@ -413,6 +447,12 @@ int orc_coarse_newton(int scheme, double c, double gam, double theta, int m, int
   return it + 1;
 }
 
+int orc_coarse_newton(int scheme, double c, double gam, double theta, int m, int n, double h,
+                      double* phi, double* mu, double* kappa, const double* S1, const double* S2,
+                      const double* S3, const double* phik) {
+  return coarse_newton_w(scheme, c, gam, theta, m, n, h, phi, mu, kappa, S1, S2, S3, phik, NULL);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Level hierarchy and the FAS V-cycle                                      */
 /* ------------------------------------------------------------------------ */
@@ -424,6 +464,7 @@ typedef struct {
   double *r1, *r2, *r3;       /* residual scratch                    */
   double *b1, *b2, *b3;       /* R u_f saved for the correction      */
   double* phik;               /* phi^k on this level (scheme 2)      */
+  double* W;                  /* pinning weight (NULL: no pinning)   */
 } orc_level;
 
 typedef struct {
@@ -431,6 +472,7 @@ typedef struct {
   int nlev;
   orc_level lev[ORC_MAX_LEVELS];
   double *phik, *phikm1, *psik;   /* time-level state (Sec. 3)          */
+  double* phihat;                 /* pinning target (Sec. 4.6), finest grid */
   long step_index;
 } orc_ctx;
 
@@ -479,17 +521,36 @@ void orc_destroy(orc_ctx* ctx) {
     orc_level* L = &ctx->lev[l];
     free(L->phi); free(L->mu); free(L->kappa); free(L->S1); free(L->S2); free(L->S3);
     free(L->r1); free(L->r2); free(L->r3); free(L->b1); free(L->b2); free(L->b3); free(L->phik);
+    free(L->W);
   }
-  free(ctx->phik); free(ctx->phikm1); free(ctx->psik);
+  free(ctx->phik); free(ctx->phikm1); free(ctx->psik); free(ctx->phihat);
   free(ctx);
 }
 
 int orc_levels(const orc_ctx* ctx) { return ctx->nlev; }
 
+/* Pinning of Sec. 4.6: weight W >= 0 and target phihat on the finest grid (copied);
+ * coarse levels get the 2x2 averages of W.  weight NULL switches pinning off. */
+void orc_set_pinning(orc_ctx* ctx, const double* weight, const double* target) {
+  for (int l = 0; l < ctx->nlev; ++l) { free(ctx->lev[l].W); ctx->lev[l].W = NULL; }
+  free(ctx->phihat);
+  ctx->phihat = NULL;
+  if (!weight) return;
+  int G = ctx->p.m * ctx->p.n;
+  ctx->phihat = zalloc(G);
+  memcpy(ctx->phihat, target, sizeof(double) * G);
+  ctx->lev[0].W = zalloc(G);
+  memcpy(ctx->lev[0].W, weight, sizeof(double) * G);
+  for (int l = 1; l < ctx->nlev; ++l) {
+    ctx->lev[l].W = zalloc(ctx->lev[l].m * ctx->lev[l].n);
+    orc_restrict(ctx->lev[l].m, ctx->lev[l].n, ctx->lev[l - 1].W, ctx->lev[l].W);
+  }
+}
+
 static void level_residual(const orc_consts* k, orc_level* L) {
   int G = L->m * L->n;
-  orc_apply_N(k->scheme, k->c, k->gam, k->theta, L->m, L->n, L->h, L->phi, L->mu, L->kappa, L->phik,
-              L->r1, L->r2, L->r3);
+  apply_N_w(k->scheme, k->c, k->gam, k->theta, L->m, L->n, L->h, L->phi, L->mu, L->kappa, L->phik, L->W,
+            L->r1, L->r2, L->r3);
   for (int i = 0; i < G; ++i) {
     L->r1[i] = L->S1[i] - L->r1[i];
     L->r2[i] = L->S2[i] - L->r2[i];
@@ -513,14 +574,14 @@ static void vcycle(orc_ctx* ctx, const orc_consts* k, int l) {
   orc_level* F = &ctx->lev[l];
   const orc_params* p = &ctx->p;
   if (l == ctx->nlev - 1) {
-    orc_coarse_newton(k->scheme, k->c, k->gam, k->theta, F->m, F->n, F->h, F->phi, F->mu, F->kappa, F->S1,
-                      F->S2, F->S3, F->phik);
+    coarse_newton_w(k->scheme, k->c, k->gam, k->theta, F->m, F->n, F->h, F->phi, F->mu, F->kappa, F->S1,
+                    F->S2, F->S3, F->phik, F->W);
     return;
   }
   orc_level* C = &ctx->lev[l + 1];
   int Gc = C->m * C->n;
-  orc_smooth(k->scheme, k->c, k->gam, k->theta, p->newton, k->omega, p->nu1, F->m, F->n, F->h, F->phi, F->mu, F->kappa,
-             F->S1, F->S2, F->S3, F->phik);
+  smooth_w(k->scheme, k->c, k->gam, k->theta, p->newton, k->omega, p->nu1, F->m, F->n, F->h, F->phi, F->mu, F->kappa,
+           F->S1, F->S2, F->S3, F->phik, F->W);
   level_residual(k, F);
   orc_restrict(C->m, C->n, F->phi, C->phi);
   orc_restrict(C->m, C->n, F->mu, C->mu);
@@ -529,8 +590,8 @@ static void vcycle(orc_ctx* ctx, const orc_consts* k, int l) {
   memcpy(C->b2, C->mu, sizeof(double) * Gc);
   memcpy(C->b3, C->kappa, sizeof(double) * Gc);
   /* S_c = N_c(R u) + R r */
-  orc_apply_N(k->scheme, k->c, k->gam, k->theta, C->m, C->n, C->h, C->phi, C->mu, C->kappa, C->phik, C->S1,
-              C->S2, C->S3);
+  apply_N_w(k->scheme, k->c, k->gam, k->theta, C->m, C->n, C->h, C->phi, C->mu, C->kappa, C->phik, C->W, C->S1,
+            C->S2, C->S3);
   orc_restrict(C->m, C->n, F->r1, C->r1);
   orc_restrict(C->m, C->n, F->r2, C->r2);
   orc_restrict(C->m, C->n, F->r3, C->r3);
@@ -549,8 +610,8 @@ static void vcycle(orc_ctx* ctx, const orc_consts* k, int l) {
   orc_prolong_add(C->m, C->n, C->b1, F->phi);
   orc_prolong_add(C->m, C->n, C->b2, F->mu);
   orc_prolong_add(C->m, C->n, C->b3, F->kappa);
-  orc_smooth(k->scheme, k->c, k->gam, k->theta, p->newton, k->omega, p->nu2, F->m, F->n, F->h, F->phi, F->mu, F->kappa,
-             F->S1, F->S2, F->S3, F->phik);
+  smooth_w(k->scheme, k->c, k->gam, k->theta, p->newton, k->omega, p->nu2, F->m, F->n, F->h, F->phi, F->mu, F->kappa,
+           F->S1, F->S2, F->S3, F->phik, F->W);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -609,6 +670,7 @@ static void initial_guess(orc_ctx* ctx, const orc_consts* k, int guess, const do
   for (int i = 0; i < G; ++i) {
     double pk = (k->scheme == 2) ? L->phik[i] : 0.0;
     L->mu[i] = L->S2[i] + g_of(k->scheme, L->phi[i], pk) + k->gam * L->phi[i] + lap[i];
+    if (L->W) L->mu[i] += L->W[i] * L->phi[i];
   }
   free(lap);
 }
@@ -627,7 +689,8 @@ int orc_step(orc_ctx* ctx, int scheme, int guess, const double* phi0_in, double 
   orc_level* L0 = &ctx->lev[0];
   int G = p->m * p->n;
   if ((scheme != 1 && scheme != 2) || guess < 0 || guess > 2 || (guess == 2 && !phi0_in)) return -1;
-  orc_source(scheme, p, ctx->phik, ctx->phikm1, ctx->psik, L0->S1, L0->S2, L0->S3);
+  if (L0->W && scheme != 2) return -1;   /* pinning is defined for the second-order scheme (Sec. 4.6) */
+  source_w(scheme, p, ctx->phik, ctx->phikm1, ctx->psik, L0->W, ctx->phihat, L0->S1, L0->S2, L0->S3);
   memcpy(L0->phik, ctx->phik, sizeof(double) * G);
   for (int l = 1; l < ctx->nlev; ++l)
     orc_restrict(ctx->lev[l].m, ctx->lev[l].n, ctx->lev[l - 1].phik, ctx->lev[l].phik);
@@ -715,4 +778,30 @@ int orc_solve(orc_ctx* ctx, int scheme, double* phi, double* mu, double* kappa, 
   memcpy(kappa, L0->kappa, sizeof(double) * G);
   if (res_out) *res_out = res;
   return cycles;
+}
+
+/* Level operators with a pinning weight W on the grid (Sec. 4.6), for the kernel
+ * parity tests. */
+void orc_apply_N_pinned(int scheme, double c, double gam, double theta, int m, int n, double h,
+                        const double* phi, const double* mu, const double* kappa, const double* phik,
+                        const double* W, double* N1, double* N2, double* N3) {
+  apply_N_w(scheme, c, gam, theta, m, n, h, phi, mu, kappa, phik, W, N1, N2, N3);
+}
+
+void orc_smooth_pinned(int scheme, double c, double gam, double theta, int newton, double omega, int sweeps, int m,
+                       int n, double h, double* phi, double* mu, double* kappa, const double* S1, const double* S2,
+                       const double* S3, const double* phik, const double* W) {
+  smooth_w(scheme, c, gam, theta, newton, omega, sweeps, m, n, h, phi, mu, kappa, S1, S2, S3, phik, W);
+}
+
+int orc_coarse_newton_pinned(int scheme, double c, double gam, double theta, int m, int n, double h,
+                             double* phi, double* mu, double* kappa, const double* S1, const double* S2,
+                             const double* S3, const double* phik, const double* W) {
+  return coarse_newton_w(scheme, c, gam, theta, m, n, h, phi, mu, kappa, S1, S2, S3, phik, W);
+}
+
+void orc_source_pinned(int scheme, const orc_params* p, const double* phik, const double* phikm1,
+                       const double* psik, const double* W, const double* phihat, double* S1, double* S2,
+                       double* S3) {
+  source_w(scheme, p, phik, phikm1, psik, W, phihat, S1, S2, S3);
 }

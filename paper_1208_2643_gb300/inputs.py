@@ -109,3 +109,13 @@ def polycrystal_seeds(m: int, n: int, mean: float, count: int, size_cells: int, 
         x0 = int((xs[k] + 1.0) * 0.5 * (m - size_cells))
         phi[0:size_cells, x0:x0 + size_cells] += amp * noise[k]
     return phi
+
+
+def one_mode_crystal(m: int, n: int, h: float, phi_s: float, eps: float, shift: float = 0.0) -> np.ndarray:
+    """The one-mode hexagonal density of Sec. 4.6, (4.4)-(4.5), at cell centres, with its
+    x origin moved by `shift` (the shear of the pinned configuration)."""
+    X, Y = cell_centres(m, n, h)
+    A = single_mode_amplitude(phi_s, eps)
+    q = math.sqrt(3.0) / 2.0
+    return phi_s + A * (np.cos(q * (X - shift)) * np.cos(q * Y / math.sqrt(3.0))
+                        - 0.5 * np.cos(2.0 * q * Y / math.sqrt(3.0)))
