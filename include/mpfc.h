@@ -71,6 +71,8 @@ typedef struct {
   int guess;         /* MPFC_GUESS_*                                                      */
   int inner_cycles;  /* MPFC_FP32_INNER: FP32 V-cycles per FP64 outer iteration (0 = 2)   */
   int bc;            /* MPFC_BC_PERIODIC (default) or MPFC_BC_NEUMANN_Y                   */
+  int pinning;       /* 1: reserve the pinning weight and target of Sec. 4.6 in the
+                        workspace (mpfc_set_pinning); MPFC_FP64 with PREV/EXTRAP guess only */
 } mpfc_params;
 
 typedef struct {
@@ -84,6 +86,8 @@ typedef struct {
   double F;          /* F(phi^k), Sec. 3 (3.1)                                            */
   double pseudoF;    /* F + ||psi^k||_{-1}^2 / (2M), Sec. 3 (3.2)                         */
   double tildeF;     /* pseudoF + ||grad_h(phi^k - phi^{k-1})||^2 / 2, Sec. 3.4 (3.26)     */
+  double pinning;    /* h^2 sum W (phi^k - phihat)^2, the pinning energy of Sec. 4.6 (0 if
+                        pinning is off); not included in F, pseudoF, tildeF              */
 } mpfc_energy_t;
 
 typedef struct mpfc_s mpfc_t;
@@ -159,9 +163,19 @@ int mpfc_set_guess_model(mpfc_t* h, const float* params, size_t count);
 int mpfc_mass(mpfc_t* h, double* out);
 
 /* Discrete energies of Sec. 3 at the current state.  The -1 norm of App. A,
- * (A.16)-(A.18), comes from a periodic Poisson multigrid solve to 1e-13 relative
- * residual.  Synchronises. */
+ * (A.16)-(A.18), comes from a Poisson multigrid solve (under the handle's boundary
+ * rule) to 1e-13 relative residual.  Synchronises. */
 int mpfc_energy(mpfc_t* h, mpfc_energy_t* out);
+
+/* Pinning of Sec. 4.6: the second-order scheme then solves with the pinned potential
+ * mu~ = mu + 2 (phi^{k+1/2} - phihat) W, i.e. row 2 of N gains -W phi (a pointwise
+ * linear term of the cell system) and S2 gains W (phi^k - 2 phihat); coarse levels
+ * use the 2x2 averages of W.  weight (W >= 0) and target (phihat): m*n doubles, host
+ * or device, copied.  weight NULL switches pinning off.  The handle must have been
+ * created with pinning = 1 (else MPFC_ERR_INVALID).  While pinning is on, steps of
+ * scheme 1 return MPFC_ERR_INVALID.  The step's mu is the pinned potential mu~.
+ * Synchronises. */
+int mpfc_set_pinning(mpfc_t* h, const double* weight, const double* target);
 
 /* Mass h^2 sum phi of a caller's device array, without any device allocation and
  * without a handle.  The paper has no counterpart: this is for callers that cannot

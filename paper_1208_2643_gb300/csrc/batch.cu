@@ -511,7 +511,8 @@ size_t carve_batch(mpfc_batch_s* B, int count, const mpfc_params* each, char* ba
       Lev v;
       v.m = m;
       v.n = n;
-      v.nyn = 0;   // batches are periodic
+      v.nyn = 0;   // batches are periodic and unpinned
+      v.W = nullptr;
       v.h = h;
       v.phi = c.take<double>(G);
       v.mu = c.take<double>(G);
@@ -664,7 +665,7 @@ extern "C" size_t mpfc_batch_workspace_bytes(int count, const mpfc_params* each)
   for (int i = 0; i < count; ++i) {
     if (mpfc_workspace_bytes(&each[i]) == 0) return 0;
     if (!same_solver_settings(each[i], each[0]) || each[i].precision != MPFC_FP64 ||
-        each[i].guess == MPFC_GUESS_LEARNED || each[i].bc != MPFC_BC_PERIODIC)
+        each[i].guess == MPFC_GUESS_LEARNED || each[i].bc != MPFC_BC_PERIODIC || each[i].pinning)
       return 0;
   }
   return carve_batch(nullptr, count, each, nullptr);
@@ -716,6 +717,8 @@ extern "C" int mpfc_batch_create(int count, const mpfc_params* each, void* d_wor
         A.psik = B->state[3 * i + 2];
         A.psi_coef = (s == 0) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
         A.half_alpha = 0.5 * (1.0 - p.epsilon);
+        A.W = nullptr;
+        A.phihat = nullptr;
         A.guess = (p.guess == MPFC_GUESS_PREV) ? 0 : 1;
       }
       inv_s[i] = 1.0 / p.dt;

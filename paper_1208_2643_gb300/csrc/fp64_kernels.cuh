@@ -20,6 +20,8 @@ struct SourceArgs {
   const double* phik;
   const double* phikm1;
   const double* psik;
+  const double* W;       // pinning weight (scheme 2), nullptr: none
+  const double* phihat;  // pinning target
   double psi_coef;   // 1/(beta+1/s) (scheme 1) or 2/(beta+2/s) (scheme 2)
   double half_alpha; // alpha/2 (scheme 2)
   int guess;         // 0 prev, 1 extrapolated, 2 given in L.phi already
@@ -48,7 +50,8 @@ __device__ __forceinline__ void source_cell(const Lev& L, const SourceArgs& A, i
     double ts = 0.5 * (3.0 * pk[s] - pm[s]), tn = 0.5 * (3.0 * pk[nn] - pm[nn]);
     double lap_t = ((tw + te) + (ts + tn) - 4.0 * t0) * ih2;
     L.S1[c] = p0 + A.psi_coef * A.psik[c];
-    L.S2[c] = A.half_alpha * p0 + 2.0 * lap_t;
+    // pinning (Sec. 4.6): 2 W (phi^{k+1/2} - phihat) minus its part W phi in N gives W (phi^k - 2 phihat)
+    L.S2[c] = A.half_alpha * p0 + 2.0 * lap_t + (A.W ? A.W[c] * (p0 - 2.0 * A.phihat[c]) : 0.0);
     L.S3[c] = 0.5 * lap_k;
   }
   if (A.guess == 0) L.phi[c] = p0;
@@ -90,7 +93,8 @@ __device__ __forceinline__ void guess_mu_cell(const Lev& L, const Coef& k, int i
   double sum = (f[(size_t)j * m + im] + f[(size_t)j * m + ip]) + (f[(size_t)jm * m + i] + f[(size_t)jp * m + i]);
   double p = L.phi[c];
   double pk = (SCH == 2) ? L.pk[c] : 0.0;
-  L.mu[c] = L.S2[c] + g_of<SCH>(p, pk) + k.gam * p + k.ih2 * (sum - 4.0 * f[c]);
+  double gam = (SCH == 2 && L.W) ? k.gam + L.W[c] : k.gam;   // pinning weight joins gam (Sec. 4.6)
+  L.mu[c] = L.S2[c] + g_of<SCH>(p, pk) + gam * p + k.ih2 * (sum - 4.0 * f[c]);
 }
 
 template <int SCH>
@@ -147,6 +151,7 @@ __device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const 
     double pk = __ldg(L.pk + c);
     double q = dg_of<2>(p, pk);
     R2 = fma(k.ih2, ska, __ldg(L.S2 + c) + (g_of<2>(p, pk) - q * p));
+    if (L.W) q += __ldg(L.W + c);   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
     det = fma(k.a, q, k.D0);
     Qq = k.Q0 + q;
   }
@@ -200,7 +205,8 @@ __device__ __forceinline__ void resid_at(const Lev& L, const Coef& k, int i, int
   // r1 = S1 - phi + c Delta_h mu
   r1 = fma(k.cmu, fma(-4.0, u, smu), __ldg(L.S1 + c) - p);
   // r2 = S2 - mu + g(phi) + gam phi + Delta_h kappa
-  r2 = fma(k.ih2, fma(-4.0, v, ska), fma(k.gam, p, __ldg(L.S2 + c) - u) + g_of<SCH>(p, pk));
+  double gam = (SCH == 2 && L.W) ? k.gam + __ldg(L.W + c) : k.gam;
+  r2 = fma(k.ih2, fma(-4.0, v, ska), fma(gam, p, __ldg(L.S2 + c) - u) + g_of<SCH>(p, pk));
   // r3 = S3 - kappa + theta Delta_h phi
   r3 = fma(k.th2, fma(-4.0, p, sph), __ldg(L.S3 + c) - v);
 }
@@ -280,7 +286,8 @@ __device__ __forceinline__ void tau_cell(const Lev& C, const Coef& k, int i, int
   double sph = (phi[w] + phi[e]) + (phi[s] + phi[nn]);
   double pk = (SCH == 2) ? C.pk[c] : 0.0;
   double N1 = fma(-k.cmu, fma(-4.0, u, smu), p);
-  double N2 = fma(-k.ih2, fma(-4.0, v, ska), fma(-k.gam, p, u) - g_of<SCH>(p, pk));
+  double gam = (SCH == 2 && C.W) ? k.gam + C.W[c] : k.gam;
+  double N2 = fma(-k.ih2, fma(-4.0, v, ska), fma(-gam, p, u) - g_of<SCH>(p, pk));
   double N3 = fma(-k.th2, fma(-4.0, p, sph), v);
   C.S1[c] += N1;
   C.S2[c] += N2;
@@ -415,7 +422,8 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
     for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t, nyn) - 4.0 * ph[t]);
     __syncwarp();
     for (int t = lane; t < G; t += 32)
-      muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t, nyn) - 4.0 * kap[t]);
+      muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + (k.gam + (C.W ? C.W[t] : 0.0)) * ph[t] +
+               k.ih2 * (nbsum_s(kap, m, n, t, nyn) - 4.0 * kap[t]);
     __syncwarp();
     for (int t = lane; t < G; t += 32)
       Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t, nyn) - 4.0 * muv[t]));
@@ -426,7 +434,7 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
       int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
                 (ci == ri && cj == ywrap(rj - 1, n, nyn)) + (ci == ri && cj == ywrap(rj + 1, n, nyn));
       float Lrc = ih2f * ((float)cnt - (r == col ? 4.f : 0.f));
-      Jm[r * W + col] = K3f[idx] - cf * Lrc * (gamf + (float)dg_of<SCH>(ph[col], pk[col]));
+      Jm[r * W + col] = K3f[idx] - cf * Lrc * (gamf + (float)((C.W ? C.W[col] : 0.0) + dg_of<SCH>(ph[col], pk[col])));
     }
     __syncwarp();
     for (int col = 0; col < G; ++col) {
@@ -482,7 +490,8 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
   for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t, C.nyn) - 4.0 * ph[t]);
   __syncwarp();
   for (int t = lane; t < G; t += 32) {
-    muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + k.gam * ph[t] + k.ih2 * (nbsum_s(kap, m, n, t, C.nyn) - 4.0 * kap[t]);
+    muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + (k.gam + (C.W ? C.W[t] : 0.0)) * ph[t] +
+             k.ih2 * (nbsum_s(kap, m, n, t, C.nyn) - 4.0 * kap[t]);
     C.phi[t] = ph[t];
     C.ka[t] = kap[t];
     C.mu[t] = muv[t];
@@ -652,14 +661,15 @@ static __global__ void k_sum1(const double* __restrict__ f, int G, Ctl* ctl, dou
 }
 
 // sums: 0 phi^4, 1 phi^2, 2 |grad phi|^2 (edge differences), 3 (Delta_h phi)^2 h^4,
-// 4 psi * xi, 5 |grad (phi - phi_prev)|^2
+// 4 psi * xi, 5 |grad (phi - phi_prev)|^2, 6 W (phi - phihat)^2 (pinning, W nullable)
 // With the Neumann rule the north edge of the top row has zero difference (ghost =
 // boundary row) and the bottom row's south edge is never counted, as App. A's
 // Neumann grid has only the n - 1 interior north-south edges.
 static __global__ void k_energy_sums(const double* __restrict__ phi, const double* __restrict__ phip,
                               const double* __restrict__ psi, const double* __restrict__ xi, int m, int n, int nyn,
-                              Ctl* ctl, double* partials) {
-  double v[6] = {0, 0, 0, 0, 0, 0};
+                              const double* __restrict__ W, const double* __restrict__ phat, Ctl* ctl,
+                              double* partials) {
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
   int G = m * n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
     int i = t % m, j = t / m;
@@ -677,9 +687,13 @@ static __global__ void k_energy_sums(const double* __restrict__ phi, const doubl
     double d0 = p - phip[t];
     double ddx = (pe - phip[j * m + ip]) - d0, ddy = (pn - phip[jp * m + i]) - d0;
     v[5] += ddx * ddx + ddy * ddy;
+    if (W) {
+      double dp = p - phat[t];
+      v[6] += W[t] * dp * dp;
+    }
   }
-  if (grid_sum<6>(v, partials, &ctl->counter))
-    for (int s = 0; s < 6; ++s) ctl->sums[s] = v[s];
+  if (grid_sum<7>(v, partials, &ctl->counter))
+    for (int s = 0; s < 7; ++s) ctl->sums[s] = v[s];
 }
 
 // x = f - mean: the right-hand side of the mean-zero Poisson problem

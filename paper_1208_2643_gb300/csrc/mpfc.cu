@@ -80,6 +80,8 @@ static bool params_valid(const mpfc_params* p) {
   if (p->guess < MPFC_GUESS_PREV || p->guess > MPFC_GUESS_LEARNED) return false;
   if (p->inner_cycles < 0 || p->inner_cycles > 64) return false;
   if (p->bc != MPFC_BC_PERIODIC && p->bc != MPFC_BC_NEUMANN_Y) return false;
+  if (p->pinning != 0 && p->pinning != 1) return false;
+  if (p->pinning && (p->precision != MPFC_FP64 || p->guess == MPFC_GUESS_LEARNED)) return false;
   // the mixed conditions are built for the FP64 path with the analytic guesses
   if (p->bc == MPFC_BC_NEUMANN_Y && (p->precision != MPFC_FP64 || p->guess == MPFC_GUESS_LEARNED)) return false;
   int L = mpfc_num_levels(p->m, p->n, p->coarsest);
@@ -150,13 +152,14 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
   int m = p->m, n = p->n;
   double h = p->h;
   Lev lev[kMaxLevels];
-  double *px[kMaxLevels], *pf[kMaxLevels];
+  double *px[kMaxLevels], *pf[kMaxLevels], *pw[kMaxLevels];
   for (int l = 0; l < L; ++l) {
     size_t G = (size_t)m * n;
     Lev& v = lev[l];
     v.m = m;
     v.n = n;
     v.nyn = p->bc == MPFC_BC_NEUMANN_Y;
+    v.W = nullptr;
     v.h = h;
     v.phi = c.take<double>(G);
     v.mu = c.take<double>(G);
@@ -175,10 +178,12 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
     }
     px[l] = c.take<double>(G);
     pf[l] = c.take<double>(G);
+    pw[l] = p->pinning ? c.take<double>(G) : nullptr;
     m /= 2;
     n /= 2;
     h *= 2.0;
   }
+  double* pinhat = p->pinning ? c.take<double>(G0) : nullptr;
   int Gc = lev[L - 1].m * lev[L - 1].n;
   float* K3a = c.take<float>((size_t)Gc * Gc);
   float* K3b = c.take<float>((size_t)Gc * Gc);
@@ -196,7 +201,10 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
       H->lev[l] = lev[l];
       H->px[l] = px[l];
       H->pf[l] = pf[l];
+      H->pinW[l] = pw[l];
     }
+    H->pinhat = pinhat;
+    H->pin_active = 0;
     H->K3[0] = K3a;
     H->K3[1] = K3b;
   }
@@ -393,6 +401,8 @@ static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
   A.psik = H->psik;
   A.psi_coef = (SCH == 1) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
   A.half_alpha = 0.5 * (1.0 - p.epsilon);
+  A.W = H->pin_active ? H->pinW[0] : nullptr;
+  A.phihat = H->pinhat;
   A.guess = (p.guess == MPFC_GUESS_PREV) ? 0 : 1;   // the learned guess corrects the extrapolation
   dim3 g0 = grid_for(L0.m, L0.n, kBlk2d);
   k_source_guess<SCH><<<g0, kBlk2d, 0, s>>>(L0, A);
@@ -592,6 +602,7 @@ extern "C" int mpfc_get_state(mpfc_t* H, double* phi, double* phi_prev, double* 
 
 static int run_steps(mpfc_s* H, int scheme, int nsteps, int fixed_cycles, mpfc_step_info* per_step) {
   if (!H || (scheme != 1 && scheme != 2) || nsteps < 0) return MPFC_ERR_INVALID;
+  if (H->pin_active && scheme != 2) return MPFC_ERR_INVALID;   // pinning is a second-order-scheme term
   if (H->p.guess == MPFC_GUESS_LEARNED && !mpfc_has_guess_model(H)) return MPFC_ERR_INVALID;
   int rc = ensure_graph(H, scheme);
   if (rc != MPFC_OK) return rc;
@@ -642,6 +653,7 @@ extern "C" int mpfc_step(mpfc_t* H, int scheme, int nsteps, mpfc_step_info* per_
 
 extern "C" int mpfc_step_async(mpfc_t* H, int scheme, int nsteps) {
   if (!H || (scheme != 1 && scheme != 2) || nsteps < 0) return MPFC_ERR_INVALID;
+  if (H->pin_active && scheme != 2) return MPFC_ERR_INVALID;
   if (H->p.guess == MPFC_GUESS_LEARNED && !mpfc_has_guess_model(H)) return MPFC_ERR_INVALID;
   int rc = ensure_graph(H, scheme);
   if (rc != MPFC_OK) return rc;
@@ -750,11 +762,12 @@ extern "C" int mpfc_energy(mpfc_t* H, mpfc_energy_t* out) {
   int rc = poisson_solve(H, H->psik);
   if (rc) return rc;
   size_t G = (size_t)H->p.m * H->p.n;
-  k_energy_sums<<<mpfc_reduce_blocks(G), 256, 0, H->stream>>>(H->phik, H->phikm1, H->psik, H->px[0], H->p.m, H->p.n,
-                                                              H->lev[0].nyn, H->ctl, H->partials);
+  k_energy_sums<<<mpfc_reduce_blocks(G), 256, 0, H->stream>>>(
+      H->phik, H->phikm1, H->psik, H->px[0], H->p.m, H->p.n, H->lev[0].nyn, H->pin_active ? H->pinW[0] : nullptr,
+      H->pinhat, H->ctl, H->partials);
   CK(cudaGetLastError());
-  double v[6];
-  rc = read_sums(H, v, 6);
+  double v[7];
+  rc = read_sums(H, v, 7);
   if (rc) return rc;
   double h = H->p.h, h2 = h * h, alpha = 1.0 - H->p.epsilon;
   double F = 0.25 * h2 * v[0] + 0.5 * alpha * h2 * v[1] - v[2] + 0.5 * h2 * v[3] / (h2 * h2);
@@ -762,6 +775,29 @@ extern "C" int mpfc_energy(mpfc_t* H, mpfc_energy_t* out) {
   out->F = F;
   out->pseudoF = F + m1 / (2.0 * H->p.M);
   out->tildeF = out->pseudoF + 0.5 * v[5];
+  out->pinning = h2 * v[6];
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_set_pinning(mpfc_t* H, const double* weight, const double* target) {
+  if (!H || !H->p.pinning || (weight && !target)) return MPFC_ERR_INVALID;
+  mpfc_drop_graphs(H);   // the levels' weight pointers are part of the captured kernels
+  if (!weight) {
+    H->pin_active = 0;
+    for (int l = 0; l < H->nlev; ++l) H->lev[l].W = nullptr;
+    return MPFC_OK;
+  }
+  size_t G = (size_t)H->p.m * H->p.n;
+  CK(cudaMemcpyAsync(H->pinW[0], weight, G * sizeof(double), cudaMemcpyDefault, H->stream));
+  CK(cudaMemcpyAsync(H->pinhat, target, G * sizeof(double), cudaMemcpyDefault, H->stream));
+  for (int l = 1; l < H->nlev; ++l) {
+    const Lev& C = H->lev[l];
+    k_restrict_plane<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, H->stream>>>(H->pinW[l - 1], H->pinW[l], C.m, C.n);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(H->stream));
+  H->pin_active = 1;
+  for (int l = 0; l < H->nlev; ++l) H->lev[l].W = H->pinW[l];
   return MPFC_OK;
 }
 
@@ -792,8 +828,8 @@ extern "C" int mpfc_op_source(mpfc_t* H, int scheme, const double* phik, const d
   L.S2 = S2;
   L.S3 = S3;
   L.phi = nullptr;
-  SourceArgs A{phik, phikm1, psik, scheme == 1 ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt),
-               0.5 * (1.0 - p.epsilon), 2};
+  SourceArgs A{phik, phikm1, psik, H->pin_active ? H->pinW[0] : nullptr, H->pinhat,
+               scheme == 1 ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt), 0.5 * (1.0 - p.epsilon), 2};
   dim3 g = grid_for(L.m, L.n, kBlk2d);
   if (scheme == 1) k_source_guess<1><<<g, kBlk2d, 0, H->stream>>>(L, A);
   else k_source_guess<2><<<g, kBlk2d, 0, H->stream>>>(L, A);

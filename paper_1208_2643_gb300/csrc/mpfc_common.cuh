@@ -21,6 +21,7 @@ struct Lev {
   double *S1, *S2, *S3;     // FAS source (tau-corrected below the finest level)
   double *b1, *b2, *b3;     // R u_f kept for the correction u_c_new - R u_f (levels >= 1)
   double* pk;               // phi^k on this level (scheme 2)
+  const double* W;          // pinning weight on this level (Sec. 4.6, scheme 2), nullptr: none
 };
 
 // Coefficients of the cell system of App. B on one level, for one scheme.

@@ -59,6 +59,11 @@ struct mpfc_s {
   int outer_max = 0;
   // learned initial guess
   MpfcGuess guess;
+  // pinning (Sec. 4.6): weight per level and the finest-level target, carved when
+  // p.pinning; active once mpfc_set_pinning gave a weight
+  double* pinW[mpfc::kMaxLevels] = {};
+  double* pinhat = nullptr;
+  int pin_active = 0;
 };
 
 void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);

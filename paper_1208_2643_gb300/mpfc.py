@@ -41,7 +41,7 @@ class mpfc_params(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("guess", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("bc", ctypes.c_int)]
+                ("bc", ctypes.c_int), ("pinning", ctypes.c_int)]
 
 
 class mpfc_step_info(ctypes.Structure):
@@ -50,7 +50,8 @@ class mpfc_step_info(ctypes.Structure):
 
 
 class mpfc_energy_t(ctypes.Structure):
-    _fields_ = [("F", ctypes.c_double), ("pseudoF", ctypes.c_double), ("tildeF", ctypes.c_double)]
+    _fields_ = [("F", ctypes.c_double), ("pseudoF", ctypes.c_double), ("tildeF", ctypes.c_double),
+                ("pinning", ctypes.c_double)]
 
 
 _lib = None
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_batch_time_smooth.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_float)]
     lib.mpfc_mass.argtypes = [_VP, P(ctypes.c_double)]
     lib.mpfc_energy.argtypes = [_VP, P(mpfc_energy_t)]
+    lib.mpfc_set_pinning.argtypes = [_VP, _VP, _VP]
     lib.mpfc_strerror.argtypes = [ctypes.c_int]
     lib.mpfc_strerror.restype = ctypes.c_char_p
     lib.mpfc_levels.argtypes = [_VP]
@@ -274,10 +276,28 @@ class Solver:
         _check(self.lib.mpfc_mass(self.h, ctypes.byref(v)), "mpfc_mass")
         return v.value
 
+    def set_pinning(self, weight=None, target=None):
+        """Pinning of Sec. 4.6 (scheme 2): weight W >= 0 and target phihat, (n, m) numpy
+        arrays or device tensors; weight None switches it off."""
+        if weight is None:
+            _check(self.lib.mpfc_set_pinning(self.h, None, None), "mpfc_set_pinning")
+            return
+        import numpy as np
+        keep = []
+        ptrs = []
+        for a in (weight, target):
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                keep.append(a)
+                ptrs.append(a.ctypes.data)
+            else:
+                ptrs.append(_ptr(a))
+        _check(self.lib.mpfc_set_pinning(self.h, ptrs[0], ptrs[1]), "mpfc_set_pinning")
+
     def energy(self):
         e = mpfc_energy_t()
         _check(self.lib.mpfc_energy(self.h, ctypes.byref(e)), "mpfc_energy")
-        return dict(F=e.F, pseudoF=e.pseudoF, tildeF=e.tildeF)
+        return dict(F=e.F, pseudoF=e.pseudoF, tildeF=e.tildeF, pinning=e.pinning)
 
     # component entry points (device tensors in and out)
     def op_source(self, scheme, phik, phikm1, psik):
