@@ -111,12 +111,11 @@ __global__ void k_guess_mu(Lev L, Coef k) {
 // `color` (0 = red, (i+j) even).  Cells of one colour only read the other colour,
 // so a half sweep is exactly parallel.
 // ---------------------------------------------------------------------------
-// Next to a Neumann boundary (L.nyn, rows 0 and n-1) the ghost neighbour is the cell's
-// own unknown (App. A, (A.7)): it leaves the neighbour sums and the cell system uses
-// the coefficients of three neighbours, kb.  Rows are warp-uniform, so the branch
-// does not diverge, and periodic levels never take it.
-template <int SCH>
-__device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const Coef& kb, int i, int j) {
+// EDGE: a row next to a Neumann boundary, where the ghost neighbour is the cell's own
+// unknown (App. A, (A.7)): it leaves the neighbour sums and k holds the coefficients
+// of three neighbours.
+template <int SCH, bool EDGE>
+__device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, int i, int j) {
   int m = L.m;
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
@@ -129,13 +128,11 @@ __device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const 
   double ska = (__ldg(ka + w) + __ldg(ka + e)) + (__ldg(ka + s) + __ldg(ka + nn));
   double sph = (__ldg(phi + w) + __ldg(phi + e)) + (__ldg(phi + s) + __ldg(phi + nn));
   double p = phi[c];
-  const bool edge = L.nyn && (j == 0 || j == L.n - 1);
-  if (edge) {   // the ghost was read as the cell's current value: take it out again
+  if (EDGE) {   // the ghost was read as the cell's current value: take it out again
     smu -= mu[c];
     ska -= ka[c];
     sph -= p;
   }
-  const Coef& k = edge ? kb : k0;
   double R1 = fma(k.cmu, smu, __ldg(L.S1 + c));
   double R3 = fma(k.th2, sph, __ldg(L.S3 + c));
   // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
@@ -174,6 +171,14 @@ __device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const 
     mu[c] = nmu * rdet;
     ka[c] = fma(-k.b3, phin, R3);
   }
+}
+
+// Rows are warp-uniform, so the branch does not diverge; periodic levels never take
+// it.  Two bodies, each reading its coefficient set at fixed parameter offsets.
+template <int SCH>
+__device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const Coef& kb, int i, int j) {
+  if (L.nyn && (j == 0 || j == L.n - 1)) smooth_cell_body<SCH, true>(L, kb, i, j);
+  else smooth_cell_body<SCH, false>(L, k0, i, j);
 }
 
 template <int SCH>
