@@ -46,7 +46,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("h", ctypes.c_double), ("M", ctypes.c_double),
                 ("eps", ctypes.c_double), ("beta", ctypes.c_double), ("s", ctypes.c_double),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("newton", ctypes.c_int),
-                ("coarse_cells", ctypes.c_int), ("omega", ctypes.c_double)]
+                ("coarse_cells", ctypes.c_int), ("omega", ctypes.c_double), ("model", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -149,10 +149,11 @@ class Params:
     coarse_cells: int = 4
     omega: float = 0.8
     ny_neumann: int = 0   # 1: homogeneous Neumann in y (Sec. 4.5); applied by Solver around each call
+    model: int = 0        # 0: MPFC (2); 1: PFC (1), d_t phi = M Delta mu
 
     def c_struct(self) -> _Params:
         return _Params(self.m, self.n, self.h, self.M, self.eps, self.beta, self.s, self.nu1, self.nu2,
-                       self.newton, self.coarse_cells, self.omega)
+                       self.newton, self.coarse_cells, self.omega, self.model)
 
 
 def scheme_consts(p: Params, scheme: int):

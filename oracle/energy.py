@@ -139,3 +139,36 @@ def scheme1_identity_terms(phi_new, phi_k, psi_new, psi_k, h, eps, M, beta, s, n
     diss = (G4 + 0.5 * alpha * h2 * float(np.sum(d * d)) + 0.5 * h2 * float(np.sum(Ld * Ld)) + grad_sq(d, h, nn)
             + s * beta / M * norm_m1_sq(psi_new, h, nn) + norm_m1_sq(psi_new - psi_k, h, nn) / (2.0 * M))
     return pseudo_F(a, psi_new, h, eps, M, nn) + diss, pseudo_F(b, psi_k, h, eps, M, nn)
+
+
+def pfc_scheme1_identity_terms(phi_new, phi_k, h, eps, M, s, ny_neumann=False):
+    """Exact energy balance of the first-order convex-splitting scheme of the PFC
+    equation (1): with d = phi^{k+1} - phi^k = s M Delta_h mu,
+      F^{k+1} + G4 + alpha/2 ||d||^2 + 1/2 ||Delta_h d||^2 + ||grad_h d||^2
+        + ||d||_{-1}^2 / (s M) = F^k,
+    the MPFC balance of scheme 1 without the inertial terms (G4 as there).
+    Returns (lhs, rhs)."""
+    alpha = 1.0 - eps
+    h2 = h * h
+    a, b = phi_new, phi_k
+    d = a - b
+    G4 = h2 * float(np.sum(d * a**3 - 0.25 * (a**4 - b**4)))
+    Ld = lap(d, h, ny_neumann)
+    diss = (G4 + 0.5 * alpha * h2 * float(np.sum(d * d)) + 0.5 * h2 * float(np.sum(Ld * Ld))
+            + grad_sq(d, h, ny_neumann) + norm_m1_sq(d, h, ny_neumann) / (s * M))
+    return F(a, h, eps, ny_neumann) + diss, F(b, h, eps, ny_neumann)
+
+
+def pfc_scheme2_identity_terms(phi_new, phi_k, phi_km1, h, eps, M, s, ny_neumann=False):
+    """Exact energy balance of the second-order scheme for the PFC equation (1), the
+    analogue of (3.28) without the inertial terms: with
+    tildeF(phi, phi_prev) = F(phi) + 1/2 ||grad_h(phi - phi_prev)||^2 and
+    d = phi^{k+1} - phi^k = s M Delta_h mu^{k+1/2},
+      tildeF^{k+1} + ||d||_{-1}^2 / (s M) + 1/2 ||grad_h(phi^{k+1} - 2 phi^k + phi^{k-1})||^2 = tildeF^k.
+    Returns (lhs, rhs)."""
+    nn = ny_neumann
+    d = phi_new - phi_k
+    t_new = F(phi_new, h, eps, nn) + 0.5 * grad_sq(phi_new - phi_k, h, nn)
+    t_old = F(phi_k, h, eps, nn) + 0.5 * grad_sq(phi_k - phi_km1, h, nn)
+    diss = norm_m1_sq(d, h, nn) / (s * M) + 0.5 * grad_sq(phi_new - 2.0 * phi_k + phi_km1, h, nn)
+    return t_new + diss, t_old

@@ -67,6 +67,8 @@ typedef struct {
   int coarse_cells;  /* coarsen while the coarse grid keeps >= this many cells
                         per side and both sides stay even                        */
   double omega;      /* relaxation of the cell update; 1 = the paper's smoother */
+  int model;         /* 0: MPFC (2), the damped wave equation; 1: PFC (1), the
+                        parabolic special case d_t phi = M Delta mu (Sec. 1)      */
 } orc_params;
 
 /* Scheme constants of the FAS operator N (App. B.1 / B.2).
@@ -89,6 +91,9 @@ static orc_consts consts_of(const orc_params* p, int scheme) {
     k.gam = 0.5 * alpha;
     k.theta = 0.5;
   }
+  /* PFC, (phi^{k+1} - phi^k)/s = M Delta_h mu with the same mu as the MPFC schemes:
+   * row 1 of N reads phi - s M Delta_h mu */
+  if (p->model == 1) k.c = p->s * p->M;
   return k;
 }
 
@@ -188,6 +193,7 @@ void orc_apply_N(int scheme, double c, double gam, double theta, int m, int n, d
 
 /* Source S.
  * Scheme 1 (App. B.1): S1 = phik + psik/(beta+1/s), S2 = 2 Delta_h phik, S3 = 0.
+ * PFC (either scheme): S1 = phik (no velocity term).
  * Scheme 2 (App. B.2): S1 = phik + 2 psik/(beta+2/s),
  *   S2 = (alpha/2) phik + 2 Delta_h phitilde, phitilde = (3 phik - phikm1)/2,
  *   S3 = (1/2) Delta_h phik. */
@@ -211,7 +217,7 @@ static void source_w(int scheme, const orc_params* p, const double* phik, const 
   if (scheme == 1) {
     orc_laplacian(m, n, p->h, phik, lap);
     for (int k = 0; k < N; ++k) {
-      S1[k] = phik[k] + psik[k] / (p->beta + 1.0 / p->s);
+      S1[k] = phik[k] + (p->model == 1 ? 0.0 : psik[k] / (p->beta + 1.0 / p->s));
       S2[k] = 2.0 * lap[k];
       S3[k] = 0.0;
     }
@@ -222,7 +228,7 @@ static void source_w(int scheme, const orc_params* p, const double* phik, const 
     orc_laplacian(m, n, p->h, tl, lap_t);
     orc_laplacian(m, n, p->h, phik, lap);
     for (int k = 0; k < N; ++k) {
-      S1[k] = phik[k] + 2.0 * psik[k] / (p->beta + 2.0 / p->s);
+      S1[k] = phik[k] + (p->model == 1 ? 0.0 : 2.0 * psik[k] / (p->beta + 2.0 / p->s));
       S2[k] = 0.5 * alpha * phik[k] + 2.0 * lap_t[k];
       if (W) S2[k] += W[k] * (phik[k] - 2.0 * phihat[k]);
       S3[k] = 0.5 * lap[k];
@@ -712,8 +718,9 @@ int orc_step(orc_ctx* ctx, int scheme, int guess, const double* phi0_in, double 
   if (status != 0) return status;
   for (int i = 0; i < G; ++i) {
     double phinew = L0->phi[i];
-    double psinew = (scheme == 1) ? (phinew - ctx->phik[i]) / p->s
-                                   : 2.0 / p->s * (phinew - ctx->phik[i]) - ctx->psik[i];
+    /* MPFC: (3.9) / (3.15); PFC has no velocity unknown, psi keeps (phi^{k+1} - phi^k)/s */
+    double psinew = (scheme == 1 || p->model == 1) ? (phinew - ctx->phik[i]) / p->s
+                                                  : 2.0 / p->s * (phinew - ctx->phik[i]) - ctx->psik[i];
     ctx->psik[i] = psinew;
     ctx->phikm1[i] = ctx->phik[i];
     ctx->phik[i] = phinew;
