@@ -501,6 +501,18 @@ def run_ours(args):
                                          "trained on solver trajectories at 256^2"}
             sl.close()
 
+    # the PFC variant (Sec. 1, (1)) on the headline workload
+    pq = mpfc.default_params(m=size, n=size, h=w["h"], M=w["M"], epsilon=w["epsilon"], beta=w["beta"], dt=w["dt"],
+                             tol=w["tol"], omega=w["omega"], guess=mpfc.MPFC_GUESS_EXTRAP, model=mpfc.MPFC_MODEL_PFC)
+    sq = mpfc.Solver(pq, stream=stream)
+    sq.set_state(phi0)
+    msq, recq = timed_steps(sq, K, max(args.warmup, 0))
+    msq = replicas.job_time_ms(msq, device="cuda")
+    forms["pfc"] = {"workload": "the headline workload with the PFC model (d_t phi = M Delta mu, Sec. 1)",
+                    "steps_per_s": world * K / (msq * 1e-3),
+                    "vcycles_per_step": float(np.mean([r["cycles"] for r in recq]))}
+    sq.close()
+
     # mixed boundary conditions: the polycrystal run of Sec. 4.5 (periodic in x,
     # homogeneous Neumann in y), 2048^2, scheme 2, s = 1
     if not args.no_polycrystal:

@@ -54,6 +54,13 @@ extern "C" {
 #define MPFC_BC_PERIODIC 0
 #define MPFC_BC_NEUMANN_Y 1
 
+/* Model: the MPFC damped wave equation (Sec. 1, (2)), or its purely parabolic special
+ * case, the PFC equation d_t phi = M Delta mu (Sec. 1, (1)), solved by the same
+ * convex-splitting schemes: row 1 of N reads phi - s M Delta_h mu and S1 = phi^k (no
+ * velocity term); psi then holds the discrete velocity (phi^{k+1} - phi^k)/s. */
+#define MPFC_MODEL_MPFC 0
+#define MPFC_MODEL_PFC 1
+
 typedef struct {
   int m, n;          /* cells in x and y; the hierarchy halves both while they stay even
                         and at least `coarsest` cells per side remain                    */
@@ -73,6 +80,7 @@ typedef struct {
   int bc;            /* MPFC_BC_PERIODIC (default) or MPFC_BC_NEUMANN_Y                   */
   int pinning;       /* 1: reserve the pinning weight and target of Sec. 4.6 in the
                         workspace (mpfc_set_pinning); MPFC_FP64 with PREV/EXTRAP guess only */
+  int model;         /* MPFC_MODEL_MPFC (default) or MPFC_MODEL_PFC                        */
 } mpfc_params;
 
 typedef struct {
@@ -84,7 +92,7 @@ typedef struct {
 
 typedef struct {
   double F;          /* F(phi^k), Sec. 3 (3.1)                                            */
-  double pseudoF;    /* F + ||psi^k||_{-1}^2 / (2M), Sec. 3 (3.2)                         */
+  double pseudoF;    /* F + ||psi^k||_{-1}^2 / (2M), Sec. 3 (3.2); F for the PFC model     */
   double tildeF;     /* pseudoF + ||grad_h(phi^k - phi^{k-1})||^2 / 2, Sec. 3.4 (3.26)     */
   double pinning;    /* h^2 sum W (phi^k - phihat)^2, the pinning energy of Sec. 4.6 (0 if
                         pinning is off); not included in F, pseudoF, tildeF              */

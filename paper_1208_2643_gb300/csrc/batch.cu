@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) kb_resnorm(const BItem* __restrict__ item
 // keeps its state and is halted for the rest of the call.
 template <int SCH>
 __global__ void kb_commit(const BItem* __restrict__ items, int n, const Lev* __restrict__ levs,
-                          const double* __restrict__ inv_s, double* const* __restrict__ state, BCtl* ctl,
+                          const double* __restrict__ inv_s, int pfc, double* const* __restrict__ state, BCtl* ctl,
                           const BGlobal* glob) {
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     BItem w = items[it];
@@ -269,7 +269,7 @@ __global__ void kb_commit(const BItem* __restrict__ items, int n, const Lev* __r
       double* psik = state[3 * w.inst + 2];
       double pn = L.phi[t], p0 = phik[t];
       double is = inv_s[w.inst];
-      psik[t] = (SCH == 1) ? (pn - p0) * is : 2.0 * is * (pn - p0) - psik[t];
+      psik[t] = (SCH == 1 || pfc) ? (pn - p0) * is : 2.0 * is * (pn - p0) - psik[t];
       phikm1[t] = p0;
       phik[t] = pn;
     }
@@ -372,7 +372,7 @@ struct BCarver {
 
 bool same_solver_settings(const mpfc_params& a, const mpfc_params& b) {
   return a.nu1 == b.nu1 && a.nu2 == b.nu2 && a.coarsest == b.coarsest && a.omega == b.omega && a.tol == b.tol &&
-         a.max_cycles == b.max_cycles && a.precision == b.precision && a.guess == b.guess;
+         a.max_cycles == b.max_cycles && a.precision == b.precision && a.guess == b.guess && a.model == b.model;
 }
 
 // Work items of one iteration domain (dx x dy cells or half-cells) tiled tx x ty.
@@ -609,8 +609,8 @@ void enqueue_batch_prologue(mpfc_batch_s* B, cudaStream_t s) {
 template <int SCH>
 void enqueue_batch_commit(mpfc_batch_s* B, cudaStream_t s) {
   const BItem* fin = B->d_items + B->fin_off;
-  kb_commit<SCH><<<grid_for_items(B->fin_cnt), dim3(kPTX, kPTY), 0, s>>>(fin, B->fin_cnt, B->d_lev, B->d_inv_s,
-                                                                          B->d_state, B->d_ctl, B->d_glob);
+  kb_commit<SCH><<<grid_for_items(B->fin_cnt), dim3(kPTX, kPTY), 0, s>>>(
+      fin, B->fin_cnt, B->d_lev, B->d_inv_s, B->p0.model == MPFC_MODEL_PFC, B->d_state, B->d_ctl, B->d_glob);
   kb_step_end<<<(B->count + 127) / 128, 128, 0, s>>>(B->d_ctl, B->d_glob, B->count);
 }
 
@@ -715,7 +715,7 @@ extern "C" int mpfc_batch_create(int count, const mpfc_params* each, void* d_wor
         A.phik = B->state[3 * i];
         A.phikm1 = B->state[3 * i + 1];
         A.psik = B->state[3 * i + 2];
-        A.psi_coef = (s == 0) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
+        A.psi_coef = (p.model == MPFC_MODEL_PFC) ? 0.0 : (s == 0) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
         A.half_alpha = 0.5 * (1.0 - p.epsilon);
         A.W = nullptr;
         A.phihat = nullptr;

@@ -631,8 +631,10 @@ __device__ __forceinline__ int step_status(const Ctl* ctl) {
 // (scheme 2, (3.15)); then phi^{k-1} <- phi^k, phi^k <- phi.  Skipped for a
 // failed or skipped step, which also halts the remaining steps of the call.
 template <int SCH>
+// pfc: psi keeps the discrete velocity (phi^{k+1} - phi^k)/s (the PFC model has no
+// velocity unknown); otherwise (3.9) / (3.15).
 __global__ void k_commit(const double* __restrict__ phinew, double* phik, double* phikm1, double* psik,
-                         double* phikm2, int G, double inv_s, Ctl* ctl, StepRecord* info) {
+                         double* phikm2, int G, double inv_s, int pfc, Ctl* ctl, StepRecord* info) {
   int st = step_status(ctl);
   int skip = ctl->skip;
   if (blockIdx.x == 0 && threadIdx.x == 0 && !skip) {
@@ -648,7 +650,7 @@ __global__ void k_commit(const double* __restrict__ phinew, double* phik, double
   if (skip || st != 0) return;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
     double pn = phinew[t], p0 = phik[t];
-    double ps = (SCH == 1) ? (pn - p0) * inv_s : 2.0 * inv_s * (pn - p0) - psik[t];
+    double ps = (SCH == 1 || pfc) ? (pn - p0) * inv_s : 2.0 * inv_s * (pn - p0) - psik[t];
     psik[t] = ps;
     if (phikm2) phikm2[t] = phikm1[t];
     phikm1[t] = p0;

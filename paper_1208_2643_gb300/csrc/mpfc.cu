@@ -81,6 +81,7 @@ static bool params_valid(const mpfc_params* p) {
   if (p->inner_cycles < 0 || p->inner_cycles > 64) return false;
   if (p->bc != MPFC_BC_PERIODIC && p->bc != MPFC_BC_NEUMANN_Y) return false;
   if (p->pinning != 0 && p->pinning != 1) return false;
+  if (p->model != MPFC_MODEL_MPFC && p->model != MPFC_MODEL_PFC) return false;
   if (p->pinning && (p->precision != MPFC_FP64 || p->guess == MPFC_GUESS_LEARNED)) return false;
   // the mixed conditions are built for the FP64 path with the analytic guesses
   if (p->bc == MPFC_BC_NEUMANN_Y && (p->precision != MPFC_FP64 || p->guess == MPFC_GUESS_LEARNED)) return false;
@@ -105,6 +106,7 @@ Coef mpfc_coef(const mpfc_params* p, int scheme, double h, int nb) {
     k.gam = 0.5 * alpha;
     k.theta = 0.5;
   }
+  if (p->model == MPFC_MODEL_PFC) k.c = p->dt * p->M;   // (phi - phi^k)/s = M Delta_h mu
   k.omega = p->omega;
   double h2 = h * h;
   k.cmu = k.c / h2;
@@ -399,7 +401,7 @@ static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
   A.phik = H->phik;
   A.phikm1 = H->phikm1;
   A.psik = H->psik;
-  A.psi_coef = (SCH == 1) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
+  A.psi_coef = (p.model == MPFC_MODEL_PFC) ? 0.0 : (SCH == 1) ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt);
   A.half_alpha = 0.5 * (1.0 - p.epsilon);
   A.W = H->pin_active ? H->pinW[0] : nullptr;
   A.phihat = H->pinhat;
@@ -422,7 +424,7 @@ static void enqueue_commit(mpfc_s* H, cudaStream_t s) {
   int blocks = (int)((G + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_commit<SCH><<<blocks, 256, 0, s>>>(H->lev[0].phi, H->phik, H->phikm1, H->psik, H->guess.phikm2, (int)G,
-                                       1.0 / H->p.dt, H->ctl, H->info);
+                                       1.0 / H->p.dt, H->p.model == MPFC_MODEL_PFC, H->ctl, H->info);
 }
 
 template <int SCH>
@@ -773,7 +775,7 @@ extern "C" int mpfc_energy(mpfc_t* H, mpfc_energy_t* out) {
   double F = 0.25 * h2 * v[0] + 0.5 * alpha * h2 * v[1] - v[2] + 0.5 * h2 * v[3] / (h2 * h2);
   double m1 = h2 * v[4];
   out->F = F;
-  out->pseudoF = F + m1 / (2.0 * H->p.M);
+  out->pseudoF = H->p.model == MPFC_MODEL_PFC ? F : F + m1 / (2.0 * H->p.M);
   out->tildeF = out->pseudoF + 0.5 * v[5];
   out->pinning = h2 * v[6];
   return MPFC_OK;
@@ -829,7 +831,10 @@ extern "C" int mpfc_op_source(mpfc_t* H, int scheme, const double* phik, const d
   L.S3 = S3;
   L.phi = nullptr;
   SourceArgs A{phik, phikm1, psik, H->pin_active ? H->pinW[0] : nullptr, H->pinhat,
-               scheme == 1 ? 1.0 / (p.beta + 1.0 / p.dt) : 2.0 / (p.beta + 2.0 / p.dt), 0.5 * (1.0 - p.epsilon), 2};
+               p.model == MPFC_MODEL_PFC ? 0.0
+               : scheme == 1             ? 1.0 / (p.beta + 1.0 / p.dt)
+                                         : 2.0 / (p.beta + 2.0 / p.dt),
+               0.5 * (1.0 - p.epsilon), 2};
   dim3 g = grid_for(L.m, L.n, kBlk2d);
   if (scheme == 1) k_source_guess<1><<<g, kBlk2d, 0, H->stream>>>(L, A);
   else k_source_guess<2><<<g, kBlk2d, 0, H->stream>>>(L, A);

@@ -34,6 +34,9 @@ MPFC_GUESS_LEARNED = 2
 MPFC_BC_PERIODIC = 0
 MPFC_BC_NEUMANN_Y = 1
 
+MPFC_MODEL_MPFC = 0
+MPFC_MODEL_PFC = 1
+
 
 class mpfc_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("h", ctypes.c_double), ("M", ctypes.c_double),
@@ -41,7 +44,7 @@ class mpfc_params(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("guess", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("bc", ctypes.c_int), ("pinning", ctypes.c_int)]
+                ("bc", ctypes.c_int), ("pinning", ctypes.c_int), ("model", ctypes.c_int)]
 
 
 class mpfc_step_info(ctypes.Structure):
