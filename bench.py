@@ -425,15 +425,12 @@ def run_ours(args):
     # beta ~ U[0.5, 1.5], mean density ~ U[0.05, 0.1], h = 0.5, s = 0.01, noise 0.05 U (seed 4)
     if not args.no_batch:
         from paper_1208_2643_gb300 import tuning
-        rng = np.random.default_rng(4)
-        bs = rng.choice([128, 256, 512, 1024], size=64)
-        bps = [mpfc.default_params(m=int(m), n=int(m), h=0.5, dt=0.01, epsilon=float(rng.uniform(0.02, 0.1)),
-                                   beta=float(rng.uniform(0.5, 1.5)), tol=w["tol"], omega=w["omega"])
-               for m in bs]
-        bbar = rng.uniform(0.05, 0.1, size=64)
+        ens = inputs.ensemble_instances(64, seed=4, rank=rank)
+        bps = [mpfc.default_params(m=e["m"], n=e["n"], h=e["h"], dt=e["dt"], epsilon=e["epsilon"], beta=e["beta"],
+                                   tol=w["tol"], omega=w["omega"]) for e in ens]
         b = mpfc.BatchSolver(bps, stream=stream)
-        for i, bp in enumerate(bps):
-            b.set_state(i, inputs.noise_field(bp.m, bp.n, float(bbar[i]), 0.05, 100 + i + 1000 * rank))
+        for i, e in enumerate(ens):
+            b.set_state(i, e["phi0"])
         tiles = tuning.autotune(b, scheme, reps=3)
         b.step(scheme, 2)
         Kb = max(2, K // 10)
@@ -449,7 +446,7 @@ def run_ours(args):
         seq_ms = 0.0
         for i, bp in enumerate(bps[:16]):
             g1 = mpfc.Solver(bp, stream=stream)
-            g1.set_state(inputs.noise_field(bp.m, bp.n, float(bbar[i]), 0.05, 100 + i + 1000 * rank))
+            g1.set_state(ens[i]["phi0"])
             g1.step(scheme, 2)
             ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ea.record(stream)

@@ -119,3 +119,23 @@ def one_mode_crystal(m: int, n: int, h: float, phi_s: float, eps: float, shift: 
     q = math.sqrt(3.0) / 2.0
     return phi_s + A * (np.cos(q * (X - shift)) * np.cos(q * Y / math.sqrt(3.0))
                         - 0.5 * np.cos(2.0 * q * Y / math.sqrt(3.0)))
+
+
+def ensemble_instances(count: int = 64, seed: int = 4, rank: int = 0):
+    """The batched-ensemble workload: `count` first-order instances with sizes drawn
+    uniformly from {128, 256, 512, 1024}^2, epsilon ~ U[0.02, 0.1], beta ~ U[0.5, 1.5],
+    mean density ~ U[0.05, 0.1], h = 0.5, s = 0.01, and noise 0.05 U(-1, 1) initial
+    data.  Returns a list of dicts: m, n, h, dt, epsilon, beta and phi0."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice([128, 256, 512, 1024], size=count)
+    eps, beta = [], []
+    for _ in range(count):   # drawn per instance, epsilon then beta
+        eps.append(float(rng.uniform(0.02, 0.1)))
+        beta.append(float(rng.uniform(0.5, 1.5)))
+    mean = rng.uniform(0.05, 0.1, size=count)
+    out = []
+    for i in range(count):
+        m = int(sizes[i])
+        out.append(dict(m=m, n=m, h=0.5, dt=0.01, epsilon=eps[i], beta=beta[i],
+                        phi0=noise_field(m, m, float(mean[i]), 0.05, 100 + i + 1000 * rank)))
+    return out
