@@ -105,89 +105,7 @@ __global__ void k_guess_mu(Lev L, Coef k) {
   guess_mu_cell<SCH>(L, k, i, j);
 }
 
-// ---------------------------------------------------------------------------
-// Red-black nonlinear block Gauss-Seidel half sweep (App. B.1 / B.2 smoothing
-// scheme).  Thread (x, j) visits cell i = 2x + ((j + color) & 1) of colour
-// `color` (0 = red, (i+j) even).  Cells of one colour only read the other colour,
-// so a half sweep is exactly parallel.
-// ---------------------------------------------------------------------------
-// EDGE: a row next to a Neumann boundary, where the ghost neighbour is the cell's own
-// unknown (App. A, (A.7)): it leaves the neighbour sums and k holds the coefficients
-// of three neighbours.
-template <int SCH, bool EDGE>
-__device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, int i, int j) {
-  int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
-  size_t c = (size_t)j * m + i;
-  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
-  double* __restrict__ phi = L.phi;
-  double* __restrict__ mu = L.mu;
-  double* __restrict__ ka = L.ka;
-  // neighbours belong to the other colour: read-only during this launch
-  double smu = (__ldg(mu + w) + __ldg(mu + e)) + (__ldg(mu + s) + __ldg(mu + nn));
-  double ska = (__ldg(ka + w) + __ldg(ka + e)) + (__ldg(ka + s) + __ldg(ka + nn));
-  double sph = (__ldg(phi + w) + __ldg(phi + e)) + (__ldg(phi + s) + __ldg(phi + nn));
-  double p = phi[c];
-  if (EDGE) {   // the ghost was read as the cell's current value: take it out again
-    smu -= mu[c];
-    ska -= ka[c];
-    sph -= p;
-  }
-  double R1 = fma(k.cmu, smu, __ldg(L.S1 + c));
-  double R3 = fma(k.th2, sph, __ldg(L.S3 + c));
-  // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
-  // q = g'(p) enters the determinant and the Cramer numerator of mu, and
-  // e = g(p) - g'(p) p the right-hand side of row 2
-  double R2, det, Qq;
-  if (SCH == 1) {
-    double p2 = p * p;
-    R2 = fma(k.ih2, ska, fma(-2.0, p2 * p, __ldg(L.S2 + c)));   // e = -2 p^3
-    det = fma(k.a3, p2, k.D0);                                    // q = 3 p^2
-    Qq = fma(3.0, p2, k.Q0);
-  } else {
-    double pk = __ldg(L.pk + c);
-    double q = dg_of<2>(p, pk);
-    R2 = fma(k.ih2, ska, __ldg(L.S2 + c) + (g_of<2>(p, pk) - q * p));
-    if (L.W) q += __ldg(L.W + c);   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
-    det = fma(k.a, q, k.D0);
-    Qq = k.Q0 + q;
-  }
-  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]]:
-  //   phi* = (R1 + a (b R3 - R2)) / det,  mu* = ((Q0 + q) R1 + R2 - b R3) / det,
-  //   kappa* = R3 - b3 phi*; then u <- (1 - omega) u + omega u*
-  double rdet = rcp_nr(det);
-  double nphi = fma(k.a, fma(k.b, R3, -R2), R1);
-  double nmu = fma(Qq, R1, fma(-k.b, R3, R2));
-  if (k.relax) {
-    double wr = k.omega * rdet;
-    double wphi = nphi * wr;
-    double m0 = mu[c], k0 = ka[c];
-    phi[c] = fma(k.omw, p, wphi);
-    mu[c] = fma(k.omw, m0, nmu * wr);
-    ka[c] = fma(-k.b3, wphi, fma(k.omega, R3, k.omw * k0));
-  } else {
-    double phin = nphi * rdet;
-    phi[c] = phin;
-    mu[c] = nmu * rdet;
-    ka[c] = fma(-k.b3, phin, R3);
-  }
-}
-
-// Rows are warp-uniform, so the branch does not diverge; periodic levels never take
-// it.  Two bodies, each reading its coefficient set at fixed parameter offsets.
-template <int SCH>
-__device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const Coef& kb, int i, int j) {
-  if (L.nyn && (j == 0 || j == L.n - 1)) smooth_cell_body<SCH, true>(L, kb, i, j);
-  else smooth_cell_body<SCH, false>(L, k0, i, j);
-}
-
-template <int SCH>
-__global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, Coef kb, int color) {
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= (L.m >> 1) || j >= L.n) return;
-  smooth_cell<SCH>(L, k, kb, 2 * x + ((j + color) & 1), j);
-}
+#include "fp64_smooth.cuh"
 
 // ---------------------------------------------------------------------------
 // Residual r = S - N(u) at one cell (App. B.1 / B.2 operator N).
@@ -233,25 +151,50 @@ __global__ void k_residual(Lev L, Coef k, double* r1, double* r2, double* r3) {
 // FAS restriction, part 1: per coarse cell, the 2x2 averages of u and of the
 // fine residual.  u_c = R u (also kept in b), S_c = R r (part 2 adds N_c(u_c)).
 // ---------------------------------------------------------------------------
+// Summed over a 2x2 block B of fine cells, the five-point Laplacian needs no per-cell
+// evaluation: each cell of B is an inner neighbour of two others, so
+//   sum_{c in B} Delta_h f(c) = (sum of the 8 cells bordering B - 2 sum_{c in B} f) / h^2.
+// The restricted residual R r = (1/4) sum_B (S - N(u)) therefore takes the block sums
+// of S, u and of the Laplacians, plus the per-cell nonlinear term (and the pinning
+// term), instead of four full residual evaluations.
 template <int SCH>
 __device__ __forceinline__ void resid_restrict_cell(const Lev& F, const Lev& C, const Coef& kf, int keep_b, int I,
                                                     int J) {
-  double sr1 = 0.0, sr2 = 0.0, sr3 = 0.0, sp = 0.0, sm = 0.0, sk = 0.0;
+  const int m = F.m, i0 = 2 * I, j0 = 2 * J;
+  const int iw = wrapm(i0 - 1, m), ie = wrapm(i0 + 2, m);
+  const int js = ywrap(j0 - 1, F.n, F.nyn), jn = ywrap(j0 + 2, F.n, F.nyn);
+  const size_t r0 = (size_t)j0 * m, r1 = r0 + m, rs = (size_t)js * m, rn = (size_t)jn * m;
+  // block sum and the sum over the 8 bordering cells of one field
+  auto sums = [&](const double* f, double& blk, double& outer) {
+    blk = (__ldg(f + r0 + i0) + __ldg(f + r0 + i0 + 1)) + (__ldg(f + r1 + i0) + __ldg(f + r1 + i0 + 1));
+    outer = ((__ldg(f + r0 + iw) + __ldg(f + r1 + iw)) + (__ldg(f + r0 + ie) + __ldg(f + r1 + ie))) +
+            ((__ldg(f + rs + i0) + __ldg(f + rs + i0 + 1)) + (__ldg(f + rn + i0) + __ldg(f + rn + i0 + 1)));
+  };
+  double sp, op, sm, om, sk, ok;
+  sums(F.phi, sp, op);
+  sums(F.mu, sm, om);
+  sums(F.ka, sk, ok);
+  double gs = 0.0;   // sum of the per-cell nonlinear term (and pinning term) of row 2
 #pragma unroll
   for (int dj = 0; dj < 2; ++dj)
 #pragma unroll
     for (int di = 0; di < 2; ++di) {
-      int i = 2 * I + di, j = 2 * J + dj;
-      double a, b, c;
-      resid_at<SCH>(F, kf, i, j, a, b, c);
-      sr1 += a;
-      sr2 += b;
-      sr3 += c;
-      size_t id = (size_t)j * F.m + i;
-      sp += __ldg(F.phi + id);
-      sm += __ldg(F.mu + id);
-      sk += __ldg(F.ka + id);
+      const size_t id = (dj ? r1 : r0) + i0 + di;
+      const double p = __ldg(F.phi + id);
+      const double pk = (SCH == 2) ? __ldg(F.pk + id) : 0.0;
+      gs += g_of<SCH>(p, pk);
+      if (SCH == 2 && F.W) gs = fma(__ldg(F.W + id), p, gs);
     }
+  const double ss1 = (__ldg(F.S1 + r0 + i0) + __ldg(F.S1 + r0 + i0 + 1)) +
+                     (__ldg(F.S1 + r1 + i0) + __ldg(F.S1 + r1 + i0 + 1));
+  const double ss2 = (__ldg(F.S2 + r0 + i0) + __ldg(F.S2 + r0 + i0 + 1)) +
+                     (__ldg(F.S2 + r1 + i0) + __ldg(F.S2 + r1 + i0 + 1));
+  const double ss3 = (__ldg(F.S3 + r0 + i0) + __ldg(F.S3 + r0 + i0 + 1)) +
+                     (__ldg(F.S3 + r1 + i0) + __ldg(F.S3 + r1 + i0 + 1));
+  // sum_B r1 = sum S1 - sum phi + c sum Delta_h mu, and likewise rows 2 and 3
+  const double sr1 = fma(kf.cmu, fma(-2.0, sm, om), ss1 - sp);
+  const double sr2 = fma(kf.ih2, fma(-2.0, sk, ok), fma(kf.gam, sp, ss2 - sm) + gs);
+  const double sr3 = fma(kf.th2, fma(-2.0, sp, op), ss3 - sk);
   size_t cid = (size_t)J * C.m + I;
   double up = 0.25 * sp, um = 0.25 * sm, uk = 0.25 * sk;
   C.phi[cid] = up;

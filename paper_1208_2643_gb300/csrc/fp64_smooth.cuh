@@ -1,0 +1,90 @@
+// The FP64 red-black nonlinear block Gauss-Seidel half sweep (App. B.1 / B.2
+// smoothing schemes), kept in its own header: the DRAM traffic recorded for the
+// roofline is tied to this file's contents.  Included by fp64_kernels.cuh inside
+// namespace mpfc.
+#pragma once
+
+// ---------------------------------------------------------------------------
+// Red-black nonlinear block Gauss-Seidel half sweep (App. B.1 / B.2 smoothing
+// scheme).  Thread (x, j) visits cell i = 2x + ((j + color) & 1) of colour
+// `color` (0 = red, (i+j) even).  Cells of one colour only read the other colour,
+// so a half sweep is exactly parallel.
+// ---------------------------------------------------------------------------
+// EDGE: a row next to a Neumann boundary, where the ghost neighbour is the cell's own
+// unknown (App. A, (A.7)): it leaves the neighbour sums and k holds the coefficients
+// of three neighbours.
+template <int SCH, bool EDGE>
+__device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, int i, int j) {
+  int m = L.m;
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
+  size_t c = (size_t)j * m + i;
+  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
+  double* __restrict__ phi = L.phi;
+  double* __restrict__ mu = L.mu;
+  double* __restrict__ ka = L.ka;
+  // neighbours belong to the other colour: read-only during this launch
+  double smu = (__ldg(mu + w) + __ldg(mu + e)) + (__ldg(mu + s) + __ldg(mu + nn));
+  double ska = (__ldg(ka + w) + __ldg(ka + e)) + (__ldg(ka + s) + __ldg(ka + nn));
+  double sph = (__ldg(phi + w) + __ldg(phi + e)) + (__ldg(phi + s) + __ldg(phi + nn));
+  double p = phi[c];
+  if (EDGE) {   // the ghost was read as the cell's current value: take it out again
+    smu -= mu[c];
+    ska -= ka[c];
+    sph -= p;
+  }
+  double R1 = fma(k.cmu, smu, __ldg(L.S1 + c));
+  double R3 = fma(k.th2, sph, __ldg(L.S3 + c));
+  // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
+  // q = g'(p) enters the determinant and the Cramer numerator of mu, and
+  // e = g(p) - g'(p) p the right-hand side of row 2
+  double R2, det, Qq;
+  if (SCH == 1) {
+    double p2 = p * p;
+    R2 = fma(k.ih2, ska, fma(-2.0, p2 * p, __ldg(L.S2 + c)));   // e = -2 p^3
+    det = fma(k.a3, p2, k.D0);                                    // q = 3 p^2
+    Qq = fma(3.0, p2, k.Q0);
+  } else {
+    double pk = __ldg(L.pk + c);
+    double q = dg_of<2>(p, pk);
+    R2 = fma(k.ih2, ska, __ldg(L.S2 + c) + (g_of<2>(p, pk) - q * p));
+    if (L.W) q += __ldg(L.W + c);   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
+    det = fma(k.a, q, k.D0);
+    Qq = k.Q0 + q;
+  }
+  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]]:
+  //   phi* = (R1 + a (b R3 - R2)) / det,  mu* = ((Q0 + q) R1 + R2 - b R3) / det,
+  //   kappa* = R3 - b3 phi*; then u <- (1 - omega) u + omega u*
+  double rdet = rcp_nr(det);
+  double nphi = fma(k.a, fma(k.b, R3, -R2), R1);
+  double nmu = fma(Qq, R1, fma(-k.b, R3, R2));
+  if (k.relax) {
+    double wr = k.omega * rdet;
+    double wphi = nphi * wr;
+    double m0 = mu[c], k0 = ka[c];
+    phi[c] = fma(k.omw, p, wphi);
+    mu[c] = fma(k.omw, m0, nmu * wr);
+    ka[c] = fma(-k.b3, wphi, fma(k.omega, R3, k.omw * k0));
+  } else {
+    double phin = nphi * rdet;
+    phi[c] = phin;
+    mu[c] = nmu * rdet;
+    ka[c] = fma(-k.b3, phin, R3);
+  }
+}
+
+// Rows are warp-uniform, so the branch does not diverge; periodic levels never take
+// it.  Two bodies, each reading its coefficient set at fixed parameter offsets.
+template <int SCH>
+__device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const Coef& kb, int i, int j) {
+  if (L.nyn && (j == 0 || j == L.n - 1)) smooth_cell_body<SCH, true>(L, kb, i, j);
+  else smooth_cell_body<SCH, false>(L, k0, i, j);
+}
+
+template <int SCH>
+__global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, Coef kb, int color) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= (L.m >> 1) || j >= L.n) return;
+  smooth_cell<SCH>(L, k, kb, 2 * x + ((j + color) & 1), j);
+}
+
