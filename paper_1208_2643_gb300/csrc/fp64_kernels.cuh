@@ -375,6 +375,10 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
     __syncwarp();
     for (int t = lane; t < G; t += 32)
       Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t, nyn) - 4.0 * muv[t]));
+    // the diagonal factor gam + W + g'(phi) of each column, once per column (d is free
+    // until the back-substitution below)
+    for (int t = lane; t < G; t += 32) d[t] = gamf + (float)((C.W ? C.W[t] : 0.0) + dg_of<SCH>(ph[t], pk[t]));
+    __syncwarp();
     for (int idx = lane; idx < G * G; idx += 32) {
       int r = idx / G, col = idx % G;
       int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
@@ -382,7 +386,7 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
       int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
                 (ci == ri && cj == ywrap(rj - 1, n, nyn)) + (ci == ri && cj == ywrap(rj + 1, n, nyn));
       float Lrc = ih2f * ((float)cnt - (r == col ? 4.f : 0.f));
-      Jm[r * W + col] = K3f[idx] - cf * Lrc * (gamf + (float)((C.W ? C.W[col] : 0.0) + dg_of<SCH>(ph[col], pk[col])));
+      Jm[r * W + col] = K3f[idx] - cf * Lrc * d[col];
     }
     __syncwarp();
     for (int col = 0; col < G; ++col) {
