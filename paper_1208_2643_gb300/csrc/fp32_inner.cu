@@ -55,6 +55,7 @@ dim3 grid_of(int X, int Y) { return dim3((X + kBlk.x - 1) / kBlk.x, (Y + kBlk.y 
 template <int SCH>
 __global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl, double* partials, int mode,
                                                 cudaGraphConditionalHandle hnd, int set_cond) {
+  pdl_enter();
   double v[1] = {0.0};
   int G = L.m * L.n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl
 
 // u += e (FP64 update with the FP32 correction)
 __global__ void k_update(Lev L, Lev32 E) {
+  pdl_enter();
   int G = L.m * L.n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
     float a = E.ephi[t], b = E.emu[t], c = E.eka[t];
@@ -106,6 +108,7 @@ __global__ void k_update(Lev L, Lev32 E) {
 }
 
 __global__ void k_restrict_q(const float* __restrict__ qf, float* __restrict__ qc, int mc, int nc) {
+  pdl_enter();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mc || J >= nc) return;
@@ -119,6 +122,7 @@ __global__ void k_restrict_q(const float* __restrict__ qf, float* __restrict__ q
 // the frozen linearisation q = gam + g'(phi)).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_smooth32(Lev32 L, Coef32 k, int color) {
+  pdl_enter();
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int m = L.m;
@@ -176,6 +180,7 @@ __device__ __forceinline__ void defect32(const Lev32& L, const Coef32& k, int i,
 
 // coarse source = R(r - J e), coarse correction starts at zero
 __global__ void k_restrict_defect32(Lev32 F, Lev32 C, Coef32 kf) {
+  pdl_enter();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= C.m || J >= C.n) return;
@@ -226,6 +231,7 @@ __device__ __forceinline__ void prolong32_plane(const float* __restrict__ ec, fl
 }
 
 __global__ void __launch_bounds__(kTX * kTY) k_prolong32(Lev32 F, Lev32 C) {
+  pdl_enter();
   __shared__ float E[kTY + 2][kTX + 2];
   prolong32_plane(C.ephi, F.ephi, C.m, C.n, E);
   prolong32_plane(C.emu, F.emu, C.m, C.n, E);
@@ -245,6 +251,7 @@ __device__ __forceinline__ float nbsum32(const float* f, int m, int n, int t) {
 }
 
 __global__ void k_coarse32(Lev32 C, Coef32 k, const float* __restrict__ K3f) {
+  pdl_enter();
   extern __shared__ float smf[];
   const int m = C.m, n = C.n, G = m * n, W = G + 1;
   float* A = smf;
@@ -321,11 +328,11 @@ size_t coarse32_smem(const Lev32& C) {
 // `sweeps` red-black sweeps of one level, one launch per colour.  (A single-launch
 // sweep over shared-memory tiles with a 2-cell halo halves the DRAM reads at 2048^2 but
 // was slower on GB300 at every level size measured: its staging is latency bound.)
-void sweeps32(const Lev32& F, const Coef32& kf, int sweeps, cudaStream_t s) {
-  dim3 g = grid_of(F.m / 2, F.n);
+void sweeps32(const mpfc_launch_shape& sh, const Lev32& F, const Coef32& kf, int sweeps, cudaStream_t s) {
+  dim3 g = mpfc_grid_of(sh, F.m / 2, F.n), b = mpfc_blk_for(sh, F.m / 2, F.n);
   for (int sw = 0; sw < sweeps; ++sw) {
-    k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 0);
-    k_smooth32<<<g, kBlk, 0, s>>>(F, kf, 1);
+    mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, 0);
+    mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, 1);
   }
 }
 
@@ -334,22 +341,24 @@ int inner_cycles_of(const mpfc_s* H) { return H->p.inner_cycles > 0 ? H->p.inner
 // One inner correction-scheme V-cycle.
 void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
   const mpfc_params& p = H->p;
+  const mpfc_launch_shape& sh = H->shape;
   int L = H->nlev;
   for (int l = 0; l < L - 1; ++l) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
-    sweeps32(F, kf, p.nu1, s);
-    k_restrict_defect32<<<grid_of(C.m, C.n), kBlk, 0, s>>>(F, C, kf);
+    sweeps32(sh, F, kf, p.nu1, s);
+    mpfc_launch(sh, k_restrict_defect32, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C, kf);
   }
   const Lev32& Cc = H->lev32[L - 1];
-  k_coarse32<<<1, 256, coarse32_smem(Cc), s>>>(Cc, coef32_of(H->coef[scheme - 1][L - 1]), H->K3f[scheme - 1]);
+  mpfc_launch(sh, k_coarse32, dim3(1), dim3(256), coarse32_smem(Cc), s, Cc, coef32_of(H->coef[scheme - 1][L - 1]),
+              (const float*)H->K3f[scheme - 1]);
   for (int l = L - 2; l >= 0; --l) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
-    k_prolong32<<<grid_of(C.m, C.n), kBlk, 0, s>>>(F, C);
-    sweeps32(F, kf, p.nu2, s);
+    mpfc_launch(sh, k_prolong32, grid_of(C.m, C.n), kBlk, 0, s, F, C);
+    sweeps32(sh, F, kf, p.nu2, s);
   }
 }
 
@@ -357,9 +366,11 @@ void enqueue_defect(mpfc_s* H, int scheme, int mode, cudaGraphConditionalHandle 
   const Lev& L0 = H->lev[0];
   int blocks = mpfc_reduce_blocks((size_t)L0.m * L0.n);
   if (scheme == 1)
-    k_defect<1><<<blocks, 256, 0, s>>>(L0, H->coef[0][0], H->lev32[0], H->ctl, H->partials, mode, hnd, set_cond);
+    mpfc_launch(H->shape, k_defect<1>, dim3(blocks), dim3(256), 0, s, L0, H->coef[0][0], H->lev32[0], H->ctl,
+                H->partials, mode, hnd, set_cond);
   else
-    k_defect<2><<<blocks, 256, 0, s>>>(L0, H->coef[1][0], H->lev32[0], H->ctl, H->partials, mode, hnd, set_cond);
+    mpfc_launch(H->shape, k_defect<2>, dim3(blocks), dim3(256), 0, s, L0, H->coef[1][0], H->lev32[0], H->ctl,
+                H->partials, mode, hnd, set_cond);
 }
 
 // Body of one outer iteration: restrict q to the coarse grids, the inner V-cycles,
@@ -367,11 +378,12 @@ void enqueue_defect(mpfc_s* H, int scheme, int mode, cudaGraphConditionalHandle 
 void outer_body(mpfc_s* H, int scheme, cudaStream_t s, cudaGraphConditionalHandle hnd, int set_cond) {
   for (int l = 1; l < H->nlev; ++l) {
     const Lev32& C = H->lev32[l];
-    k_restrict_q<<<grid_of(C.m, C.n), kBlk, 0, s>>>(H->lev32[l - 1].q, C.q, C.m, C.n);
+    mpfc_launch(H->shape, k_restrict_q, grid_of(C.m, C.n), kBlk, 0, s, (const float*)H->lev32[l - 1].q, C.q, C.m,
+                C.n);
   }
   for (int c = 0; c < inner_cycles_of(H); ++c) enqueue_inner_vcycle(H, scheme, s);
   const Lev& L0 = H->lev[0];
-  k_update<<<mpfc_reduce_blocks((size_t)L0.m * L0.n), 256, 0, s>>>(L0, H->lev32[0]);
+  mpfc_launch(H->shape, k_update, dim3(mpfc_reduce_blocks((size_t)L0.m * L0.n)), dim3(256), 0, s, L0, H->lev32[0]);
   enqueue_defect(H, scheme, 1, hnd, set_cond, s);
 }
 

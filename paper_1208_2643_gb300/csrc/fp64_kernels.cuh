@@ -60,6 +60,7 @@ __device__ __forceinline__ void source_cell(const Lev& L, const SourceArgs& A, i
 
 template <int SCH>
 __global__ void k_source_guess(Lev L, SourceArgs A) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.m || j >= L.n) return;
@@ -77,6 +78,7 @@ __device__ __forceinline__ void guess_kappa_cell(const Lev& L, const Coef& k, in
 }
 
 static __global__ void k_guess_kappa(Lev L, Coef k) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.m || j >= L.n) return;
@@ -99,6 +101,7 @@ __device__ __forceinline__ void guess_mu_cell(const Lev& L, const Coef& k, int i
 
 template <int SCH>
 __global__ void k_guess_mu(Lev L, Coef k) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= L.m || j >= L.n) return;
@@ -212,6 +215,7 @@ __device__ __forceinline__ void resid_restrict_cell(const Lev& F, const Lev& C, 
 
 template <int SCH>
 __global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
+  pdl_enter();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= C.m || J >= C.n) return;
@@ -244,6 +248,7 @@ __device__ __forceinline__ void tau_cell(const Lev& C, const Coef& k, int i, int
 
 template <int SCH>
 __global__ void k_tau(Lev C, Coef k) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= C.m || j >= C.n) return;
@@ -252,6 +257,7 @@ __global__ void k_tau(Lev C, Coef k) {
 
 // Plain 2x2 average of one plane (phi^k onto the coarse levels, scheme 2).
 static __global__ void k_restrict_plane(const double* __restrict__ f, double* __restrict__ c, int mc, int nc) {
+  pdl_enter();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mc || J >= nc) return;
@@ -315,6 +321,7 @@ __device__ __forceinline__ void prolong_tile(const ProlongArgs& A, double (*E)[k
 }
 
 static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
+  pdl_enter();
   __shared__ double E[kPTY + 2][kPTX + 2];
   prolong_tile(A, E, blockIdx.x * kPTX, blockIdx.y * kPTY);
 }
@@ -323,8 +330,8 @@ static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
 // Coarsest level: Newton on the eliminated equation for phi,
 //   F(phi) = phi - c L (S2 + g(phi) + gam phi + L (S3 + theta L phi)) - S1 = 0,
 // with Jacobian J = K3 - c L diag(gam + g'(phi)), K3 = I - c theta L^3 built on the
-// host.  Dense Gaussian elimination with partial pivoting in shared memory, one
-// warp.  Stops one iteration after the update falls below 1e-15 (1 + |phi|_inf);
+// host.  FP32 elimination on one warp (registers up to 31 cells, shared memory up to
+// 64).  Stops one iteration after the update falls below 1e-15 (1 + |phi|_inf);
 // at most 40 iterations.  mu and kappa are then recovered from rows 3 and 2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t, int nyn) {
@@ -333,15 +340,68 @@ __device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t, 
          (f[ywrap(j - 1, n, nyn) * m + i] + f[ywrap(j + 1, n, nyn) * m + i]);
 }
 
-template <int SCH>
-__device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __restrict__ K3f) {
-  // One warp.  Newton's method for F(phi) = 0 with F evaluated in FP64; the
-  // Jacobian is assembled, factorised (Gaussian elimination, partial pivoting) and
-  // solved in FP32, i.e. Newton with iterative refinement: every update is computed
-  // from the FP64 residual, so the iteration converges to the FP64 root.  FP32 keeps
-  // the serial elimination off the slow FP64 pipe (on GB300 one warp-wide FP64
-  // instruction occupies a sub-partition's FP64 unit for about 80 cycles).
-  extern __shared__ double sm[];
+// Gauss-Jordan elimination with implicit partial pivoting on [J | rhs], one column per
+// lane held in registers (lane c < G: column c of J; lane G: the right-hand side), R
+// register rows (R >= G).  Column col: the lane that holds it picks the unused row of
+// largest magnitude, every lane divides its entry of that row by the pivot and
+// subtracts multiples of it from all other rows.  No row is moved: afterwards row
+// pivs[col] holds unknown col in the right-hand-side lane.  Writes the solution to
+// x[0..G); xr (G floats) and pivs (G ints) are shared scratch.
+template <int R>
+__device__ __forceinline__ void gauss_jordan_cols(float (&a)[R], int G, float* x, float* xr, int* pivs) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned used = 0u;
+  for (int col = 0; col < G; ++col) {
+    float best = -1.f;
+    int pr = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float v = fabsf(a[r]);
+      if (r < G && !((used >> r) & 1u) && v > best) {
+        best = v;
+        pr = r;
+      }
+    }
+    pr = __shfl_sync(FULL, pr, col);
+    float vp = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r == pr) vp = a[r];
+    const float rp = 1.f / __shfl_sync(FULL, vp, col);
+    const float vn = vp * rp;   // this lane's entry of the normalised pivot row
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float f = __shfl_sync(FULL, a[r], col);
+      a[r] = (r == pr) ? vn : fmaf(-f, vn, a[r]);
+    }
+    used |= 1u << pr;
+    if (lane == 0) pivs[col] = pr;
+  }
+  if (lane == G)
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r < G) xr[r] = a[r];
+  __syncwarp();
+  for (int t = lane; t < G; t += 32) x[t] = xr[pivs[t]];
+  __syncwarp();
+}
+
+// Entry (r, col) of c L, L the five-point Laplacian of the coarsest grid (a Neumann
+// ghost is the cell itself, so it lands on the diagonal: count 3 - 4).
+__device__ __forceinline__ float coarse_cL(const Lev& C, float cih2, int r, int col) {
+  const int m = C.m, n = C.n, nyn = C.nyn;
+  int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
+  int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
+            (ci == ri && cj == ywrap(rj - 1, n, nyn)) + (ci == ri && cj == ywrap(rj + 1, n, nyn));
+  return cih2 * ((float)cnt - (r == col ? 4.f : 0.f));
+}
+
+// The Newton iteration on the coarsest grid.  R > 0: grids of at most min(R, 31)
+// cells, one Jacobian column per lane in R registers (gauss_jordan_cols); R == 0:
+// up to 64 cells, Gaussian elimination with row swaps in shared memory.
+template <int SCH, int R>
+__device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restrict__ K3f, double* sm) {
   const int m = C.m, n = C.n, G = m * n, W = G + 1;
   double* ph = sm;
   double* s1 = ph + G;
@@ -354,7 +414,6 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
   float* d = Jm + G * W;
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  if (threadIdx.x >= 32) return;
   for (int t = lane; t < G; t += 32) {
     ph[t] = C.phi[t];
     s1[t] = C.S1[t];
@@ -364,64 +423,82 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
   }
   __syncwarp();
   const float cf = (float)k.c, ih2f = (float)k.ih2, gamf = (float)k.gam;
+  constexpr int RR = R > 0 ? R : 1;
+  float k3c[RR], lcc[RR];   // this lane's column of K3 and of c L (register path)
+  if (R > 0) {
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      k3c[r] = (lane < G && r < G) ? K3f[r * G + lane] : 0.f;
+      lcc[r] = (lane < G && r < G) ? cf * coarse_cL(C, ih2f, r, lane) : 0.f;
+    }
+  }
+  auto kappa_at = [&](int t) { return s3[t] + k.th2 * (nbsum_s(ph, m, n, t, C.nyn) - 4.0 * ph[t]); };
+  auto mu_at = [&](int t) {
+    return s2[t] + g_of<SCH>(ph[t], pk[t]) + (k.gam + (C.W ? C.W[t] : 0.0)) * ph[t] +
+           k.ih2 * (nbsum_s(kap, m, n, t, C.nyn) - 4.0 * kap[t]);
+  };
   bool extra = false;
   for (int it = 0; it < 40; ++it) {
-    const int nyn = C.nyn;
-    for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t, nyn) - 4.0 * ph[t]);
+    for (int t = lane; t < G; t += 32) kap[t] = kappa_at(t);
+    __syncwarp();
+    for (int t = lane; t < G; t += 32) muv[t] = mu_at(t);
     __syncwarp();
     for (int t = lane; t < G; t += 32)
-      muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + (k.gam + (C.W ? C.W[t] : 0.0)) * ph[t] +
-               k.ih2 * (nbsum_s(kap, m, n, t, nyn) - 4.0 * kap[t]);
-    __syncwarp();
-    for (int t = lane; t < G; t += 32)
-      Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t, nyn) - 4.0 * muv[t]));
-    // the diagonal factor gam + W + g'(phi) of each column, once per column (d is free
-    // until the back-substitution below)
+      Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t, C.nyn) - 4.0 * muv[t]));
+    // the diagonal factor gam + W + g'(phi) of each column, once per column
     for (int t = lane; t < G; t += 32) d[t] = gamf + (float)((C.W ? C.W[t] : 0.0) + dg_of<SCH>(ph[t], pk[t]));
     __syncwarp();
-    for (int idx = lane; idx < G * G; idx += 32) {
-      int r = idx / G, col = idx % G;
-      int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
-      // a Neumann ghost is the cell itself, so it lands on the diagonal (count 3 - 4)
-      int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
-                (ci == ri && cj == ywrap(rj - 1, n, nyn)) + (ci == ri && cj == ywrap(rj + 1, n, nyn));
-      float Lrc = ih2f * ((float)cnt - (r == col ? 4.f : 0.f));
-      Jm[r * W + col] = K3f[idx] - cf * Lrc * d[col];
-    }
-    __syncwarp();
-    for (int col = 0; col < G; ++col) {
-      float best = -1.f;
-      int piv = col;
-      for (int r = col + lane; r < G; r += 32) {
-        float v = fabsf(Jm[r * W + col]);
-        if (v > best) { best = v; piv = r; }
+    if (R > 0) {
+      // J = K3 - c L diag(d): this lane's column, or the right-hand side in lane G
+      float a[RR];
+      const float dc = lane < G ? d[lane] : 0.f;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        const float rhs = (lane == G && r < G) ? Jm[r * W + G] : 0.f;
+        a[r] = lane < G ? fmaf(-lcc[r], dc, k3c[r]) : rhs;
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        float ob = __shfl_down_sync(FULL, best, o);
-        int op = __shfl_down_sync(FULL, piv, o);
-        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+      __syncwarp();   // Jm is free from here: pivot scratch
+      gauss_jordan_cols<RR>(a, G, d, Jm + G, reinterpret_cast<int*>(Jm));
+    } else {
+      for (int idx = lane; idx < G * G; idx += 32) {
+        int r = idx / G, col = idx % G;
+        Jm[r * W + col] = K3f[idx] - cf * coarse_cL(C, ih2f, r, col) * d[col];
       }
-      piv = __shfl_sync(FULL, piv, 0);
-      if (piv != col)
-        for (int c2 = col + lane; c2 <= G; c2 += 32) {
-          float t = Jm[col * W + c2];
-          Jm[col * W + c2] = Jm[piv * W + c2];
-          Jm[piv * W + c2] = t;
+      __syncwarp();
+      for (int col = 0; col < G; ++col) {
+        float best = -1.f;
+        int piv = col;
+        for (int r = col + lane; r < G; r += 32) {
+          float v = fabsf(Jm[r * W + col]);
+          if (v > best) { best = v; piv = r; }
         }
-      __syncwarp();
-      float rp = 1.f / Jm[col * W + col];
-      for (int r = col + 1 + lane; r < G; r += 32) {
-        float f = Jm[r * W + col] * rp;
-        for (int c2 = col + 1; c2 <= G; ++c2) Jm[r * W + c2] = fmaf(-f, Jm[col * W + c2], Jm[r * W + c2]);
+        for (int o = 16; o > 0; o >>= 1) {
+          float ob = __shfl_down_sync(FULL, best, o);
+          int op = __shfl_down_sync(FULL, piv, o);
+          if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+        }
+        piv = __shfl_sync(FULL, piv, 0);
+        if (piv != col)
+          for (int c2 = col + lane; c2 <= G; c2 += 32) {
+            float t = Jm[col * W + c2];
+            Jm[col * W + c2] = Jm[piv * W + c2];
+            Jm[piv * W + c2] = t;
+          }
+        __syncwarp();
+        float rp = 1.f / Jm[col * W + col];
+        for (int r = col + 1 + lane; r < G; r += 32) {
+          float f = Jm[r * W + col] * rp;
+          for (int c2 = col + 1; c2 <= G; ++c2) Jm[r * W + c2] = fmaf(-f, Jm[col * W + c2], Jm[r * W + c2]);
+        }
+        __syncwarp();
       }
-      __syncwarp();
-    }
-    for (int r = G - 1; r >= 0; --r) {
-      float acc = 0.f;
-      for (int c2 = r + 1 + lane; c2 < G; c2 += 32) acc = fmaf(Jm[r * W + c2], d[c2], acc);
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
-      if (lane == 0) d[r] = (Jm[r * W + G] - acc) / Jm[r * W + r];
-      __syncwarp();
+      for (int r = G - 1; r >= 0; --r) {
+        float acc = 0.f;
+        for (int c2 = r + 1 + lane; c2 < G; c2 += 32) acc = fmaf(Jm[r * W + c2], d[c2], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+        if (lane == 0) d[r] = (Jm[r * W + G] - acc) / Jm[r * W + r];
+        __syncwarp();
+      }
     }
     float dmax = 0.f;
     double umax = 0.0;
@@ -439,19 +516,34 @@ __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __r
     if (extra || !(dmax == dmax)) break;
     if ((double)dmax <= 1e-15 * (1.0 + umax)) extra = true;
   }
-  for (int t = lane; t < G; t += 32) kap[t] = s3[t] + k.th2 * (nbsum_s(ph, m, n, t, C.nyn) - 4.0 * ph[t]);
+  for (int t = lane; t < G; t += 32) kap[t] = kappa_at(t);
   __syncwarp();
   for (int t = lane; t < G; t += 32) {
-    muv[t] = s2[t] + g_of<SCH>(ph[t], pk[t]) + (k.gam + (C.W ? C.W[t] : 0.0)) * ph[t] +
-             k.ih2 * (nbsum_s(kap, m, n, t, C.nyn) - 4.0 * kap[t]);
+    muv[t] = mu_at(t);
     C.phi[t] = ph[t];
     C.ka[t] = kap[t];
     C.mu[t] = muv[t];
   }
 }
 
+// One warp.  Newton's method for F(phi) = 0 with F evaluated in FP64; the Jacobian
+// is assembled, factorised and solved in FP32, i.e. Newton with iterative refinement:
+// every update is computed from the FP64 residual, so the iteration converges to the
+// FP64 root.  FP32 keeps the elimination off the slow FP64 pipe (on GB300 one
+// warp-wide FP64 instruction occupies a sub-partition's FP64 unit for about 80 cycles).
+template <int SCH>
+__device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __restrict__ K3f) {
+  extern __shared__ double sm[];
+  if (threadIdx.x >= 32) return;
+  const int G = C.m * C.n;
+  if (G <= 16) coarse_newton<SCH, 16>(C, k, K3f, sm);
+  else if (G <= 31) coarse_newton<SCH, 32>(C, k, K3f, sm);
+  else coarse_newton<SCH, 0>(C, k, K3f, sm);
+}
+
 template <int SCH>
 __global__ void k_coarse_solve(Lev C, Coef k, const float* __restrict__ K3f) {
+  pdl_enter();
   coarse_solve_block<SCH>(C, k, K3f);
 }
 
@@ -519,6 +611,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NS], double* partials, unsi
 template <int SCH>
 __global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double* partials, int mode,
                                                  cudaGraphConditionalHandle hnd, int set_cond) {
+  pdl_enter();
   double v[1] = {0.0};
   int G = L.m * L.n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
@@ -551,6 +644,7 @@ __global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double
 // Step bookkeeping and the psi update.
 // ---------------------------------------------------------------------------
 static __global__ void k_step_begin(Ctl* ctl) {
+  pdl_enter();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctl->skip = ctl->halt;
     ctl->cycles = 0;
@@ -582,6 +676,7 @@ template <int SCH>
 // velocity unknown); otherwise (3.9) / (3.15).
 __global__ void k_commit(const double* __restrict__ phinew, double* phik, double* phikm1, double* psik,
                          double* phikm2, int G, double inv_s, int pfc, Ctl* ctl, StepRecord* info) {
+  pdl_enter();
   int st = step_status(ctl);
   int skip = ctl->skip;
   if (blockIdx.x == 0 && threadIdx.x == 0 && !skip) {

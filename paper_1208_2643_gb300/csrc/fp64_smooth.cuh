@@ -82,6 +82,7 @@ __device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const 
 
 template <int SCH>
 __global__ void __launch_bounds__(256) k_smooth(Lev L, Coef k, Coef kb, int color) {
+  pdl_enter();
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= (L.m >> 1) || j >= L.n) return;

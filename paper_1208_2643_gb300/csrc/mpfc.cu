@@ -353,11 +353,12 @@ int mpfc_reduce_blocks(size_t G) {
 }
 
 template <int SCH>
-static void launch_smooth(const Lev& L, const Coef& k, const Coef& kb, int sweeps, cudaStream_t s) {
-  dim3 g = grid_for(L.m / 2, L.n, kBlk2d);
+static void launch_smooth(const mpfc_launch_shape& sh, const Lev& L, const Coef& k, const Coef& kb, int sweeps,
+                          cudaStream_t s) {
+  dim3 b = mpfc_blk_for(sh, L.m / 2, L.n), g = mpfc_grid_of(sh, L.m / 2, L.n);
   for (int sw = 0; sw < sweeps; ++sw) {
-    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, kb, 0);
-    k_smooth<SCH><<<g, kBlk2d, 0, s>>>(L, k, kb, 1);
+    mpfc_launch(sh, k_smooth<SCH>, g, b, 0, s, L, k, kb, 0);
+    mpfc_launch(sh, k_smooth<SCH>, g, b, 0, s, L, k, kb, 1);
   }
 }
 
@@ -368,27 +369,29 @@ static size_t coarse_smem(const Lev& C) {
 
 template <int SCH>
 static void launch_coarse(mpfc_s* H, const Lev& C, const Coef& k, cudaStream_t s) {
-  k_coarse_solve<SCH><<<1, 32, coarse_smem(C), s>>>(C, k, H->K3[SCH - 1]);
+  mpfc_launch(H->shape, k_coarse_solve<SCH>, dim3(1), dim3(32), coarse_smem(C), s, C, k, (const float*)H->K3[SCH - 1]);
 }
 
 template <int SCH>
 static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
   const mpfc_params& p = H->p;
+  const mpfc_launch_shape& sh = H->shape;
   int L = H->nlev;
   for (int l = 0; l < L - 1; ++l) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
-    launch_smooth<SCH>(F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu1, s);
-    k_resid_restrict<SCH><<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(F, C, H->coef[SCH - 1][l], 1);
-    k_tau<SCH><<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(C, H->coef[SCH - 1][l + 1]);
+    launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu1, s);
+    mpfc_launch(sh, k_resid_restrict<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C,
+               H->coef[SCH - 1][l], 1);
+    mpfc_launch(sh, k_tau<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, C, H->coef[SCH - 1][l + 1]);
   }
   launch_coarse<SCH>(H, H->lev[L - 1], H->coef[SCH - 1][L - 1], s);
   for (int l = L - 2; l >= 0; --l) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
     ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n, C.nyn};
-    k_prolong<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(A);
-    launch_smooth<SCH>(F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu2, s);
+    mpfc_launch(sh, k_prolong, grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s, A);
+    launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu2, s);
   }
 }
 
@@ -396,7 +399,7 @@ template <int SCH>
 static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
   const mpfc_params& p = H->p;
   const Lev& L0 = H->lev[0];
-  k_step_begin<<<1, 32, 0, s>>>(H->ctl);
+  mpfc_launch(H->shape, k_step_begin, dim3(1), dim3(32), 0, s, H->ctl);
   SourceArgs A;
   A.phik = H->phik;
   A.phikm1 = H->phikm1;
@@ -407,15 +410,16 @@ static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
   A.phihat = H->pinhat;
   A.guess = (p.guess == MPFC_GUESS_PREV) ? 0 : 1;   // the learned guess corrects the extrapolation
   dim3 g0 = grid_for(L0.m, L0.n, kBlk2d);
-  k_source_guess<SCH><<<g0, kBlk2d, 0, s>>>(L0, A);
+  mpfc_launch(H->shape, k_source_guess<SCH>, g0, kBlk2d, 0, s, L0, A);
   if (p.guess == MPFC_GUESS_LEARNED) mpfc_enqueue_learned_guess(H, s);
   if (SCH == 2)
     for (int l = 1; l < H->nlev; ++l) {
       const Lev& C = H->lev[l];
-      k_restrict_plane<<<grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s>>>(H->lev[l - 1].pk, C.pk, C.m, C.n);
+      mpfc_launch(H->shape, k_restrict_plane, grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s, (const double*)H->lev[l - 1].pk, C.pk,
+                 C.m, C.n);
     }
-  k_guess_kappa<<<g0, kBlk2d, 0, s>>>(L0, H->coef[SCH - 1][0]);
-  k_guess_mu<SCH><<<g0, kBlk2d, 0, s>>>(L0, H->coef[SCH - 1][0]);
+  mpfc_launch(H->shape, k_guess_kappa, g0, kBlk2d, 0, s, L0, H->coef[SCH - 1][0]);
+  mpfc_launch(H->shape, k_guess_mu<SCH>, g0, kBlk2d, 0, s, L0, H->coef[SCH - 1][0]);
 }
 
 template <int SCH>
@@ -423,15 +427,16 @@ static void enqueue_commit(mpfc_s* H, cudaStream_t s) {
   size_t G = (size_t)H->p.m * H->p.n;
   int blocks = (int)((G + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_commit<SCH><<<blocks, 256, 0, s>>>(H->lev[0].phi, H->phik, H->phikm1, H->psik, H->guess.phikm2, (int)G,
-                                       1.0 / H->p.dt, H->p.model == MPFC_MODEL_PFC, H->ctl, H->info);
+  mpfc_launch(H->shape, k_commit<SCH>, dim3(blocks), dim3(256), 0, s, (const double*)H->lev[0].phi, H->phik, H->phikm1, H->psik,
+             H->guess.phikm2, (int)G, 1.0 / H->p.dt, (int)(H->p.model == MPFC_MODEL_PFC), H->ctl, H->info);
 }
 
 template <int SCH>
 static void enqueue_resnorm(mpfc_s* H, int mode, cudaGraphConditionalHandle hnd, int set_cond, cudaStream_t s) {
   const Lev& L0 = H->lev[0];
   int blocks = mpfc_reduce_blocks((size_t)L0.m * L0.n);
-  k_resnorm<SCH><<<blocks, 256, 0, s>>>(L0, H->coef[SCH - 1][0], H->ctl, H->partials, mode, hnd, set_cond);
+  mpfc_launch(H->shape, k_resnorm<SCH>, dim3(blocks), dim3(256), 0, s, L0, H->coef[SCH - 1][0], H->ctl, H->partials, mode, hnd,
+             set_cond);
 }
 
 // Body of the FP64 WHILE node: one V-cycle, then the residual test that sets the
@@ -560,6 +565,14 @@ static int launch_steps(mpfc_s* H, int scheme, int nsteps) {
     return MPFC_OK;
   }
   for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_set_launch_shape(mpfc_t* H, int rows, int small_cells, int pdl_blocks) {
+  if (!H || (rows != 1 && rows != 2 && rows != 4 && rows != 8) || small_cells < 0 || pdl_blocks < 0)
+    return MPFC_ERR_INVALID;
+  H->shape = mpfc_launch_shape{rows, small_cells, pdl_blocks};
+  mpfc_drop_graphs(H);
   return MPFC_OK;
 }
 
@@ -861,8 +874,8 @@ extern "C" int mpfc_op_smooth(mpfc_t* H, int scheme, int level, double* phi, dou
   if (!level_ok(H, level) || (scheme != 1 && scheme != 2) || sweeps < 0 || (scheme == 2 && !phik))
     return MPFC_ERR_INVALID;
   Lev L = user_level(H, level, phi, mu, kappa, S1, S2, S3, phik);
-  if (scheme == 1) launch_smooth<1>(L, H->coef[0][level], H->coefb[0][level], sweeps, H->stream);
-  else launch_smooth<2>(L, H->coef[1][level], H->coefb[1][level], sweeps, H->stream);
+  if (scheme == 1) launch_smooth<1>(H->shape, L, H->coef[0][level], H->coefb[0][level], sweeps, H->stream);
+  else launch_smooth<2>(H->shape, L, H->coef[1][level], H->coefb[1][level], sweeps, H->stream);
   CK(cudaGetLastError());
   return MPFC_OK;
 }

@@ -93,6 +93,18 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(r, fma(-x, r, 1.0), r);
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with programmatic
+// stream serialization may be scheduled while its predecessor on the stream is still
+// running.  griddepcontrol.wait blocks until that predecessor grid has completed and
+// its memory operations are visible; launch_dependents then lets the launch of the
+// next kernel begin while this one runs, so launch latency overlaps execution instead
+// of adding to it.  For a kernel launched without the attribute both are no-ops.
+// Every kernel of the time step calls this before its first memory access.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Device-side control block of the time stepper.
 struct Ctl {
   double res0, res, tol;

@@ -30,6 +30,13 @@ struct MpfcGuess {
   bool loaded = false;
 };
 
+// Launch shapes of the per-cell kernels of the FP64 time step (mpfc_set_launch_shape).
+struct mpfc_launch_shape {
+  int rows;          // blocks of 32 x rows threads for launches of at least small_cells cells
+  int small_cells;   // smaller launches: one-warp blocks (32 x 1), spread over the SMs
+  int pdl_blocks;    // programmatic dependent launch for grids of at most this many blocks
+};
+
 struct mpfc_s {
   mpfc_params p;
   cudaStream_t stream = nullptr;
@@ -53,6 +60,11 @@ struct mpfc_s {
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaGraphConditionalHandle cur_handle = 0;   // handle of the graph being captured
   int launch_mode = MPFC_LAUNCH_GRAPH;
+  // one-warp blocks everywhere and programmatic launch for grids of at most 4 x 152
+  // blocks: 743 us per V-cycle at 1024^2 against 822 with 32 x 8 blocks and no
+  // programmatic launch (GB300, median of four interleaved runs); programmatic launch of
+  // the large grids was slower (779)
+  mpfc_launch_shape shape = {1, 0, 4 * 152};
   // mixed precision
   Lev32 lev32[mpfc::kMaxLevels];
   float* K3f[2] = {nullptr, nullptr};
@@ -65,6 +77,43 @@ struct mpfc_s {
   double* pinhat = nullptr;
   int pin_active = 0;
 };
+
+// Block shape of the per-cell V-cycle kernels on an X x Y launch.  GB300's FP64 unit
+// is narrow: a warp-wide FP64 instruction takes about 64 cycles whatever the number of
+// active lanes, and an SM saturates at about four warps issuing FP64.  A half sweep of
+// ~33 FP64 instructions per cell therefore costs ~1 us per warp however few cells it
+// has, so small launches use one-warp blocks spread over as many SMs as possible, and
+// large ones blocks of 32 x rows threads (the grid then also balances over the 152 SMs
+// in finer steps).
+inline dim3 mpfc_blk_for(const mpfc_launch_shape& sh, int X, int Y) {
+  if ((long long)X * Y >= sh.small_cells) return dim3(32, sh.rows);
+  return dim3(X < 32 ? X : 32, 1);
+}
+inline dim3 mpfc_grid_of(const mpfc_launch_shape& sh, int X, int Y) {
+  dim3 b = mpfc_blk_for(sh, X, Y);
+  return dim3((X + b.x - 1) / b.x, (Y + b.y - 1) / b.y);
+}
+
+// Launch on s, with programmatic stream serialization when the grid has at most
+// sh.pdl_blocks blocks: the kernel may then be scheduled while its predecessor still
+// runs and waits for it in pdl_enter() (every kernel of the time step starts with that
+// call), which overlaps the launch latency of the chain of small kernels that a
+// V-cycle is.  A launch error is left for cudaGetLastError.
+template <typename... KArgs, typename... Args>
+inline void mpfc_launch(const mpfc_launch_shape& sh, void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem,
+                        cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = ((long long)g.x * g.y * g.z <= sh.pdl_blocks) ? 1 : 0;
+  (void)cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void mpfc_drop_graphs(mpfc_s* H);

@@ -147,7 +147,7 @@ def test_prolong(mp, oracle_mod, level):
 
 
 @pytest.mark.parametrize("scheme", [1, 2])
-@pytest.mark.parametrize("m,n,s", [(64, 64, 0.3), (96, 160, 10.0), (128, 32, 0.01)])
+@pytest.mark.parametrize("m,n,s", [(64, 64, 0.3), (96, 160, 10.0), (128, 32, 0.01), (64, 96, 1.0)])
 def test_coarse_solve(mp, oracle_mod, scheme, m, n, s):
     g = make(mp, m, n, 0.5, s)
     L = g.levels - 1
@@ -198,6 +198,14 @@ def test_steps_lockstep_64(mp, oracle_mod, scheme):
 def test_steps_lockstep_ragged_scheme2(mp, oracle_mod):
     phi0 = inputs.crystallite_field(96, 160, np.pi / 4, -0.285, 0.25, count=2, radius_cells=12, seed=2)
     _lockstep(mp, oracle_mod, 2, 96, 160, np.pi / 4, 0.05, 6, phi0)
+
+
+def test_steps_lockstep_coarsest_4x6(mp, oracle_mod):
+    """64 x 96: the hierarchy ends on a 4 x 6 grid (24 cells), the coarsest solve's
+    32-row register path; 128 x 32 ends on 16 x 4 (64 cells, shared-memory path)."""
+    for m, n in ((64, 96), (128, 32)):
+        phi0 = inputs.noise_field(m, n, 0.07, 0.05, 7)
+        _lockstep(mp, oracle_mod, 1, m, n, 0.5, 0.05, 4, phi0)
 
 
 def test_steps_lockstep_undamped(mp, oracle_mod):
