@@ -119,6 +119,9 @@ Coef mpfc_coef(const mpfc_params* p, int scheme, double h, int nb) {
   k.Q0 = k.gam + k.b * k.b3;
   k.a3 = 3.0 * k.a;
   k.omw = 1.0 - k.omega;
+  k.D0w = k.D0 / k.omega;
+  k.aw = k.a / k.omega;
+  k.a3w = k.a3 / k.omega;
   k.relax = (k.omega != 1.0);
   k.pad = 0;
   return k;
@@ -250,6 +253,21 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
       K3[(size_t)r * G + c2] = (r == c2 ? 1.0 : 0.0) - k.c * k.theta * L3[(size_t)r * G + c2];
 }
 
+// Default launch shapes, from interleaved timings on GB300 (V-cycle at 1024^2):
+//   FP64: one-warp blocks everywhere and programmatic launch for grids of at most 4 x 152
+//     blocks, 743 us per V-cycle, against 822 with 32 x 8 blocks and no programmatic
+//     launch; programmatic launch of the large grids too was slower (779);
+//   FP32 inner cycles (memory-latency bound, they want occupancy): 32 x 4 blocks and the
+//     same programmatic launch, 472 us per outer iteration against 479 (32 x 8, none)
+//     and 725 with one-warp blocks;
+//   the FP64 levels of at most 16 x 16 cells as one cluster launch: 2 to 9 us less per
+//     V-cycle (1024^2 to 64^2 grids); larger tails were slower, their phases being
+//     bound by the FP64 instruction latency of the cell updates, not by launches.
+mpfc_launch_shape mpfc_default_launch_shape(int precision) {
+  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * 152, 0, 8};
+  return mpfc_launch_shape{1, 0, 4 * 152, 256, mpfc_tail_max_ctas()};
+}
+
 extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes, void* cuda_stream, mpfc_t** out) {
   if (!out) return MPFC_ERR_INVALID;
   *out = nullptr;
@@ -258,6 +276,7 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
   if (!d_workspace || bytes < need || ((uintptr_t)d_workspace & 255)) return MPFC_ERR_WORKSPACE;
   mpfc_s* H = new mpfc_s();
   H->p = *p;
+  H->shape = mpfc_default_launch_shape(p->precision);
   H->stream = (cudaStream_t)cuda_stream;
   H->ws = (char*)d_workspace;
   H->ws_bytes = bytes;
@@ -367,26 +386,100 @@ static size_t coarse_smem(const Lev& C) {
   return sizeof(double) * 7 * (size_t)G + sizeof(float) * ((size_t)G * (G + 1) + (size_t)G);
 }
 
+// Largest tail cluster this GPU runs: 16 CTAs where a non-portable cluster of that size
+// can be resident (one query, then cached), else the portable 8.
+int mpfc_tail_max_ctas() {
+  static int cached = 0;
+  if (cached) return cached;
+  int best = 8;
+  if (cudaFuncSetAttribute(k_tail<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(k_tail<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = coarse_smem(Lev{8, 8});
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 16;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tail<1>, &cfg) == cudaSuccess && n > 0) best = 16;
+  }
+  (void)cudaGetLastError();
+  cached = best;
+  return cached;
+}
+
 template <int SCH>
 static void launch_coarse(mpfc_s* H, const Lev& C, const Coef& k, cudaStream_t s) {
   mpfc_launch(H->shape, k_coarse_solve<SCH>, dim3(1), dim3(32), coarse_smem(C), s, C, k, (const float*)H->K3[SCH - 1]);
+}
+
+// First level run by the tail kernel: the finest level of at most shape.tail_cells
+// cells, leaving at least one level above the coarsest and at most kMaxTail levels in
+// the tail; nlev when no tail is used.
+static int tail_first_level(const mpfc_s* H) {
+  const int L = H->nlev;
+  if (H->shape.tail_cells <= 0 || L < 2) return L;
+  int lt = L - 1;
+  while (lt > 0 && (long long)H->lev[lt - 1].m * H->lev[lt - 1].n <= H->shape.tail_cells) --lt;
+  if (lt > L - 2) return L;
+  if (L - lt > kMaxTail) lt = L - kMaxTail;
+  return lt;
+}
+
+// Levels lt .. nlev-1 as one cluster launch (k_tail).
+template <int SCH>
+static void launch_tail(mpfc_s* H, int lt, cudaStream_t s) {
+  TailArgs A;
+  A.nlev = H->nlev - lt;
+  A.nu1 = H->p.nu1;
+  A.nu2 = H->p.nu2;
+  A.K3f = H->K3[SCH - 1];
+  for (int i = 0; i < A.nlev; ++i) {
+    A.lv[i].L = H->lev[lt + i];
+    A.lv[i].k = H->coef[SCH - 1][lt + i];
+    A.lv[i].kb = H->coefb[SCH - 1][lt + i];
+  }
+  const int nc = H->shape.tail_ctas;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = coarse_smem(H->lev[H->nlev - 1]);
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = nc;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = (nc <= H->shape.pdl_blocks) ? 2 : 1;
+  (void)cudaLaunchKernelEx(&cfg, k_tail<SCH>, A);
 }
 
 template <int SCH>
 static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
   const mpfc_params& p = H->p;
   const mpfc_launch_shape& sh = H->shape;
-  int L = H->nlev;
-  for (int l = 0; l < L - 1; ++l) {
+  const int L = H->nlev;
+  const int lt = tail_first_level(H);
+  const int down = lt < L ? lt : L - 1;   // levels smoothed and restricted by per-level launches
+  for (int l = 0; l < down; ++l) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
     launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu1, s);
     mpfc_launch(sh, k_resid_restrict<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C,
-               H->coef[SCH - 1][l], 1);
+                H->coef[SCH - 1][l], 1);
     mpfc_launch(sh, k_tau<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, C, H->coef[SCH - 1][l + 1]);
   }
-  launch_coarse<SCH>(H, H->lev[L - 1], H->coef[SCH - 1][L - 1], s);
-  for (int l = L - 2; l >= 0; --l) {
+  if (lt < L) launch_tail<SCH>(H, lt, s);
+  else launch_coarse<SCH>(H, H->lev[L - 1], H->coef[SCH - 1][L - 1], s);
+  for (int l = down - 1; l >= 0; --l) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
     ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n, C.nyn};
@@ -568,10 +661,13 @@ static int launch_steps(mpfc_s* H, int scheme, int nsteps) {
   return MPFC_OK;
 }
 
-extern "C" int mpfc_set_launch_shape(mpfc_t* H, int rows, int small_cells, int pdl_blocks) {
-  if (!H || (rows != 1 && rows != 2 && rows != 4 && rows != 8) || small_cells < 0 || pdl_blocks < 0)
+extern "C" int mpfc_set_launch_shape(mpfc_t* H, int rows, int small_cells, int pdl_blocks, int tail_cells,
+                                     int tail_ctas) {
+  if (!H || (rows != 1 && rows != 2 && rows != 4 && rows != 8) || small_cells < 0 || pdl_blocks < 0 ||
+      tail_cells < 0 || (tail_ctas != 8 && tail_ctas != 16))
     return MPFC_ERR_INVALID;
-  H->shape = mpfc_launch_shape{rows, small_cells, pdl_blocks};
+  if (tail_ctas > mpfc_tail_max_ctas()) return MPFC_ERR_INVALID;
+  H->shape = mpfc_launch_shape{rows, small_cells, pdl_blocks, tail_cells, tail_ctas};
   mpfc_drop_graphs(H);
   return MPFC_OK;
 }

@@ -40,6 +40,10 @@ struct Coef {
   double Q0;    // gam + b b3            (Cramer numerator of mu without the cubic)
   double a3;    // 3 a                   (scheme 1: det = D0 + 3 a p^2)
   double omw;   // 1 - omega
+  // the determinant divided by omega, so that its reciprocal is omega / det at once:
+  double D0w;   // D0 / omega
+  double aw;    // a / omega
+  double a3w;   // 3 a / omega
   int relax;    // omega != 1
   int pad;
 };
@@ -103,6 +107,23 @@ __device__ __forceinline__ double rcp_nr(double x) {
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Loads of the per-cell stencil functions.  NC: the read-only (non-coherent) path,
+// valid only for data that no thread writes during the kernel; otherwise an L2 load
+// (ld.global.cg), for kernels that read what other CTAs of the same kernel wrote
+// before a release/acquire barrier.
+template <bool NC>
+__device__ __forceinline__ double ldv(const double* p) {
+  if (NC) return __ldg(p);
+  return __ldcg(p);
+}
+// A cell's own value, which the same thread may write later in the kernel: a plain
+// load, or an L2 load in the cross-CTA case.
+template <bool NC>
+__device__ __forceinline__ double ldown(const double* p) {
+  if (NC) return *p;
+  return __ldcg(p);
 }
 
 // Device-side control block of the time stepper.

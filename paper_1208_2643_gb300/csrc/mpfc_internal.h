@@ -35,6 +35,8 @@ struct mpfc_launch_shape {
   int rows;          // blocks of 32 x rows threads for launches of at least small_cells cells
   int small_cells;   // smaller launches: one-warp blocks (32 x 1), spread over the SMs
   int pdl_blocks;    // programmatic dependent launch for grids of at most this many blocks
+  int tail_cells;    // levels of at most this many cells run in one cluster launch (0: none)
+  int tail_ctas;     // CTAs of that cluster (8, or 16 where the GPU allows it)
 };
 
 struct mpfc_s {
@@ -60,11 +62,8 @@ struct mpfc_s {
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaGraphConditionalHandle cur_handle = 0;   // handle of the graph being captured
   int launch_mode = MPFC_LAUNCH_GRAPH;
-  // one-warp blocks everywhere and programmatic launch for grids of at most 4 x 152
-  // blocks: 743 us per V-cycle at 1024^2 against 822 with 32 x 8 blocks and no
-  // programmatic launch (GB300, median of four interleaved runs); programmatic launch of
-  // the large grids was slower (779)
-  mpfc_launch_shape shape = {1, 0, 4 * 152};
+  // set by mpfc_create from the precision (mpfc_default_launch_shape)
+  mpfc_launch_shape shape = {1, 0, 4 * 152, 0, 8};
   // mixed precision
   Lev32 lev32[mpfc::kMaxLevels];
   float* K3f[2] = {nullptr, nullptr};
@@ -121,6 +120,8 @@ int mpfc_num_levels(int m, int n, int coarsest);
 mpfc::Coef mpfc_coef(const mpfc_params* p, int scheme, double h, int nb);
 void mpfc_build_K3(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<double>& K3);
 int mpfc_reduce_blocks(size_t G);
+int mpfc_tail_max_ctas();
+mpfc_launch_shape mpfc_default_launch_shape(int precision);
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd,
                        void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme);
 void mpfc_enqueue_prologue(mpfc_s* H, int scheme, cudaStream_t s);

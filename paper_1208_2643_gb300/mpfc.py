@@ -99,7 +99,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_probe_fp64_fma.argtypes = [_VP, _VP, P(ctypes.c_double)]
     lib.mpfc_probe_rcp.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.mpfc_set_launch_mode.argtypes = [_VP, ctypes.c_int]
-    lib.mpfc_set_launch_shape.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
     lib.mpfc_op_learned_guess.argtypes = [_VP]
     lib.mpfc_batch_workspace_bytes.argtypes = [ctypes.c_int, P(mpfc_params)]
     lib.mpfc_batch_workspace_bytes.restype = ctypes.c_size_t
@@ -258,10 +258,12 @@ class Solver:
     def set_launch_mode(self, mode: int):
         _check(self.lib.mpfc_set_launch_mode(self.h, mode), "mpfc_set_launch_mode")
 
-    def set_launch_shape(self, rows: int, small_cells: int, pdl_blocks: int):
+    def set_launch_shape(self, rows: int, small_cells: int, pdl_blocks: int, tail_cells: int = 0, tail_ctas: int = 8):
         """Block rows of large launches, the cell count below which launches use one-warp
-        blocks, and the largest grid launched with programmatic dependent launch."""
-        _check(self.lib.mpfc_set_launch_shape(self.h, rows, small_cells, pdl_blocks), "mpfc_set_launch_shape")
+        blocks, the largest grid launched with programmatic dependent launch, and the
+        levels (at most tail_cells cells) run as one cluster launch of tail_ctas CTAs."""
+        _check(self.lib.mpfc_set_launch_shape(self.h, rows, small_cells, pdl_blocks, tail_cells, tail_ctas),
+               "mpfc_set_launch_shape")
 
     def step_async(self, scheme: int, nsteps: int = 1):
         """Enqueues steps without synchronising (records via records())."""

@@ -384,3 +384,42 @@ def test_integer_pipe_conversions_match_ieee(mp):
     nz = x != 0
     assert np.all(np.abs(t[nz] - x[nz]) <= np.abs(x[nz]) * 2.0 ** -23)
     assert np.all(np.abs(t[nz]) <= np.abs(x[nz]))
+
+
+@pytest.mark.parametrize("ctas", [8, 16])
+@pytest.mark.parametrize("case", ["periodic1", "periodic2", "ragged2", "neumann2", "pinned2"])
+def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
+    """The coarse levels run as one thread-block cluster launch (barriers between the
+    phases) give exactly the bits of the per-level launches, over several steps."""
+    probe = mp.Solver(mp.default_params(m=64, n=64))
+    try:
+        probe.set_launch_shape(1, 0, 4 * 152, 64 * 64, ctas)
+    except mp.MPFCError:
+        pytest.skip(f"this GPU holds no {ctas}-CTA cluster")
+    finally:
+        probe.close()
+    scheme = int(case[-1])
+    m, n = (96, 160) if case.startswith("ragged") else (128, 128)
+    kw = {}
+    if case.startswith("neumann"):
+        kw["bc"] = mp.MPFC_BC_NEUMANN_Y
+    if case.startswith("pinned"):
+        kw["pinning"] = 1
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 3)
+    runs = []
+    for tail_cells in (0, 32 * 32, 64 * 64):
+        g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=0.05, **kw))
+        if case.startswith("pinned"):
+            W = np.zeros((n, m))
+            W[:10] = 2.0
+            W[-10:] = 2.0
+            g.set_pinning(W, inputs.noise_field(m, n, 0.1, 0.05, 4))
+        g.set_launch_shape(1, 0, 4 * 152, tail_cells, ctas)
+        g.set_state(phi0)
+        infos = g.step(scheme, 3)
+        runs.append(([i["cycles"] for i in infos], g.get_state()))
+        g.close()
+    for cyc, st in runs[1:]:
+        assert cyc == runs[0][0]
+        for a, b in zip(st, runs[0][1]):
+            assert np.array_equal(a, b)
