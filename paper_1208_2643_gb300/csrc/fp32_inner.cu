@@ -117,30 +117,30 @@ __global__ void k_restrict_q(const float* __restrict__ qf, float* __restrict__ q
   qc[(size_t)J * mc + I] = 0.25f * ((qf[a] + qf[a + 1]) + (qf[b] + qf[b + 1]));
 }
 
-// ---------------------------------------------------------------------------
-// FP32 red-black half sweep of the correction equation (App. B cell system with
-// the frozen linearisation q = gam + g'(phi)).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_smooth32(Lev32 L, Coef32 k, int color) {
-  pdl_enter();
-  int x = blockIdx.x * blockDim.x + threadIdx.x;
-  int j = blockIdx.y * blockDim.y + threadIdx.y;
+// Loads of the FP32 cell functions: the read-only path for global planes that the
+// kernel does not write, plain loads otherwise (also for planes in shared memory).
+template <bool NC>
+__device__ __forceinline__ float ld32(const float* p) {
+  if (NC) return __ldg(p);
+  return *p;
+}
+
+template <bool NC>
+__device__ __forceinline__ void smooth32_cell(const Lev32& L, const Coef32& k, int i, int j) {
   int m = L.m;
-  if (x >= (m >> 1) || j >= L.n) return;
-  int i = 2 * x + ((j + color) & 1);
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
   float* __restrict__ ep = L.ephi;
   float* __restrict__ em = L.emu;
   float* __restrict__ ek = L.eka;
-  float smu = (__ldg(em + w) + __ldg(em + e)) + (__ldg(em + s) + __ldg(em + nn));
-  float ska = (__ldg(ek + w) + __ldg(ek + e)) + (__ldg(ek + s) + __ldg(ek + nn));
-  float sph = (__ldg(ep + w) + __ldg(ep + e)) + (__ldg(ep + s) + __ldg(ep + nn));
-  float q = __ldg(L.q + c);
-  float R1 = fmaf(k.cmu, smu, __ldg(L.r1 + c));
-  float R2 = fmaf(k.ih2, ska, __ldg(L.r2 + c));
-  float R3 = fmaf(k.th2, sph, __ldg(L.r3 + c));
+  float smu = (ld32<NC>(em + w) + ld32<NC>(em + e)) + (ld32<NC>(em + s) + ld32<NC>(em + nn));
+  float ska = (ld32<NC>(ek + w) + ld32<NC>(ek + e)) + (ld32<NC>(ek + s) + ld32<NC>(ek + nn));
+  float sph = (ld32<NC>(ep + w) + ld32<NC>(ep + e)) + (ld32<NC>(ep + s) + ld32<NC>(ep + nn));
+  float q = ld32<NC>(L.q + c);
+  float R1 = fmaf(k.cmu, smu, ld32<NC>(L.r1 + c));
+  float R2 = fmaf(k.ih2, ska, ld32<NC>(L.r2 + c));
+  float R3 = fmaf(k.th2, sph, ld32<NC>(L.r3 + c));
   float rdet = __frcp_rn(fmaf(k.a, q, k.D0));
   float nphi = fmaf(k.a, fmaf(k.b, R3, -R2), R1);
   float nmu = fmaf(k.Q0 + q, R1, fmaf(-k.b, R3, R2));
@@ -159,7 +159,20 @@ __global__ void __launch_bounds__(256) k_smooth32(Lev32 L, Coef32 k, int color) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 red-black half sweep of the correction equation (App. B cell system with
+// the frozen linearisation q = gam + g'(phi)).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_smooth32(Lev32 L, Coef32 k, int color) {
+  pdl_enter();
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= (L.m >> 1) || j >= L.n) return;
+  smooth32_cell<true>(L, k, 2 * x + ((j + color) & 1), j);
+}
+
 // defect of the correction equation at one cell: rho = r - J e
+template <bool NC>
 __device__ __forceinline__ void defect32(const Lev32& L, const Coef32& k, int i, int j, float& d1, float& d2,
                                          float& d3) {
   int m = L.m;
@@ -169,28 +182,25 @@ __device__ __forceinline__ void defect32(const Lev32& L, const Coef32& k, int i,
   const float* ep = L.ephi;
   const float* em = L.emu;
   const float* ek = L.eka;
-  float p = __ldg(ep + c), u = __ldg(em + c), v = __ldg(ek + c);
-  float smu = (__ldg(em + w) + __ldg(em + e)) + (__ldg(em + s) + __ldg(em + nn));
-  float ska = (__ldg(ek + w) + __ldg(ek + e)) + (__ldg(ek + s) + __ldg(ek + nn));
-  float sph = (__ldg(ep + w) + __ldg(ep + e)) + (__ldg(ep + s) + __ldg(ep + nn));
-  d1 = fmaf(k.cmu, fmaf(-4.f, u, smu), __ldg(L.r1 + c) - p);
-  d2 = fmaf(k.ih2, fmaf(-4.f, v, ska), fmaf(__ldg(L.q + c), p, __ldg(L.r2 + c) - u));
-  d3 = fmaf(k.th2, fmaf(-4.f, p, sph), __ldg(L.r3 + c) - v);
+  float p = ld32<NC>(ep + c), u = ld32<NC>(em + c), v = ld32<NC>(ek + c);
+  float smu = (ld32<NC>(em + w) + ld32<NC>(em + e)) + (ld32<NC>(em + s) + ld32<NC>(em + nn));
+  float ska = (ld32<NC>(ek + w) + ld32<NC>(ek + e)) + (ld32<NC>(ek + s) + ld32<NC>(ek + nn));
+  float sph = (ld32<NC>(ep + w) + ld32<NC>(ep + e)) + (ld32<NC>(ep + s) + ld32<NC>(ep + nn));
+  d1 = fmaf(k.cmu, fmaf(-4.f, u, smu), ld32<NC>(L.r1 + c) - p);
+  d2 = fmaf(k.ih2, fmaf(-4.f, v, ska), fmaf(ld32<NC>(L.q + c), p, ld32<NC>(L.r2 + c) - u));
+  d3 = fmaf(k.th2, fmaf(-4.f, p, sph), ld32<NC>(L.r3 + c) - v);
 }
 
 // coarse source = R(r - J e), coarse correction starts at zero
-__global__ void k_restrict_defect32(Lev32 F, Lev32 C, Coef32 kf) {
-  pdl_enter();
-  int I = blockIdx.x * blockDim.x + threadIdx.x;
-  int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I >= C.m || J >= C.n) return;
+template <bool NC>
+__device__ __forceinline__ void restrict_defect32_cell(const Lev32& F, const Lev32& C, const Coef32& kf, int I, int J) {
   float s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
   for (int dj = 0; dj < 2; ++dj)
 #pragma unroll
     for (int di = 0; di < 2; ++di) {
       float a, b, c;
-      defect32(F, kf, 2 * I + di, 2 * J + dj, a, b, c);
+      defect32<NC>(F, kf, 2 * I + di, 2 * J + dj, a, b, c);
       s1 += a;
       s2 += b;
       s3 += c;
@@ -202,6 +212,14 @@ __global__ void k_restrict_defect32(Lev32 F, Lev32 C, Coef32 kf) {
   C.ephi[cid] = 0.f;
   C.emu[cid] = 0.f;
   C.eka[cid] = 0.f;
+}
+
+__global__ void k_restrict_defect32(Lev32 F, Lev32 C, Coef32 kf) {
+  pdl_enter();
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= C.m || J >= C.n) return;
+  restrict_defect32_cell<true>(F, C, kf, I, J);
 }
 
 // e_f += P e_c (bilinear, shared-memory tile of the coarse correction)
@@ -250,9 +268,9 @@ __device__ __forceinline__ float nbsum32(const float* f, int m, int n, int t) {
          (f[wrapm(j - 1, n) * m + i] + f[wrapm(j + 1, n) * m + i]);
 }
 
-__global__ void k_coarse32(Lev32 C, Coef32 k, const float* __restrict__ K3f) {
-  pdl_enter();
-  extern __shared__ float smf[];
+// The whole block; smf holds G (G + 1) + 4 G floats.  C's planes may be in global or
+// shared memory (plain loads).
+__device__ void coarse32_block(const Lev32& C, const Coef32& k, const float* __restrict__ K3f, float* smf) {
   const int m = C.m, n = C.n, G = m * n, W = G + 1;
   float* A = smf;
   float* t1 = A + G * W;
@@ -267,50 +285,74 @@ __global__ void k_coarse32(Lev32 C, Coef32 k, const float* __restrict__ K3f) {
   for (int t = tid; t < G; t += nt) t2[t] = C.r2[t] + t1[t];
   __syncthreads();
   for (int t = tid; t < G; t += nt) A[t * W + G] = C.r1[t] + k.cmu * (nbsum32(t2, m, n, t) - 4.f * t2[t]);
-  for (int idx = tid; idx < G * G; idx += nt) {
-    int r = idx / G, col = idx % G;
+  auto entry = [&](int r, int col) {
     int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
     int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
               (ci == ri && cj == wrapm(rj - 1, n)) + (ci == ri && cj == wrapm(rj + 1, n));
     float Lrc = k.ih2 * ((float)cnt - (r == col ? 4.f : 0.f));
-    A[r * W + col] = K3f[idx] - k.c * Lrc * C.q[col];
-  }
-  __syncthreads();
-  for (int col = 0; col < G; ++col) {
-    if (tid == 0) {
-      int piv = col;
-      float best = fabsf(A[col * W + col]);
-      for (int r = col + 1; r < G; ++r) {
-        float v = fabsf(A[r * W + col]);
-        if (v > best) { best = v; piv = r; }
+    return K3f[r * G + col] - k.c * Lrc * C.q[col];
+  };
+  if (G <= 31) {
+    // one warp: a Jacobian column per lane in registers, Gauss-Jordan with implicit
+    // pivoting (gauss_jordan_cols); the right-hand side in lane G
+    __syncthreads();
+    auto column = [&](auto& a) {
+      constexpr int R = sizeof(a) / sizeof(a[0]);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        a[r] = (r < G) ? (tid < G ? entry(r, tid) : (tid == G ? A[r * W + G] : 0.f)) : 0.f;
+      __syncwarp();
+      gauss_jordan_cols<R>(a, G, x, t2, reinterpret_cast<int*>(d));
+    };
+    if (tid < 32) {
+      if (G <= 16) {
+        float a[16];
+        column(a);
+      } else {
+        float a[32];
+        column(a);
       }
-      s_piv = piv;
     }
     __syncthreads();
-    int piv = s_piv;
-    if (piv != col)
-      for (int c2 = col + tid; c2 <= G; c2 += nt) {
-        float t = A[col * W + c2];
-        A[col * W + c2] = A[piv * W + c2];
-        A[piv * W + c2] = t;
+  } else {
+    for (int idx = tid; idx < G * G; idx += nt) A[(idx / G) * W + idx % G] = entry(idx / G, idx % G);
+    __syncthreads();
+    for (int col = 0; col < G; ++col) {
+      if (tid == 0) {
+        int piv = col;
+        float best = fabsf(A[col * W + col]);
+        for (int r = col + 1; r < G; ++r) {
+          float v = fabsf(A[r * W + col]);
+          if (v > best) { best = v; piv = r; }
+        }
+        s_piv = piv;
+      }
+      __syncthreads();
+      int piv = s_piv;
+      if (piv != col)
+        for (int c2 = col + tid; c2 <= G; c2 += nt) {
+          float t = A[col * W + c2];
+          A[col * W + c2] = A[piv * W + c2];
+          A[piv * W + c2] = t;
+        }
+      __syncthreads();
+      for (int r = col + 1 + tid; r < G; r += nt) d[r] = A[r * W + col] / A[col * W + col];
+      __syncthreads();
+      int rows = G - col - 1, cols = G - col;
+      for (int idx = tid; idx < rows * cols; idx += nt) {
+        int r = col + 1 + idx / cols, c2 = col + 1 + idx % cols;
+        A[r * W + c2] -= d[r] * A[col * W + c2];
+      }
+      __syncthreads();
+    }
+    if (tid == 0)
+      for (int r = G - 1; r >= 0; --r) {
+        float acc = A[r * W + G];
+        for (int c2 = r + 1; c2 < G; ++c2) acc -= A[r * W + c2] * x[c2];
+        x[r] = acc / A[r * W + r];
       }
     __syncthreads();
-    for (int r = col + 1 + tid; r < G; r += nt) d[r] = A[r * W + col] / A[col * W + col];
-    __syncthreads();
-    int rows = G - col - 1, cols = G - col;
-    for (int idx = tid; idx < rows * cols; idx += nt) {
-      int r = col + 1 + idx / cols, c2 = col + 1 + idx % cols;
-      A[r * W + c2] -= d[r] * A[col * W + c2];
-    }
-    __syncthreads();
   }
-  if (tid == 0)
-    for (int r = G - 1; r >= 0; --r) {
-      float acc = A[r * W + G];
-      for (int c2 = r + 1; c2 < G; ++c2) acc -= A[r * W + c2] * x[c2];
-      x[r] = acc / A[r * W + r];
-    }
-  __syncthreads();
   for (int t = tid; t < G; t += nt) t1[t] = C.r3[t] + k.th2 * (nbsum32(x, m, n, t) - 4.f * x[t]);   // e_kappa
   __syncthreads();
   for (int t = tid; t < G; t += nt) {
@@ -318,6 +360,12 @@ __global__ void k_coarse32(Lev32 C, Coef32 k, const float* __restrict__ K3f) {
     C.ephi[t] = x[t];
     C.eka[t] = t1[t];
   }
+}
+
+__global__ void k_coarse32(Lev32 C, Coef32 k, const float* __restrict__ K3f) {
+  pdl_enter();
+  extern __shared__ float smf[];
+  coarse32_block(C, k, K3f, smf);
 }
 
 size_t coarse32_smem(const Lev32& C) {
@@ -338,22 +386,184 @@ void sweeps32(const mpfc_launch_shape& sh, const Lev32& F, const Coef32& kf, int
 
 int inner_cycles_of(const mpfc_s* H) { return H->p.inner_cycles > 0 ? H->p.inner_cycles : 2; }
 
+// ---------------------------------------------------------------------------
+// The coarse end of an inner V-cycle in one CTA with every level in shared memory:
+// the sweeps, defect restrictions, coarsest solve and prolongations of the levels
+// lt .. L-1, in the order of the per-level launches and with the same cell functions
+// (so the same bits), separated by __syncthreads instead of kernel boundaries.  The
+// FP32 work of a small level is far below a launch's cost.  Level lt's correction is
+// read at the start and written back at the end; its defect source and every level's
+// q are read from the global planes.
+// ---------------------------------------------------------------------------
+constexpr int kMaxTail32 = 8;
+constexpr int kTail32Threads = 1024;
+constexpr size_t kTail32MaxSmem = 200 * 1024;   // dynamic shared memory, below the 227 KB opt-in limit
+
+struct Tail32Args {
+  int nlev, nu1, nu2;
+  const float* K3f;
+  Lev32 g[kMaxTail32];    // the levels' global planes
+  Coef32 k[kMaxTail32];
+};
+
+// e_f += P e_c at one fine cell, with the tile version's order of operations.
+__device__ __forceinline__ void prolong32_fine(const float* ec, float* ef, int mc, int nc, int fi, int fj) {
+  const int I = fi >> 1, J = fj >> 1;
+  const int Ix = wrapm(I + ((fi & 1) ? 1 : -1), mc), Jy = wrapm(J + ((fj & 1) ? 1 : -1), nc);
+  const float e00 = ec[J * mc + I], ex = ec[J * mc + Ix], ey = ec[Jy * mc + I], exy = ec[Jy * mc + Ix];
+  const float w9 = 9.f / 16.f, w3 = 3.f / 16.f, w1 = 1.f / 16.f;
+  const int id = fj * (2 * mc) + fi;
+  ef[id] += fmaf(w3, ex + ey, fmaf(w1, exy, w9 * e00));
+}
+
+size_t tail32_smem(const Lev32* levs, int nlev) {
+  size_t cells = 0;
+  for (int l = 0; l < nlev; ++l) cells += (size_t)levs[l].m * levs[l].n;
+  return 7 * cells * sizeof(float) + coarse32_smem(levs[nlev - 1]);
+}
+
+__global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant__ Tail32Args A) {
+  extern __shared__ float ts[];
+  __shared__ Lev32 sl[kMaxTail32];
+  pdl_enter();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    float* p = ts;
+    for (int l = 0; l < A.nlev; ++l) {
+      const int G = A.g[l].m * A.g[l].n;
+      Lev32 v = A.g[l];
+      v.ephi = p;
+      v.emu = p + G;
+      v.eka = p + 2 * G;
+      v.r1 = p + 3 * G;
+      v.r2 = p + 4 * G;
+      v.r3 = p + 5 * G;
+      v.q = p + 6 * G;
+      v.b1 = v.b2 = v.b3 = nullptr;
+      sl[l] = v;
+      p += 7 * G;
+    }
+  }
+  __syncthreads();
+  float* scratch = ts;
+  for (int l = 0; l < A.nlev; ++l) scratch += 7 * A.g[l].m * A.g[l].n;
+  {
+    const Lev32& T = sl[0];
+    const Lev32& G0 = A.g[0];
+    const int G = T.m * T.n;
+    for (int t = tid; t < G; t += nt) {
+      T.ephi[t] = G0.ephi[t];
+      T.emu[t] = G0.emu[t];
+      T.eka[t] = G0.eka[t];
+      T.r1[t] = G0.r1[t];
+      T.r2[t] = G0.r2[t];
+      T.r3[t] = G0.r3[t];
+    }
+    for (int l = 0; l < A.nlev; ++l) {
+      const int Gl = A.g[l].m * A.g[l].n;
+      for (int t = tid; t < Gl; t += nt) sl[l].q[t] = A.g[l].q[t];
+    }
+  }
+  __syncthreads();
+  for (int l = 0; l < A.nlev - 1; ++l) {
+    const Lev32& F = sl[l];
+    const Lev32& C = sl[l + 1];
+    const int half = F.m >> 1, hc = half * F.n;
+    for (int sw = 0; sw < A.nu1; ++sw)
+      for (int color = 0; color < 2; ++color) {
+        for (int t = tid; t < hc; t += nt) {
+          const int j = t / half, x = t - j * half;
+          smooth32_cell<false>(F, A.k[l], 2 * x + ((j + color) & 1), j);
+        }
+        __syncthreads();
+      }
+    const int cc = C.m * C.n;
+    for (int t = tid; t < cc; t += nt) restrict_defect32_cell<false>(F, C, A.k[l], t % C.m, t / C.m);
+    __syncthreads();
+  }
+  coarse32_block(sl[A.nlev - 1], A.k[A.nlev - 1], A.K3f, scratch);
+  __syncthreads();
+  for (int l = A.nlev - 2; l >= 0; --l) {
+    const Lev32& F = sl[l];
+    const Lev32& C = sl[l + 1];
+    const int fc = F.m * F.n;
+    for (int t = tid; t < fc; t += nt) {
+      const int fi = t % F.m, fj = t / F.m;
+      prolong32_fine(C.ephi, F.ephi, C.m, C.n, fi, fj);
+      prolong32_fine(C.emu, F.emu, C.m, C.n, fi, fj);
+      prolong32_fine(C.eka, F.eka, C.m, C.n, fi, fj);
+    }
+    __syncthreads();
+    const int half = F.m >> 1, hc = half * F.n;
+    for (int sw = 0; sw < A.nu2; ++sw)
+      for (int color = 0; color < 2; ++color) {
+        for (int t = tid; t < hc; t += nt) {
+          const int j = t / half, x = t - j * half;
+          smooth32_cell<false>(F, A.k[l], 2 * x + ((j + color) & 1), j);
+        }
+        __syncthreads();
+      }
+  }
+  {
+    const Lev32& T = sl[0];
+    const Lev32& G0 = A.g[0];
+    const int G = T.m * T.n;
+    for (int t = tid; t < G; t += nt) {
+      G0.ephi[t] = T.ephi[t];
+      G0.emu[t] = T.emu[t];
+      G0.eka[t] = T.eka[t];
+    }
+  }
+}
+
+// First level of the shared-memory tail: the finest level of at most shape.tail_cells
+// cells whose levels down to the coarsest fit in shared memory, leaving at least one
+// level above the coarsest; nlev when no tail is used.
+int tail32_first_level(const mpfc_s* H) {
+  const int L = H->nlev;
+  if (H->shape.tail_cells <= 0 || L < 2) return L;
+  int lt = L - 1;
+  while (lt > 0 && (long long)H->lev32[lt - 1].m * H->lev32[lt - 1].n <= H->shape.tail_cells &&
+         L - (lt - 1) <= kMaxTail32 && tail32_smem(H->lev32 + lt - 1, L - lt + 1) <= kTail32MaxSmem)
+    --lt;
+  return lt > L - 2 ? L : lt;
+}
+
+void launch_tail32(mpfc_s* H, int scheme, int lt, cudaStream_t s) {
+  Tail32Args A;
+  A.nlev = H->nlev - lt;
+  A.nu1 = H->p.nu1;
+  A.nu2 = H->p.nu2;
+  A.K3f = H->K3f[scheme - 1];
+  for (int i = 0; i < A.nlev; ++i) {
+    A.g[i] = H->lev32[lt + i];
+    A.k[i] = coef32_of(H->coef[scheme - 1][lt + i]);
+  }
+  mpfc_launch(H->shape, k_tail32, dim3(1), dim3(kTail32Threads), tail32_smem(H->lev32 + lt, A.nlev), s, A);
+}
+
 // One inner correction-scheme V-cycle.
 void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
   const mpfc_params& p = H->p;
   const mpfc_launch_shape& sh = H->shape;
-  int L = H->nlev;
-  for (int l = 0; l < L - 1; ++l) {
+  const int L = H->nlev;
+  const int lt = tail32_first_level(H);
+  const int down = lt < L ? lt : L - 1;   // levels swept and restricted by per-level launches
+  for (int l = 0; l < down; ++l) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
     sweeps32(sh, F, kf, p.nu1, s);
     mpfc_launch(sh, k_restrict_defect32, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C, kf);
   }
-  const Lev32& Cc = H->lev32[L - 1];
-  mpfc_launch(sh, k_coarse32, dim3(1), dim3(256), coarse32_smem(Cc), s, Cc, coef32_of(H->coef[scheme - 1][L - 1]),
-              (const float*)H->K3f[scheme - 1]);
-  for (int l = L - 2; l >= 0; --l) {
+  if (lt < L) {
+    launch_tail32(H, scheme, lt, s);
+  } else {
+    const Lev32& Cc = H->lev32[L - 1];
+    mpfc_launch(sh, k_coarse32, dim3(1), dim3(256), coarse32_smem(Cc), s, Cc, coef32_of(H->coef[scheme - 1][L - 1]),
+                (const float*)H->K3f[scheme - 1]);
+  }
+  for (int l = down - 1; l >= 0; --l) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
@@ -427,6 +637,11 @@ int mpfc_fp32_init(mpfc_s* H) {
   if (H->p.precision != MPFC_FP32_INNER) return MPFC_OK;
   H->K3f[0] = H->K3[0];
   H->K3f[1] = H->K3[1];
+  cudaError_t e = cudaFuncSetAttribute(k_tail32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTail32MaxSmem);
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "shared memory of the FP32 tail kernel", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
   return MPFC_OK;
 }
 

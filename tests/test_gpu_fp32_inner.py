@@ -70,3 +70,23 @@ def test_fp32_inner_mass_conservation(mp):
     m0 = g.mass()
     g.step(1, 20)
     assert abs(g.mass() - m0) < 1e-8 * abs(m0)
+
+
+@pytest.mark.parametrize("m,n", [(64, 64), (128, 128), (96, 160)])
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_fp32_tail_is_bitwise_the_per_level_cycle(mp, m, n, scheme):
+    """The inner V-cycles' small levels run in one CTA with the levels in shared memory
+    give exactly the bits of the per-level launches (whole steps, same outer counts)."""
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 5)
+    runs = []
+    for tail_cells in (0, 16 * 16, 64 * 64):
+        g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=0.05, precision=mp.MPFC_FP32_INNER))
+        g.set_launch_shape(4, 0, 4 * 152, tail_cells, 8)
+        g.set_state(phi0)
+        infos = g.step(scheme, 3)
+        runs.append(([i["cycles"] for i in infos], g.get_state()))
+        g.close()
+    for cyc, st in runs[1:]:
+        assert cyc == runs[0][0]
+        for a, b in zip(st, runs[0][1]):
+            assert np.array_equal(a, b)
