@@ -159,10 +159,11 @@ int mpfc_set_launch_mode(mpfc_t* h, int mode);
  * depend on it).  Launches of at least small_cells cells use blocks of 32 x rows
  * threads (rows 1, 2, 4 or 8), smaller ones one-warp blocks; grids of at most
  * pdl_blocks blocks are launched with programmatic dependent launch (0: none).  The
- * FP64 V-cycle's levels of at most tail_cells cells (0: none) run as one launch of a
- * thread-block cluster of tail_ctas CTAs (8, or 16 where the GPU can hold such a
- * cluster).  Drops the handle's captured graphs (rebuilt on the next step).  Returns
- * MPFC_ERR_INVALID for other values. */
+ * V-cycle's levels of at most tail_cells cells (0: none) run as one launch: for the
+ * FP64 path of one CTA (tail_ctas 1) or of a thread-block cluster of tail_ctas CTAs (8,
+ * or 16 where the GPU can hold such a cluster), for the FP32 inner cycles of one CTA
+ * with the levels in shared memory.  Drops the handle's captured graphs (rebuilt on the
+ * next step).  Returns MPFC_ERR_INVALID for other values. */
 int mpfc_set_launch_shape(mpfc_t* h, int rows, int small_cells, int pdl_blocks, int tail_cells, int tail_ctas);
 
 /* One step with exactly ncycles V-cycles (no tolerance test), for lockstep

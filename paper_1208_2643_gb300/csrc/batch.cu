@@ -101,14 +101,15 @@ __global__ void kb_tau(const BItem* __restrict__ items, int n, const Lev* __rest
 
 __global__ void __launch_bounds__(kPTX * kPTY) kb_prolong(const BItem* __restrict__ items, int n,
                                                           const Lev* __restrict__ levs, const BCtl* __restrict__ ctl) {
-  __shared__ double E[kPTY + 2][kPTX + 2];
+  __shared__ ProlongTile E;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     BItem w = items[it];
-    if (!ctl[w.inst].active) continue;
+    if (!ctl[w.inst].active) continue;   // uniform over the block
     const int idc = w.inst * kMaxLevels + w.level;
     Lev C = levs[idc], F = levs[idc - 1];
     ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n};
     prolong_tile(A, E, w.x0, w.y0);
+    __syncthreads();   // E is restaged for the next item
   }
 }
 

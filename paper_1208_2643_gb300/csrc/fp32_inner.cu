@@ -125,6 +125,41 @@ __device__ __forceinline__ float ld32(const float* p) {
   return *p;
 }
 
+// The cell update of the correction equation on values: neighbour sums, q, the
+// defect source r and the cell's own e (in/out).  One order of operations for every
+// kernel that sweeps (global planes, shared-memory planes, temporally blocked tiles),
+// so they all give the same bits.
+__device__ __forceinline__ void smooth32_core(const Coef32& k, float smu, float ska, float sph, float q, float r1,
+                                              float r2, float r3, float& ep, float& em, float& ek) {
+  float R1 = fmaf(k.cmu, smu, r1);
+  float R2 = fmaf(k.ih2, ska, r2);
+  float R3 = fmaf(k.th2, sph, r3);
+  float rdet = __frcp_rn(fmaf(k.a, q, k.D0));
+  float nphi = fmaf(k.a, fmaf(k.b, R3, -R2), R1);
+  float nmu = fmaf(k.Q0 + q, R1, fmaf(-k.b, R3, R2));
+  if (k.relax) {
+    float wr = k.omega * rdet;
+    float wphi = nphi * wr;
+    float p0 = ep, m0 = em, k0 = ek;
+    ep = fmaf(k.omw, p0, wphi);
+    em = fmaf(k.omw, m0, nmu * wr);
+    ek = fmaf(-k.b3, wphi, fmaf(k.omega, R3, k.omw * k0));
+  } else {
+    float phin = nphi * rdet;
+    ep = phin;
+    em = nmu * rdet;
+    ek = fmaf(-k.b3, phin, R3);
+  }
+}
+
+// Defect rho = r - J e of the correction equation at one cell, on values.
+__device__ __forceinline__ void defect32_core(const Coef32& k, float p, float u, float v, float smu, float ska, float sph,
+                                              float q, float r1, float r2, float r3, float& d1, float& d2, float& d3) {
+  d1 = fmaf(k.cmu, fmaf(-4.f, u, smu), r1 - p);
+  d2 = fmaf(k.ih2, fmaf(-4.f, v, ska), fmaf(q, p, r2 - u));
+  d3 = fmaf(k.th2, fmaf(-4.f, p, sph), r3 - v);
+}
+
 template <bool NC>
 __device__ __forceinline__ void smooth32_cell(const Lev32& L, const Coef32& k, int i, int j) {
   int m = L.m;
@@ -137,26 +172,12 @@ __device__ __forceinline__ void smooth32_cell(const Lev32& L, const Coef32& k, i
   float smu = (ld32<NC>(em + w) + ld32<NC>(em + e)) + (ld32<NC>(em + s) + ld32<NC>(em + nn));
   float ska = (ld32<NC>(ek + w) + ld32<NC>(ek + e)) + (ld32<NC>(ek + s) + ld32<NC>(ek + nn));
   float sph = (ld32<NC>(ep + w) + ld32<NC>(ep + e)) + (ld32<NC>(ep + s) + ld32<NC>(ep + nn));
-  float q = ld32<NC>(L.q + c);
-  float R1 = fmaf(k.cmu, smu, ld32<NC>(L.r1 + c));
-  float R2 = fmaf(k.ih2, ska, ld32<NC>(L.r2 + c));
-  float R3 = fmaf(k.th2, sph, ld32<NC>(L.r3 + c));
-  float rdet = __frcp_rn(fmaf(k.a, q, k.D0));
-  float nphi = fmaf(k.a, fmaf(k.b, R3, -R2), R1);
-  float nmu = fmaf(k.Q0 + q, R1, fmaf(-k.b, R3, R2));
-  if (k.relax) {
-    float wr = k.omega * rdet;
-    float wphi = nphi * wr;
-    float p0 = ep[c], m0 = em[c], k0 = ek[c];
-    ep[c] = fmaf(k.omw, p0, wphi);
-    em[c] = fmaf(k.omw, m0, nmu * wr);
-    ek[c] = fmaf(-k.b3, wphi, fmaf(k.omega, R3, k.omw * k0));
-  } else {
-    float phin = nphi * rdet;
-    ep[c] = phin;
-    em[c] = nmu * rdet;
-    ek[c] = fmaf(-k.b3, phin, R3);
-  }
+  float a = ep[c], b = em[c], d = ek[c];
+  smooth32_core(k, smu, ska, sph, ld32<NC>(L.q + c), ld32<NC>(L.r1 + c), ld32<NC>(L.r2 + c), ld32<NC>(L.r3 + c), a, b,
+                d);
+  ep[c] = a;
+  em[c] = b;
+  ek[c] = d;
 }
 
 // ---------------------------------------------------------------------------
@@ -186,9 +207,8 @@ __device__ __forceinline__ void defect32(const Lev32& L, const Coef32& k, int i,
   float smu = (ld32<NC>(em + w) + ld32<NC>(em + e)) + (ld32<NC>(em + s) + ld32<NC>(em + nn));
   float ska = (ld32<NC>(ek + w) + ld32<NC>(ek + e)) + (ld32<NC>(ek + s) + ld32<NC>(ek + nn));
   float sph = (ld32<NC>(ep + w) + ld32<NC>(ep + e)) + (ld32<NC>(ep + s) + ld32<NC>(ep + nn));
-  d1 = fmaf(k.cmu, fmaf(-4.f, u, smu), ld32<NC>(L.r1 + c) - p);
-  d2 = fmaf(k.ih2, fmaf(-4.f, v, ska), fmaf(ld32<NC>(L.q + c), p, ld32<NC>(L.r2 + c) - u));
-  d3 = fmaf(k.th2, fmaf(-4.f, p, sph), ld32<NC>(L.r3 + c) - v);
+  defect32_core(k, p, u, v, smu, ska, sph, ld32<NC>(L.q + c), ld32<NC>(L.r1 + c), ld32<NC>(L.r2 + c),
+                ld32<NC>(L.r3 + c), d1, d2, d3);
 }
 
 // coarse source = R(r - J e), coarse correction starts at zero
@@ -222,38 +242,42 @@ __global__ void k_restrict_defect32(Lev32 F, Lev32 C, Coef32 kf) {
   restrict_defect32_cell<true>(F, C, kf, I, J);
 }
 
-// e_f += P e_c (bilinear, shared-memory tile of the coarse correction)
+// e_f += P e_c (bilinear, shared-memory tiles of the three components of the coarse
+// correction, staged together)
 constexpr int kTX = 32, kTY = 8;
-__device__ __forceinline__ void prolong32_plane(const float* __restrict__ ec, float* __restrict__ ef, int mc, int nc,
-                                                float (*E)[kTX + 2]) {
-  const int I0 = blockIdx.x * kTX, J0 = blockIdx.y * kTY;
-  for (int t = threadIdx.y * kTX + threadIdx.x; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
-    int ty = t / (kTX + 2), tx = t % (kTX + 2);
-    if (I0 + tx - 1 < mc + 1 && J0 + ty - 1 < nc + 1)
-      E[ty][tx] = __ldg(ec + (size_t)wrapm(J0 + ty - 1, nc) * mc + wrapm(I0 + tx - 1, mc));
-  }
-  __syncthreads();
-  int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
-  if (I < mc && J < nc) {
-    int x = threadIdx.x + 1, y = threadIdx.y + 1;
-    const float w9 = 9.f / 16.f, w3 = 3.f / 16.f, w1 = 1.f / 16.f;
-    float c9 = w9 * E[y][x];
-    int mf = 2 * mc;
-    size_t f00 = (size_t)(2 * J) * mf + 2 * I, f01 = f00 + mf;
-    ef[f00] += fmaf(w3, E[y][x - 1] + E[y - 1][x], fmaf(w1, E[y - 1][x - 1], c9));
-    ef[f00 + 1] += fmaf(w3, E[y][x + 1] + E[y - 1][x], fmaf(w1, E[y - 1][x + 1], c9));
-    ef[f01] += fmaf(w3, E[y][x - 1] + E[y + 1][x], fmaf(w1, E[y + 1][x - 1], c9));
-    ef[f01 + 1] += fmaf(w3, E[y][x + 1] + E[y + 1][x], fmaf(w1, E[y + 1][x + 1], c9));
-  }
-  __syncthreads();
+__device__ __forceinline__ void prolong32_apply(float (*E)[kTX + 2], float* __restrict__ ef, int mc, int I, int J) {
+  int x = threadIdx.x + 1, y = threadIdx.y + 1;
+  const float w9 = 9.f / 16.f, w3 = 3.f / 16.f, w1 = 1.f / 16.f;
+  float c9 = w9 * E[y][x];
+  int mf = 2 * mc;
+  size_t f00 = (size_t)(2 * J) * mf + 2 * I, f01 = f00 + mf;
+  ef[f00] += fmaf(w3, E[y][x - 1] + E[y - 1][x], fmaf(w1, E[y - 1][x - 1], c9));
+  ef[f00 + 1] += fmaf(w3, E[y][x + 1] + E[y - 1][x], fmaf(w1, E[y - 1][x + 1], c9));
+  ef[f01] += fmaf(w3, E[y][x - 1] + E[y + 1][x], fmaf(w1, E[y + 1][x - 1], c9));
+  ef[f01 + 1] += fmaf(w3, E[y][x + 1] + E[y + 1][x], fmaf(w1, E[y + 1][x + 1], c9));
 }
 
 __global__ void __launch_bounds__(kTX * kTY) k_prolong32(Lev32 F, Lev32 C) {
   pdl_enter();
-  __shared__ float E[kTY + 2][kTX + 2];
-  prolong32_plane(C.ephi, F.ephi, C.m, C.n, E);
-  prolong32_plane(C.emu, F.emu, C.m, C.n, E);
-  prolong32_plane(C.eka, F.eka, C.m, C.n, E);
+  __shared__ float E[3][kTY + 2][kTX + 2];
+  const int mc = C.m, nc = C.n;
+  const int I0 = blockIdx.x * kTX, J0 = blockIdx.y * kTY;
+  for (int t = threadIdx.y * kTX + threadIdx.x; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
+    int ty = t / (kTX + 2), tx = t % (kTX + 2);
+    if (I0 + tx - 1 < mc + 1 && J0 + ty - 1 < nc + 1) {
+      size_t id = (size_t)wrapm(J0 + ty - 1, nc) * mc + wrapm(I0 + tx - 1, mc);
+      E[0][ty][tx] = __ldg(C.ephi + id);
+      E[1][ty][tx] = __ldg(C.emu + id);
+      E[2][ty][tx] = __ldg(C.eka + id);
+    }
+  }
+  __syncthreads();
+  int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  if (I < mc && J < nc) {
+    prolong32_apply(E[0], F.ephi, mc, I, J);
+    prolong32_apply(E[1], F.emu, mc, I, J);
+    prolong32_apply(E[2], F.eka, mc, I, J);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +399,9 @@ size_t coarse32_smem(const Lev32& C) {
 
 // `sweeps` red-black sweeps of one level, one launch per colour.  (A single-launch
 // sweep over shared-memory tiles with a 2-cell halo halves the DRAM reads at 2048^2 but
-// was slower on GB300 at every level size measured: its staging is latency bound.)
+// was slower on GB300 at every level size measured: its staging is latency bound.  So
+// was temporal blocking, a level's nu sweeps plus its restriction in one launch over
+// tiles with a (2 nu + 1)-cell halo, at every level from 64^2 to 2048^2.)
 void sweeps32(const mpfc_launch_shape& sh, const Lev32& F, const Coef32& kf, int sweeps, cudaStream_t s) {
   dim3 g = mpfc_grid_of(sh, F.m / 2, F.n), b = mpfc_blk_for(sh, F.m / 2, F.n);
   for (int sw = 0; sw < sweeps; ++sw) {

@@ -160,7 +160,7 @@ __global__ void k_residual(Lev L, Coef k, double* r1, double* r2, double* r3) {
 // The restricted residual R r = (1/4) sum_B (S - N(u)) therefore takes the block sums
 // of S, u and of the Laplacians, plus the per-cell nonlinear term (and the pinning
 // term), instead of four full residual evaluations.
-template <int SCH, bool NC = true>
+template <int SCH, int LD = kLdNC>
 __device__ __forceinline__ void resid_restrict_cell(const Lev& F, const Lev& C, const Coef& kf, int keep_b, int I,
                                                     int J) {
   const int m = F.m, i0 = 2 * I, j0 = 2 * J;
@@ -169,9 +169,9 @@ __device__ __forceinline__ void resid_restrict_cell(const Lev& F, const Lev& C, 
   const size_t r0 = (size_t)j0 * m, r1 = r0 + m, rs = (size_t)js * m, rn = (size_t)jn * m;
   // block sum and the sum over the 8 bordering cells of one field
   auto sums = [&](const double* f, double& blk, double& outer) {
-    blk = (ldv<NC>(f + r0 + i0) + ldv<NC>(f + r0 + i0 + 1)) + (ldv<NC>(f + r1 + i0) + ldv<NC>(f + r1 + i0 + 1));
-    outer = ((ldv<NC>(f + r0 + iw) + ldv<NC>(f + r1 + iw)) + (ldv<NC>(f + r0 + ie) + ldv<NC>(f + r1 + ie))) +
-            ((ldv<NC>(f + rs + i0) + ldv<NC>(f + rs + i0 + 1)) + (ldv<NC>(f + rn + i0) + ldv<NC>(f + rn + i0 + 1)));
+    blk = (ldv<LD>(f + r0 + i0) + ldv<LD>(f + r0 + i0 + 1)) + (ldv<LD>(f + r1 + i0) + ldv<LD>(f + r1 + i0 + 1));
+    outer = ((ldv<LD>(f + r0 + iw) + ldv<LD>(f + r1 + iw)) + (ldv<LD>(f + r0 + ie) + ldv<LD>(f + r1 + ie))) +
+            ((ldv<LD>(f + rs + i0) + ldv<LD>(f + rs + i0 + 1)) + (ldv<LD>(f + rn + i0) + ldv<LD>(f + rn + i0 + 1)));
   };
   double sp, op, sm, om, sk, ok;
   sums(F.phi, sp, op);
@@ -183,17 +183,17 @@ __device__ __forceinline__ void resid_restrict_cell(const Lev& F, const Lev& C, 
 #pragma unroll
     for (int di = 0; di < 2; ++di) {
       const size_t id = (dj ? r1 : r0) + i0 + di;
-      const double p = ldv<NC>(F.phi + id);
-      const double pk = (SCH == 2) ? ldv<NC>(F.pk + id) : 0.0;
+      const double p = ldv<LD>(F.phi + id);
+      const double pk = (SCH == 2) ? ldv<LD>(F.pk + id) : 0.0;
       gs += g_of<SCH>(p, pk);
-      if (SCH == 2 && F.W) gs = fma(ldv<NC>(F.W + id), p, gs);
+      if (SCH == 2 && F.W) gs = fma(ldv<LD>(F.W + id), p, gs);
     }
-  const double ss1 = (ldv<NC>(F.S1 + r0 + i0) + ldv<NC>(F.S1 + r0 + i0 + 1)) +
-                     (ldv<NC>(F.S1 + r1 + i0) + ldv<NC>(F.S1 + r1 + i0 + 1));
-  const double ss2 = (ldv<NC>(F.S2 + r0 + i0) + ldv<NC>(F.S2 + r0 + i0 + 1)) +
-                     (ldv<NC>(F.S2 + r1 + i0) + ldv<NC>(F.S2 + r1 + i0 + 1));
-  const double ss3 = (ldv<NC>(F.S3 + r0 + i0) + ldv<NC>(F.S3 + r0 + i0 + 1)) +
-                     (ldv<NC>(F.S3 + r1 + i0) + ldv<NC>(F.S3 + r1 + i0 + 1));
+  const double ss1 = (ldv<LD>(F.S1 + r0 + i0) + ldv<LD>(F.S1 + r0 + i0 + 1)) +
+                     (ldv<LD>(F.S1 + r1 + i0) + ldv<LD>(F.S1 + r1 + i0 + 1));
+  const double ss2 = (ldv<LD>(F.S2 + r0 + i0) + ldv<LD>(F.S2 + r0 + i0 + 1)) +
+                     (ldv<LD>(F.S2 + r1 + i0) + ldv<LD>(F.S2 + r1 + i0 + 1));
+  const double ss3 = (ldv<LD>(F.S3 + r0 + i0) + ldv<LD>(F.S3 + r0 + i0 + 1)) +
+                     (ldv<LD>(F.S3 + r1 + i0) + ldv<LD>(F.S3 + r1 + i0 + 1));
   // sum_B r1 = sum S1 - sum phi + c sum Delta_h mu, and likewise rows 2 and 3
   const double sr1 = fma(kf.cmu, fma(-2.0, sm, om), ss1 - sp);
   const double sr2 = fma(kf.ih2, fma(-2.0, sk, ok), fma(kf.gam, sp, ss2 - sm) + gs);
@@ -223,7 +223,7 @@ __global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
 }
 
 // FAS restriction, part 2: S_c += N_c(u_c).
-template <int SCH, bool NC = true>
+template <int SCH, int LD = kLdNC>
 __device__ __forceinline__ void tau_cell(const Lev& C, const Coef& k, int i, int j) {
   int m = C.m;
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, C.n, C.nyn), jp = ywrap(j + 1, C.n, C.nyn);
@@ -232,18 +232,18 @@ __device__ __forceinline__ void tau_cell(const Lev& C, const Coef& k, int i, int
   const double* phi = C.phi;
   const double* mu = C.mu;
   const double* ka = C.ka;
-  double p = ldown<NC>(phi + c), u = ldown<NC>(mu + c), v = ldown<NC>(ka + c);
-  double smu = (ldown<NC>(mu + w) + ldown<NC>(mu + e)) + (ldown<NC>(mu + s) + ldown<NC>(mu + nn));
-  double ska = (ldown<NC>(ka + w) + ldown<NC>(ka + e)) + (ldown<NC>(ka + s) + ldown<NC>(ka + nn));
-  double sph = (ldown<NC>(phi + w) + ldown<NC>(phi + e)) + (ldown<NC>(phi + s) + ldown<NC>(phi + nn));
-  double pk = (SCH == 2) ? ldown<NC>(C.pk + c) : 0.0;
+  double p = ldown<LD>(phi + c), u = ldown<LD>(mu + c), v = ldown<LD>(ka + c);
+  double smu = (ldown<LD>(mu + w) + ldown<LD>(mu + e)) + (ldown<LD>(mu + s) + ldown<LD>(mu + nn));
+  double ska = (ldown<LD>(ka + w) + ldown<LD>(ka + e)) + (ldown<LD>(ka + s) + ldown<LD>(ka + nn));
+  double sph = (ldown<LD>(phi + w) + ldown<LD>(phi + e)) + (ldown<LD>(phi + s) + ldown<LD>(phi + nn));
+  double pk = (SCH == 2) ? ldown<LD>(C.pk + c) : 0.0;
   double N1 = fma(-k.cmu, fma(-4.0, u, smu), p);
-  double gam = (SCH == 2 && C.W) ? k.gam + ldown<NC>(C.W + c) : k.gam;
+  double gam = (SCH == 2 && C.W) ? k.gam + ldown<LD>(C.W + c) : k.gam;
   double N2 = fma(-k.ih2, fma(-4.0, v, ska), fma(-gam, p, u) - g_of<SCH>(p, pk));
   double N3 = fma(-k.th2, fma(-4.0, p, sph), v);
-  C.S1[c] = ldown<NC>(C.S1 + c) + N1;
-  C.S2[c] = ldown<NC>(C.S2 + c) + N2;
-  C.S3[c] = ldown<NC>(C.S3 + c) + N3;
+  C.S1[c] = ldown<LD>(C.S1 + c) + N1;
+  C.S2[c] = ldown<LD>(C.S2 + c) + N2;
+  C.S3[c] = ldown<LD>(C.S3 + c) + N3;
 }
 
 template <int SCH>
@@ -278,67 +278,71 @@ struct ProlongArgs {
   int nyn;                          // Neumann rule in y (ghost coarse row = boundary row)
 };
 
-// One thread per coarse cell; the block first stages e = u_c - b_c on its
-// (32+2) x (8+2) coarse tile (periodic halo) in shared memory, so each difference
-// is formed once, then writes the bilinear correction into its 2x2 fine children.
+// One thread per coarse cell; the block first stages e = u_c - b_c of all three
+// components on its (32+2) x (8+2) coarse tile (periodic halo) in shared memory, so
+// each difference is formed once and the three tiles load together, then writes the
+// bilinear correction into its 2x2 fine children.
 constexpr int kPTX = 32, kPTY = 8;
-__device__ __forceinline__ void prolong_plane(const double* __restrict__ cn, const double* __restrict__ co,
-                                              double* __restrict__ f, int mc, int nc, int nyn, double (*E)[kPTX + 2],
-                                              int I0, int J0) {
+using ProlongTile = double[3][kPTY + 2][kPTX + 2];
+
+__device__ __forceinline__ void prolong_apply(double (*E)[kPTX + 2], double* __restrict__ f, int mc, int I, int J) {
+  int x = threadIdx.x + 1, y = threadIdx.y + 1;
+  double e00 = E[y][x];
+  double eW = E[y][x - 1], eE = E[y][x + 1], eS = E[y - 1][x], eN = E[y + 1][x];
+  double eSW = E[y - 1][x - 1], eSE = E[y - 1][x + 1], eNW = E[y + 1][x - 1], eNE = E[y + 1][x + 1];
+  const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
+  int mf = 2 * mc;
+  size_t f00 = (size_t)(2 * J) * mf + 2 * I;
+  size_t f01 = f00 + mf;
+  double c9 = w9 * e00;
+  f[f00] += fma(w3, eW + eS, fma(w1, eSW, c9));
+  f[f00 + 1] += fma(w3, eE + eS, fma(w1, eSE, c9));
+  f[f01] += fma(w3, eW + eN, fma(w1, eNW, c9));
+  f[f01 + 1] += fma(w3, eE + eN, fma(w1, eNE, c9));
+}
+
+// The block's (kPTX x kPTY) coarse tile at (I0, J0): all three components.  A caller
+// that stages another tile into E afterwards synchronises the block first.
+__device__ __forceinline__ void prolong_tile(const ProlongArgs& A, ProlongTile& E, int I0, int J0) {
   for (int t = threadIdx.y * kPTX + threadIdx.x; t < (kPTX + 2) * (kPTY + 2); t += kPTX * kPTY) {
     int ty = t / (kPTX + 2), tx = t % (kPTX + 2);
-    int I = wrapm(I0 + tx - 1, mc), J = ywrap(J0 + ty - 1, nc, nyn);
-    if (I0 + tx - 1 < mc + 1 && J0 + ty - 1 < nc + 1) {
-      size_t id = (size_t)J * mc + I;
-      E[ty][tx] = __ldg(cn + id) - __ldg(co + id);
+    int I = wrapm(I0 + tx - 1, A.mc), J = ywrap(J0 + ty - 1, A.nc, A.nyn);
+    if (I0 + tx - 1 < A.mc + 1 && J0 + ty - 1 < A.nc + 1) {
+      size_t id = (size_t)J * A.mc + I;
+      E[0][ty][tx] = __ldg(A.cphi + id) - __ldg(A.ophi + id);
+      E[1][ty][tx] = __ldg(A.cmu + id) - __ldg(A.omu + id);
+      E[2][ty][tx] = __ldg(A.cka + id) - __ldg(A.oka + id);
     }
   }
   __syncthreads();
   int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
-  if (I < mc && J < nc) {
-    int x = threadIdx.x + 1, y = threadIdx.y + 1;
-    double e00 = E[y][x];
-    double eW = E[y][x - 1], eE = E[y][x + 1], eS = E[y - 1][x], eN = E[y + 1][x];
-    double eSW = E[y - 1][x - 1], eSE = E[y - 1][x + 1], eNW = E[y + 1][x - 1], eNE = E[y + 1][x + 1];
-    const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
-    int mf = 2 * mc;
-    size_t f00 = (size_t)(2 * J) * mf + 2 * I;
-    size_t f01 = f00 + mf;
-    double c9 = w9 * e00;
-    f[f00] += fma(w3, eW + eS, fma(w1, eSW, c9));
-    f[f00 + 1] += fma(w3, eE + eS, fma(w1, eSE, c9));
-    f[f01] += fma(w3, eW + eN, fma(w1, eNW, c9));
-    f[f01 + 1] += fma(w3, eE + eN, fma(w1, eNE, c9));
+  if (I < A.mc && J < A.nc) {
+    prolong_apply(E[0], A.fphi, A.mc, I, J);
+    prolong_apply(E[1], A.fmu, A.mc, I, J);
+    prolong_apply(E[2], A.fka, A.mc, I, J);
   }
-  __syncthreads();
-}
-
-// The block's (kPTX x kPTY) coarse tile at (I0, J0): all three components.
-__device__ __forceinline__ void prolong_tile(const ProlongArgs& A, double (*E)[kPTX + 2], int I0, int J0) {
-  prolong_plane(A.cphi, A.ophi, A.fphi, A.mc, A.nc, A.nyn, E, I0, J0);
-  prolong_plane(A.cmu, A.omu, A.fmu, A.mc, A.nc, A.nyn, E, I0, J0);
-  prolong_plane(A.cka, A.oka, A.fka, A.mc, A.nc, A.nyn, E, I0, J0);
 }
 
 static __global__ void __launch_bounds__(kPTX * kPTY) k_prolong(ProlongArgs A) {
   pdl_enter();
-  __shared__ double E[kPTY + 2][kPTX + 2];
+  __shared__ ProlongTile E;
   prolong_tile(A, E, blockIdx.x * kPTX, blockIdx.y * kPTY);
 }
 
 // The same correction at one fine cell (fi, fj), for kernels without the shared-memory
 // tile: the four coarse differences it needs are formed in place, and the weights are
 // applied in the tile version's order, so both give the same bits.
+template <int LD>
 __device__ __forceinline__ void prolong_fine_plane(const double* cn, const double* co, double* f, int mc, int nc, int nyn,
                                                    int fi, int fj) {
   const int I = fi >> 1, J = fj >> 1;
   const int Ix = wrapm(I + ((fi & 1) ? 1 : -1), mc), Jy = ywrap(J + ((fj & 1) ? 1 : -1), nc, nyn);
   const size_t c00 = (size_t)J * mc + I, cx = (size_t)J * mc + Ix, cy = (size_t)Jy * mc + I, cxy = (size_t)Jy * mc + Ix;
-  const double e00 = __ldcg(cn + c00) - __ldcg(co + c00), ex = __ldcg(cn + cx) - __ldcg(co + cx);
-  const double ey = __ldcg(cn + cy) - __ldcg(co + cy), exy = __ldcg(cn + cxy) - __ldcg(co + cxy);
+  const double e00 = ldown<LD>(cn + c00) - ldown<LD>(co + c00), ex = ldown<LD>(cn + cx) - ldown<LD>(co + cx);
+  const double ey = ldown<LD>(cn + cy) - ldown<LD>(co + cy), exy = ldown<LD>(cn + cxy) - ldown<LD>(co + cxy);
   const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
   const size_t id = (size_t)fj * (2 * mc) + fi;
-  f[id] = __ldcg(f + id) + fma(w3, ex + ey, fma(w1, exy, w9 * e00));
+  f[id] = ldown<LD>(f + id) + fma(w3, ex + ey, fma(w1, exy, w9 * e00));
 }
 
 // ---------------------------------------------------------------------------
@@ -415,7 +419,7 @@ __device__ __forceinline__ float coarse_cL(const Lev& C, float cih2, int r, int 
 // The Newton iteration on the coarsest grid.  R > 0: grids of at most min(R, 31)
 // cells, one Jacobian column per lane in R registers (gauss_jordan_cols); R == 0:
 // up to 64 cells, Gaussian elimination with row swaps in shared memory.
-template <int SCH, int R>
+template <int SCH, int R, int LD>
 __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restrict__ K3f, double* sm) {
   const int m = C.m, n = C.n, G = m * n, W = G + 1;
   double* ph = sm;
@@ -429,13 +433,12 @@ __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restri
   float* d = Jm + G * W;
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  // L2 loads: in the tail kernel these values were written by other CTAs of the cluster
   for (int t = lane; t < G; t += 32) {
-    ph[t] = __ldcg(C.phi + t);
-    s1[t] = __ldcg(C.S1 + t);
-    s2[t] = __ldcg(C.S2 + t);
-    s3[t] = __ldcg(C.S3 + t);
-    pk[t] = (SCH == 2) ? __ldcg(C.pk + t) : 0.0;
+    ph[t] = ldown<LD>(C.phi + t);
+    s1[t] = ldown<LD>(C.S1 + t);
+    s2[t] = ldown<LD>(C.S2 + t);
+    s3[t] = ldown<LD>(C.S3 + t);
+    pk[t] = (SCH == 2) ? ldown<LD>(C.pk + t) : 0.0;
   }
   __syncwarp();
   const float cf = (float)k.c, ih2f = (float)k.ih2, gamf = (float)k.gam;
@@ -547,20 +550,21 @@ __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restri
 // every update is computed from the FP64 residual, so the iteration converges to the
 // FP64 root.  FP32 keeps the elimination off the slow FP64 pipe (on GB300 one
 // warp-wide FP64 instruction occupies a sub-partition's FP64 unit for about 80 cycles).
-// Called by one warp (the others of the block must not wait on it).
-template <int SCH>
+// Called by one warp (the others of the block must not wait on it).  LD: how the
+// level's planes are read (kLdL2 inside a cluster kernel).
+template <int SCH, int LD = kLdPlain>
 __device__ void coarse_solve_warp(const Lev& C, const Coef& k, const float* __restrict__ K3f, double* sm) {
   const int G = C.m * C.n;
-  if (G <= 16) coarse_newton<SCH, 16>(C, k, K3f, sm);
-  else if (G <= 31) coarse_newton<SCH, 32>(C, k, K3f, sm);
-  else coarse_newton<SCH, 0>(C, k, K3f, sm);
+  if (G <= 16) coarse_newton<SCH, 16, LD>(C, k, K3f, sm);
+  else if (G <= 31) coarse_newton<SCH, 32, LD>(C, k, K3f, sm);
+  else coarse_newton<SCH, 0, LD>(C, k, K3f, sm);
 }
 
 template <int SCH>
 __device__ void coarse_solve_block(const Lev& C, const Coef& k, const float* __restrict__ K3f) {
   extern __shared__ double sm[];
   if (threadIdx.x >= 32) return;
-  coarse_solve_warp<SCH>(C, k, K3f, sm);
+  coarse_solve_warp<SCH, kLdPlain>(C, k, K3f, sm);
 }
 
 template <int SCH>

@@ -13,7 +13,7 @@
 // EDGE: a row next to a Neumann boundary, where the ghost neighbour is the cell's own
 // unknown (App. A, (A.7)): it leaves the neighbour sums and k holds the coefficients
 // of three neighbours.
-template <int SCH, bool EDGE, bool NC>
+template <int SCH, bool EDGE, int LD>
 __device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, int i, int j) {
   int m = L.m;
   int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
@@ -23,31 +23,31 @@ __device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, in
   double* __restrict__ mu = L.mu;
   double* __restrict__ ka = L.ka;
   // neighbours belong to the other colour: read-only during this launch
-  double smu = (ldv<NC>(mu + w) + ldv<NC>(mu + e)) + (ldv<NC>(mu + s) + ldv<NC>(mu + nn));
-  double ska = (ldv<NC>(ka + w) + ldv<NC>(ka + e)) + (ldv<NC>(ka + s) + ldv<NC>(ka + nn));
-  double sph = (ldv<NC>(phi + w) + ldv<NC>(phi + e)) + (ldv<NC>(phi + s) + ldv<NC>(phi + nn));
-  double p = ldown<NC>(phi + c);
+  double smu = (ldv<LD>(mu + w) + ldv<LD>(mu + e)) + (ldv<LD>(mu + s) + ldv<LD>(mu + nn));
+  double ska = (ldv<LD>(ka + w) + ldv<LD>(ka + e)) + (ldv<LD>(ka + s) + ldv<LD>(ka + nn));
+  double sph = (ldv<LD>(phi + w) + ldv<LD>(phi + e)) + (ldv<LD>(phi + s) + ldv<LD>(phi + nn));
+  double p = ldown<LD>(phi + c);
   if (EDGE) {   // the ghost was read as the cell's current value: take it out again
-    smu -= ldown<NC>(mu + c);
-    ska -= ldown<NC>(ka + c);
+    smu -= ldown<LD>(mu + c);
+    ska -= ldown<LD>(ka + c);
     sph -= p;
   }
-  double R1 = fma(k.cmu, smu, ldv<NC>(L.S1 + c));
-  double R3 = fma(k.th2, sph, ldv<NC>(L.S3 + c));
+  double R1 = fma(k.cmu, smu, ldv<LD>(L.S1 + c));
+  double R3 = fma(k.th2, sph, ldv<LD>(L.S3 + c));
   // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
   // q = g'(p) enters the determinant and the Cramer numerator of mu, and
   // e = g(p) - g'(p) p the right-hand side of row 2
   double R2, detw, Qq;   // detw = det / omega
   if (SCH == 1) {
     double p2 = p * p;
-    R2 = fma(k.ih2, ska, fma(-2.0, p2 * p, ldv<NC>(L.S2 + c)));   // e = -2 p^3
+    R2 = fma(k.ih2, ska, fma(-2.0, p2 * p, ldv<LD>(L.S2 + c)));   // e = -2 p^3
     detw = fma(k.a3w, p2, k.D0w);                                   // q = 3 p^2
     Qq = fma(3.0, p2, k.Q0);
   } else {
-    double pk = ldv<NC>(L.pk + c);
+    double pk = ldv<LD>(L.pk + c);
     double q = dg_of<2>(p, pk);
-    R2 = fma(k.ih2, ska, ldv<NC>(L.S2 + c) + (g_of<2>(p, pk) - q * p));
-    if (L.W) q += ldv<NC>(L.W + c);   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
+    R2 = fma(k.ih2, ska, ldv<LD>(L.S2 + c) + (g_of<2>(p, pk) - q * p));
+    if (L.W) q += ldv<LD>(L.W + c);   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
     detw = fma(k.aw, q, k.D0w);
     Qq = k.Q0 + q;
   }
@@ -60,7 +60,7 @@ __device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, in
   const double nmu = fma(Qq, R1, -t);
   if (k.relax) {
     double wphi = nphi * wr;
-    double m0 = ldown<NC>(mu + c), k0 = ldown<NC>(ka + c);
+    double m0 = ldown<LD>(mu + c), k0 = ldown<LD>(ka + c);
     phi[c] = fma(k.omw, p, wphi);
     mu[c] = fma(k.omw, m0, nmu * wr);
     ka[c] = fma(-k.b3, wphi, fma(k.omega, R3, k.omw * k0));
@@ -74,10 +74,10 @@ __device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, in
 
 // Rows are warp-uniform, so the branch does not diverge; periodic levels never take
 // it.  Two bodies, each reading its coefficient set at fixed parameter offsets.
-template <int SCH, bool NC = true>
+template <int SCH, int LD = kLdNC>
 __device__ __forceinline__ void smooth_cell(const Lev& L, const Coef& k0, const Coef& kb, int i, int j) {
-  if (L.nyn && (j == 0 || j == L.n - 1)) smooth_cell_body<SCH, true, NC>(L, kb, i, j);
-  else smooth_cell_body<SCH, false, NC>(L, k0, i, j);
+  if (L.nyn && (j == 0 || j == L.n - 1)) smooth_cell_body<SCH, true, LD>(L, kb, i, j);
+  else smooth_cell_body<SCH, false, LD>(L, k0, i, j);
 }
 
 template <int SCH>

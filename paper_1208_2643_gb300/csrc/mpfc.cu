@@ -260,14 +260,15 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
 //   FP32 inner cycles (memory-latency bound, they want occupancy): 32 x 4 blocks and the
 //     same programmatic launch, 472 us per outer iteration against 479 (32 x 8, none)
 //     and 725 with one-warp blocks;
-//   the FP64 levels of at most 16 x 16 cells as one cluster launch: 2 to 9 us less per
-//     V-cycle (1024^2 to 64^2 grids); larger tails were slower, their phases being
-//     bound by the FP64 instruction latency of the cell updates, not by launches;
+//   the FP64 levels of at most 16 x 16 cells as one single-CTA launch: 701 us per
+//     V-cycle at 1024^2 against 721 without (a 16-CTA cluster: 719; at 64^2: 138, 162,
+//     155); larger tails were slower, their phases being bound by the FP64 instruction
+//     latency of the cell updates, not by launches;
 //   the FP32 inner cycles' levels of at most 32 x 32 cells in one CTA with the levels in
 //     shared memory: 430 us per outer iteration at 1024^2 against 475 (64 x 64: 457).
 mpfc_launch_shape mpfc_default_launch_shape(int precision) {
-  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * 152, 32 * 32, 8};
-  return mpfc_launch_shape{1, 0, 4 * 152, 256, mpfc_tail_max_ctas()};
+  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * 152, 32 * 32, 1};
+  return mpfc_launch_shape{1, 0, 4 * 152, 256, 1};
 }
 
 extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes, void* cuda_stream, mpfc_t** out) {
@@ -394,8 +395,8 @@ int mpfc_tail_max_ctas() {
   static int cached = 0;
   if (cached) return cached;
   int best = 8;
-  if (cudaFuncSetAttribute(k_tail<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-      cudaFuncSetAttribute(k_tail<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+  if (cudaFuncSetAttribute(k_tail<1, kLdL2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+      cudaFuncSetAttribute(k_tail<2, kLdL2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3(kTailThreads);
@@ -408,7 +409,7 @@ int mpfc_tail_max_ctas() {
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_tail<1>, &cfg) == cudaSuccess && n > 0) best = 16;
+    if (cudaOccupancyMaxActiveClusters(&n, k_tail<1, kLdL2>, &cfg) == cudaSuccess && n > 0) best = 16;
   }
   (void)cudaGetLastError();
   cached = best;
@@ -433,7 +434,7 @@ static int tail_first_level(const mpfc_s* H) {
   return lt;
 }
 
-// Levels lt .. nlev-1 as one cluster launch (k_tail).
+// Levels lt .. nlev-1 as one launch (k_tail): one CTA, or a cluster of tail_ctas CTAs.
 template <int SCH>
 static void launch_tail(mpfc_s* H, int lt, cudaStream_t s) {
   TailArgs A;
@@ -447,10 +448,15 @@ static void launch_tail(mpfc_s* H, int lt, cudaStream_t s) {
     A.lv[i].kb = H->coefb[SCH - 1][lt + i];
   }
   const int nc = H->shape.tail_ctas;
+  const size_t smem = coarse_smem(H->lev[H->nlev - 1]);
+  if (nc == 1) {   // one CTA: __syncthreads between the phases, plain (L1) loads
+    mpfc_launch(H->shape, k_tail<SCH, kLdPlain>, dim3(1), dim3(kTailThreads), smem, s, A);
+    return;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nc);
   cfg.blockDim = dim3(kTailThreads);
-  cfg.dynamicSmemBytes = coarse_smem(H->lev[H->nlev - 1]);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -461,7 +467,7 @@ static void launch_tail(mpfc_s* H, int lt, cudaStream_t s) {
   at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = (nc <= H->shape.pdl_blocks) ? 2 : 1;
-  (void)cudaLaunchKernelEx(&cfg, k_tail<SCH>, A);
+  (void)cudaLaunchKernelEx(&cfg, k_tail<SCH, kLdL2>, A);
 }
 
 template <int SCH>
@@ -666,7 +672,7 @@ static int launch_steps(mpfc_s* H, int scheme, int nsteps) {
 extern "C" int mpfc_set_launch_shape(mpfc_t* H, int rows, int small_cells, int pdl_blocks, int tail_cells,
                                      int tail_ctas) {
   if (!H || (rows != 1 && rows != 2 && rows != 4 && rows != 8) || small_cells < 0 || pdl_blocks < 0 ||
-      tail_cells < 0 || (tail_ctas != 8 && tail_ctas != 16))
+      tail_cells < 0 || (tail_ctas != 1 && tail_ctas != 8 && tail_ctas != 16))
     return MPFC_ERR_INVALID;
   if (tail_ctas > mpfc_tail_max_ctas()) return MPFC_ERR_INVALID;
   H->shape = mpfc_launch_shape{rows, small_cells, pdl_blocks, tail_cells, tail_ctas};

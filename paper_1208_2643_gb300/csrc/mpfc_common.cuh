@@ -109,21 +109,25 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// Loads of the per-cell stencil functions.  NC: the read-only (non-coherent) path,
-// valid only for data that no thread writes during the kernel; otherwise an L2 load
-// (ld.global.cg), for kernels that read what other CTAs of the same kernel wrote
-// before a release/acquire barrier.
-template <bool NC>
+// Loads of the per-cell stencil functions, by the kernel's memory situation:
+//   kLdNC:    the read-only (non-coherent) path, for data no thread writes during the
+//             kernel (the per-level kernels);
+//   kLdL2:    L2 loads (ld.global.cg), for reading what other CTAs of a cluster wrote
+//             before a release/acquire cluster barrier;
+//   kLdPlain: plain loads, for a single CTA (its writes and reads meet in its own L1,
+//             ordered by __syncthreads).
+constexpr int kLdNC = 0, kLdL2 = 1, kLdPlain = 2;
+template <int LD>
 __device__ __forceinline__ double ldv(const double* p) {
-  if (NC) return __ldg(p);
-  return __ldcg(p);
+  if (LD == kLdNC) return __ldg(p);
+  if (LD == kLdL2) return __ldcg(p);
+  return *p;
 }
-// A cell's own value, which the same thread may write later in the kernel: a plain
-// load, or an L2 load in the cross-CTA case.
-template <bool NC>
+// A cell's own value, which the same thread may write later in the kernel.
+template <int LD>
 __device__ __forceinline__ double ldown(const double* p) {
-  if (NC) return *p;
-  return __ldcg(p);
+  if (LD == kLdL2) return __ldcg(p);
+  return *p;
 }
 
 // Device-side control block of the time stepper.

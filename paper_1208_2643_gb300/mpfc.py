@@ -258,10 +258,10 @@ class Solver:
     def set_launch_mode(self, mode: int):
         _check(self.lib.mpfc_set_launch_mode(self.h, mode), "mpfc_set_launch_mode")
 
-    def set_launch_shape(self, rows: int, small_cells: int, pdl_blocks: int, tail_cells: int = 0, tail_ctas: int = 8):
+    def set_launch_shape(self, rows: int, small_cells: int, pdl_blocks: int, tail_cells: int = 0, tail_ctas: int = 1):
         """Block rows of large launches, the cell count below which launches use one-warp
         blocks, the largest grid launched with programmatic dependent launch, and the
-        levels (at most tail_cells cells) run as one cluster launch of tail_ctas CTAs."""
+        levels (at most tail_cells cells) run as one launch of tail_ctas CTAs."""
         _check(self.lib.mpfc_set_launch_shape(self.h, rows, small_cells, pdl_blocks, tail_cells, tail_ctas),
                "mpfc_set_launch_shape")
 

@@ -81,7 +81,7 @@ def test_fp32_tail_is_bitwise_the_per_level_cycle(mp, m, n, scheme):
     runs = []
     for tail_cells in (0, 16 * 16, 64 * 64):
         g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=0.05, precision=mp.MPFC_FP32_INNER))
-        g.set_launch_shape(4, 0, 4 * 152, tail_cells, 8)
+        g.set_launch_shape(4, 0, 4 * 152, tail_cells, 1)
         g.set_state(phi0)
         infos = g.step(scheme, 3)
         runs.append(([i["cycles"] for i in infos], g.get_state()))

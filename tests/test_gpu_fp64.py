@@ -386,11 +386,12 @@ def test_integer_pipe_conversions_match_ieee(mp):
     assert np.all(np.abs(t[nz]) <= np.abs(x[nz]))
 
 
-@pytest.mark.parametrize("ctas", [8, 16])
+@pytest.mark.parametrize("ctas", [1, 8, 16])
 @pytest.mark.parametrize("case", ["periodic1", "periodic2", "ragged2", "neumann2", "pinned2"])
 def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
-    """The coarse levels run as one thread-block cluster launch (barriers between the
-    phases) give exactly the bits of the per-level launches, over several steps."""
+    """The coarse levels run as one launch, of one CTA or of a thread-block cluster
+    (barriers between the phases), give exactly the bits of the per-level launches,
+    over several steps."""
     probe = mp.Solver(mp.default_params(m=64, n=64))
     try:
         probe.set_launch_shape(1, 0, 4 * 152, 64 * 64, ctas)
@@ -407,7 +408,7 @@ def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
         kw["pinning"] = 1
     phi0 = inputs.noise_field(m, n, 0.07, 0.05, 3)
     runs = []
-    for tail_cells in (0, 32 * 32, 64 * 64):
+    for tail_cells in (0, 16 * 16, 32 * 32, 64 * 64):
         g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=0.05, **kw))
         if case.startswith("pinned"):
             W = np.zeros((n, m))
