@@ -471,7 +471,7 @@ size_t carve_batch(mpfc_batch_s* B, int count, const mpfc_params* each, char* ba
   for (int i = 0; i < count; ++i) {
     int mc = each[i].m >> (nl[i] - 1), nc = each[i].n >> (nl[i] - 1);
     k3off[i] = (long long)k3tot;
-    k3tot += (size_t)mc * nc * mc * nc;
+    k3tot += 2 * (size_t)mc * nc * mc * nc;   // K3 and c L (mpfc_coarse_block)
   }
   float* d_K3a = c.take<float>(k3tot);
   float* d_K3b = c.take<float>(k3tot);
@@ -726,11 +726,11 @@ extern "C" int mpfc_batch_create(int count, const mpfc_params* each, void* d_wor
       k3off[i] = k3tot;
       const Lev& C = B->lev[(size_t)i * kMaxLevels + B->nlev[i] - 1];
       for (int s = 0; s < 2; ++s) {
-        std::vector<double> K3;
-        mpfc_build_K3(C, B->coef[s][(size_t)i * kMaxLevels + B->nlev[i] - 1], K3);
-        K3all[s].insert(K3all[s].end(), K3.begin(), K3.end());
+        std::vector<float> blk;
+        mpfc_coarse_block(C, B->coef[s][(size_t)i * kMaxLevels + B->nlev[i] - 1], blk);
+        K3all[s].insert(K3all[s].end(), blk.begin(), blk.end());
       }
-      k3tot += (long long)C.m * C.n * C.m * C.n;
+      k3tot += 2LL * C.m * C.n * C.m * C.n;
     }
     BGlobal g0;
     memset(&g0, 0, sizeof(g0));

@@ -309,13 +309,8 @@ __device__ void coarse32_block(const Lev32& C, const Coef32& k, const float* __r
   for (int t = tid; t < G; t += nt) t2[t] = C.r2[t] + t1[t];
   __syncthreads();
   for (int t = tid; t < G; t += nt) A[t * W + G] = C.r1[t] + k.cmu * (nbsum32(t2, m, n, t) - 4.f * t2[t]);
-  auto entry = [&](int r, int col) {
-    int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
-    int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
-              (ci == ri && cj == wrapm(rj - 1, n)) + (ci == ri && cj == wrapm(rj + 1, n));
-    float Lrc = k.ih2 * ((float)cnt - (r == col ? 4.f : 0.f));
-    return K3f[r * G + col] - k.c * Lrc * C.q[col];
-  };
+  const float* cLf = K3f + G * G;   // c L, after K3 in the coarse block
+  auto entry = [&](int r, int col) { return K3f[r * G + col] - cLf[r * G + col] * C.q[col]; };
   if (G <= 31) {
     // one warp: a Jacobian column per lane in registers, Gauss-Jordan with implicit
     // pivoting (gauss_jordan_cols); the right-hand side in lane G

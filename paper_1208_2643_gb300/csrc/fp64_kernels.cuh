@@ -348,10 +348,11 @@ __device__ __forceinline__ void prolong_fine_plane(const double* cn, const doubl
 // ---------------------------------------------------------------------------
 // Coarsest level: Newton on the eliminated equation for phi,
 //   F(phi) = phi - c L (S2 + g(phi) + gam phi + L (S3 + theta L phi)) - S1 = 0,
-// with Jacobian J = K3 - c L diag(gam + g'(phi)), K3 = I - c theta L^3 built on the
-// host.  FP32 elimination on one warp (registers up to 31 cells, shared memory up to
-// 64).  Stops one iteration after the update falls below 1e-15 (1 + |phi|_inf);
-// at most 40 iterations.  mu and kappa are then recovered from rows 3 and 2.
+// with Jacobian J = K3 - c L diag(gam + g'(phi)), K3 = I - c theta L^3 and c L built
+// on the host (mpfc_coarse_block).  FP32 elimination on one warp (registers up to 31
+// cells, shared memory up to 64).  Stops once the applied update is below
+// 1e-15 (1 + |phi|_inf); at most 40 iterations.  mu and kappa are then recovered from
+// rows 3 and 2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t, int nyn) {
   int i = t % m, j = t / m;
@@ -406,16 +407,6 @@ __device__ __forceinline__ void gauss_jordan_cols(float (&a)[R], int G, float* x
   __syncwarp();
 }
 
-// Entry (r, col) of c L, L the five-point Laplacian of the coarsest grid (a Neumann
-// ghost is the cell itself, so it lands on the diagonal: count 3 - 4).
-__device__ __forceinline__ float coarse_cL(const Lev& C, float cih2, int r, int col) {
-  const int m = C.m, n = C.n, nyn = C.nyn;
-  int ri = r % m, rj = r / m, ci = col % m, cj = col / m;
-  int cnt = (ci == wrapm(ri - 1, m) && cj == rj) + (ci == wrapm(ri + 1, m) && cj == rj) +
-            (ci == ri && cj == ywrap(rj - 1, n, nyn)) + (ci == ri && cj == ywrap(rj + 1, n, nyn));
-  return cih2 * ((float)cnt - (r == col ? 4.f : 0.f));
-}
-
 // The Newton iteration on the coarsest grid.  R > 0: grids of at most min(R, 31)
 // cells, one Jacobian column per lane in R registers (gauss_jordan_cols); R == 0:
 // up to 64 cells, Gaussian elimination with row swaps in shared memory.
@@ -441,14 +432,15 @@ __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restri
     pk[t] = (SCH == 2) ? ldown<LD>(C.pk + t) : 0.0;
   }
   __syncwarp();
-  const float cf = (float)k.c, ih2f = (float)k.ih2, gamf = (float)k.gam;
+  const float gamf = (float)k.gam;
   constexpr int RR = R > 0 ? R : 1;
   float k3c[RR], lcc[RR];   // this lane's column of K3 and of c L (register path)
+  const float* cLf = K3f + G * G;   // c L, after K3 in the coarse block
   if (R > 0) {
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
       k3c[r] = (lane < G && r < G) ? K3f[r * G + lane] : 0.f;
-      lcc[r] = (lane < G && r < G) ? cf * coarse_cL(C, ih2f, r, lane) : 0.f;
+      lcc[r] = (lane < G && r < G) ? cLf[r * G + lane] : 0.f;
     }
   }
   auto kappa_at = [&](int t) { return s3[t] + k.th2 * (nbsum_s(ph, m, n, t, C.nyn) - 4.0 * ph[t]); };
@@ -456,7 +448,6 @@ __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restri
     return s2[t] + g_of<SCH>(ph[t], pk[t]) + (k.gam + (C.W ? C.W[t] : 0.0)) * ph[t] +
            k.ih2 * (nbsum_s(kap, m, n, t, C.nyn) - 4.0 * kap[t]);
   };
-  bool extra = false;
   for (int it = 0; it < 40; ++it) {
     for (int t = lane; t < G; t += 32) kap[t] = kappa_at(t);
     __syncwarp();
@@ -481,7 +472,7 @@ __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restri
     } else {
       for (int idx = lane; idx < G * G; idx += 32) {
         int r = idx / G, col = idx % G;
-        Jm[r * W + col] = K3f[idx] - cf * coarse_cL(C, ih2f, r, col) * d[col];
+        Jm[r * W + col] = K3f[idx] - cLf[idx] * d[col];
       }
       __syncwarp();
       for (int col = 0; col < G; ++col) {
@@ -532,8 +523,8 @@ __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restri
       umax = fmax(umax, __shfl_xor_sync(FULL, umax, o));
     }
     __syncwarp();
-    if (extra || !(dmax == dmax)) break;
-    if ((double)dmax <= 1e-15 * (1.0 + umax)) extra = true;
+    // the update just applied was below 1e-15 (1 + |phi|_inf): converged to roundoff
+    if (!(dmax == dmax) || (double)dmax <= 1e-15 * (1.0 + umax)) break;
   }
   for (int t = lane; t < G; t += 32) kap[t] = kappa_at(t);
   __syncwarp();

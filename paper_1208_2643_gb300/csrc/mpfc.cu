@@ -190,8 +190,8 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
   }
   double* pinhat = p->pinning ? c.take<double>(G0) : nullptr;
   int Gc = lev[L - 1].m * lev[L - 1].n;
-  float* K3a = c.take<float>((size_t)Gc * Gc);
-  float* K3b = c.take<float>((size_t)Gc * Gc);
+  float* K3a = c.take<float>(2 * (size_t)Gc * Gc);   // K3 and c L of scheme 1 (mpfc_coarse_block)
+  float* K3b = c.take<float>(2 * (size_t)Gc * Gc);
   mpfc_fp32_carve(H, p, &c.off, base, L);
   mpfc_guess_carve(H, p, &c.off, base);
   if (H && base) {
@@ -271,6 +271,27 @@ mpfc_launch_shape mpfc_default_launch_shape(int precision) {
   return mpfc_launch_shape{1, 0, 4 * 152, 256, 1};
 }
 
+// The coarsest grid's matrices for one scheme as the FP32 block the coarse solves read:
+// K3 = I - c theta L^3 (G x G, row-major), then c L (G x G), L the five-point Laplacian
+// with the level's boundary rule.
+void mpfc_coarse_block(const Lev& C, const Coef& k, std::vector<float>& out) {
+  std::vector<double> K3;
+  mpfc_build_K3(C, k, K3);
+  const int m = C.m, n = C.n, G = m * n;
+  const double ih2 = 1.0 / (C.h * C.h);
+  std::vector<double> cL((size_t)G * G, 0.0);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < m; ++i) {
+      const int r = j * m + i;
+      cL[(size_t)r * G + r] -= 4.0 * k.c * ih2;
+      const int js = C.nyn ? (j > 0 ? j - 1 : 0) : (j + n - 1) % n, jn = C.nyn ? (j < n - 1 ? j + 1 : n - 1) : (j + 1) % n;
+      const int nb[4] = {j * m + (i + m - 1) % m, j * m + (i + 1) % m, js * m + i, jn * m + i};
+      for (int t = 0; t < 4; ++t) cL[(size_t)r * G + nb[t]] += k.c * ih2;
+    }
+  out.assign(K3.begin(), K3.end());
+  out.insert(out.end(), cL.begin(), cL.end());
+}
+
 extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes, void* cuda_stream, mpfc_t** out) {
   if (!out) return MPFC_ERR_INVALID;
   *out = nullptr;
@@ -304,7 +325,6 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
     c0.max_cycles = p->max_cycles;
     size_t G0 = (size_t)p->m * p->n;
     const Lev& C = H->lev[H->nlev - 1];
-    std::vector<double> K3;
     if ((e = cudaMemcpyAsync(H->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, H->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(H->phik, 0, G0 * sizeof(double), H->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(H->phikm1, 0, G0 * sizeof(double), H->stream)) != cudaSuccess ||
@@ -314,8 +334,8 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
       break;
     }
     for (int s = 0; s < 2 && rc == MPFC_OK; ++s) {
-      mpfc_build_K3(C, H->coef[s][H->nlev - 1], K3);
-      std::vector<float> K3f(K3.begin(), K3.end());
+      std::vector<float> K3f;
+      mpfc_coarse_block(C, H->coef[s][H->nlev - 1], K3f);
       if ((e = cudaMemcpyAsync(H->K3[s], K3f.data(), K3f.size() * sizeof(float), cudaMemcpyHostToDevice, H->stream)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(H->stream)) != cudaSuccess) {

@@ -56,7 +56,7 @@ struct mpfc_s {
   mpfc::Ctl* ctl = nullptr;
   double* partials = nullptr;
   mpfc::StepRecord* info = nullptr;
-  float* K3[2] = {nullptr, nullptr};    // I - c theta L^3 on the coarsest grid (FP32), per scheme
+  float* K3[2] = {nullptr, nullptr};    // coarsest grid, per scheme: I - c theta L^3 then c L (FP32)
   double* px[mpfc::kMaxLevels];
   double* pf[mpfc::kMaxLevels];
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -119,6 +119,7 @@ void mpfc_drop_graphs(mpfc_s* H);
 int mpfc_num_levels(int m, int n, int coarsest);
 mpfc::Coef mpfc_coef(const mpfc_params* p, int scheme, double h, int nb);
 void mpfc_build_K3(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<double>& K3);
+void mpfc_coarse_block(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<float>& out);
 int mpfc_reduce_blocks(size_t G);
 int mpfc_tail_max_ctas();
 mpfc_launch_shape mpfc_default_launch_shape(int precision);
