@@ -360,15 +360,15 @@ __device__ __forceinline__ double nbsum_s(const double* f, int m, int n, int t, 
          (f[ywrap(j - 1, n, nyn) * m + i] + f[ywrap(j + 1, n, nyn) * m + i]);
 }
 
-// Gauss-Jordan elimination with implicit partial pivoting on [J | rhs], one column per
-// lane held in registers (lane c < G: column c of J; lane G: the right-hand side), R
-// register rows (R >= G).  Column col: the lane that holds it picks the unused row of
-// largest magnitude, every lane divides its entry of that row by the pivot and
+// Gauss-Jordan elimination with implicit partial pivoting, one column of the augmented
+// matrix per lane held in registers (R register rows, R >= G; lanes past the augmented
+// columns hold zeros).  Column col (col < G): the lane that holds it picks the unused
+// row of largest magnitude, every lane divides its entry of that row by the pivot and
 // subtracts multiples of it from all other rows.  No row is moved: afterwards row
-// pivs[col] holds unknown col in the right-hand-side lane.  Writes the solution to
-// x[0..G); xr (G floats) and pivs (G ints) are shared scratch.
+// pivs[col] holds a 1 in column col and the lanes' other columns are transformed alike
+// (pivs: G ints of shared scratch).
 template <int R>
-__device__ __forceinline__ void gauss_jordan_cols(float (&a)[R], int G, float* x, float* xr, int* pivs) {
+__device__ __forceinline__ void gj_eliminate(float (&a)[R], int G, int* pivs) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   unsigned used = 0u;
@@ -398,6 +398,15 @@ __device__ __forceinline__ void gauss_jordan_cols(float (&a)[R], int G, float* x
     used |= 1u << pr;
     if (lane == 0) pivs[col] = pr;
   }
+  __syncwarp();
+}
+
+// [J | rhs] with the right-hand side in lane G: eliminates and writes the solution to
+// x[0..G); xr (G floats) and pivs (G ints) are shared scratch.
+template <int R>
+__device__ __forceinline__ void gauss_jordan_cols(float (&a)[R], int G, float* x, float* xr, int* pivs) {
+  const int lane = threadIdx.x & 31;
+  gj_eliminate<R>(a, G, pivs);
   if (lane == G)
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -448,11 +457,62 @@ __device__ void coarse_newton(const Lev& C, const Coef& k, const float* __restri
     return s2[t] + g_of<SCH>(ph[t], pk[t]) + (k.gam + (C.W ? C.W[t] : 0.0)) * ph[t] +
            k.ih2 * (nbsum_s(kap, m, n, t, C.nyn) - 4.0 * kap[t]);
   };
+  bool refactor = true;   // chord path: eliminate J again at this iteration
+  float dprev = 0.f;
   for (int it = 0; it < 40; ++it) {
     for (int t = lane; t < G; t += 32) kap[t] = kappa_at(t);
     __syncwarp();
     for (int t = lane; t < G; t += 32) muv[t] = mu_at(t);
     __syncwarp();
+    if (R == 16) {
+      // Chord iteration with a lagged Jacobian (grids of at most 16 cells): Gauss-Jordan
+      // on [J | I] over the 32 lanes gives X with J^-1 = rows pivs[.] of X; it is redone
+      // only when the updates stop shrinking by 100x per iteration, and each iteration
+      // costs an FP64 residual and a product with J^-1.  Xs (G x G) and the right-hand
+      // side rh share Jm; pivs lives in d once d has been read.
+      float* Xs = Jm;
+      float* rh = Jm + G * G;
+      int* pivs = reinterpret_cast<int*>(d);
+      for (int t = lane; t < G; t += 32)
+        rh[t] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t, C.nyn) - 4.0 * muv[t]));
+      if (refactor) {
+        for (int t = lane; t < G; t += 32) d[t] = gamf + (float)((C.W ? C.W[t] : 0.0) + dg_of<SCH>(ph[t], pk[t]));
+        __syncwarp();
+        float a[16];
+        const float dc = lane < G ? d[lane] : 0.f;
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+          a[r] = lane < G ? fmaf(-lcc[r], dc, k3c[r]) : ((lane < 2 * G && lane - G == r) ? 1.f : 0.f);
+        __syncwarp();   // d is free from here: pivot indices
+        gj_eliminate<16>(a, G, pivs);
+        if (lane >= G && lane < 2 * G)
+#pragma unroll
+          for (int r = 0; r < 16; ++r)
+            if (r < G) Xs[r * G + (lane - G)] = a[r];
+      }
+      __syncwarp();
+      float delta = 0.f;
+      if (lane < G) {
+        const float* xrow = Xs + pivs[lane] * G;
+        for (int q = 0; q < G; ++q) delta = fmaf(xrow[q], rh[q], delta);
+      }
+      float dmax = fabsf(delta);
+      double umax = 0.0;
+      if (lane < G) {
+        const double pn = ph[lane] + (double)delta;
+        ph[lane] = pn;
+        umax = fabs(pn);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o));
+        umax = fmax(umax, __shfl_xor_sync(FULL, umax, o));
+      }
+      __syncwarp();
+      if (!(dmax == dmax) || (double)dmax <= 1e-15 * (1.0 + umax)) break;
+      refactor = it > 0 && !(dmax <= 0.01f * dprev);
+      dprev = dmax;
+      continue;
+    }
     for (int t = lane; t < G; t += 32)
       Jm[t * W + G] = (float)(s1[t] - ph[t] + k.cmu * (nbsum_s(muv, m, n, t, C.nyn) - 4.0 * muv[t]));
     // the diagonal factor gam + W + g'(phi) of each column, once per column

@@ -45,7 +45,7 @@ __device__ __forceinline__ void tail_half_sweep(const TailLev& T, int color, int
 // Every thread of the launch runs the same sequence of barriers: no thread leaves
 // early, and the coarsest solve (one warp of CTA 0) sits between two barriers.
 template <int SCH, int LD>
-__global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailArgs A) {
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const __grid_constant__ TailArgs A) {
   extern __shared__ double tail_sm[];
   pdl_enter();
   const int nth = gridDim.x * blockDim.x;
