@@ -125,10 +125,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
-def kernel_launches_per_step(levels, nu1, nu2, cycles, scheme):
-    prologue = 5 + (levels - 1 if scheme == 2 else 0)
-    per_cycle = (levels - 1) * (2 * nu1 + 2 + 1 + 2 * nu2) + 1 + 1
-    return prologue + cycles * per_cycle + 1
+def kernel_launches_per_step(solver, scheme, cycles):
+    """The library's own kernels launched by one FP64 step of `cycles` V-cycles."""
+    per_step, per_cycle = solver.launch_counts(scheme)
+    return per_step + cycles * per_cycle
 
 
 def traffic_for(kernel, size):
@@ -345,7 +345,7 @@ def run_ours(args):
         dist.barrier()
     cycles = [r["cycles"] for r in recs]
     steps_per_s = replicas.throughput(K, world, ms)
-    launches = sum(kernel_launches_per_step(solver.levels, p.nu1, p.nu2, c, scheme) for c in cycles)
+    launches = sum(kernel_launches_per_step(solver, scheme, c) for c in cycles)
 
     if args.profile:
         if rank == 0:

@@ -155,6 +155,12 @@ int mpfc_records(mpfc_t* h, mpfc_step_info* out, int max_records, int* count);
  * synchronises once per V-cycle. */
 int mpfc_set_launch_mode(mpfc_t* h, int mode);
 
+/* Kernel launches of one FP64 time step (handles with precision MPFC_FP64 and an
+ * analytic guess; MPFC_ERR_INVALID otherwise): *per_step launches besides the
+ * V-cycles, plus *per_cycle for each V-cycle, under the handle's current launch shape.
+ * Either pointer may be null. */
+int mpfc_launch_counts(const mpfc_t* h, int scheme, int* per_step, int* per_cycle);
+
 /* Launch shapes of the time step's per-cell kernels (a tuning choice: results do not
  * depend on it).  Launches of at least small_cells cells use blocks of 32 x rows
  * threads (rows 1, 2, 4 or 8), smaller ones one-warp blocks; grids of at most

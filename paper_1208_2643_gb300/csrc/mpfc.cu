@@ -700,6 +700,21 @@ extern "C" int mpfc_set_launch_shape(mpfc_t* H, int rows, int small_cells, int p
   return MPFC_OK;
 }
 
+extern "C" int mpfc_launch_counts(const mpfc_t* H, int scheme, int* per_step, int* per_cycle) {
+  if (!H || (scheme != 1 && scheme != 2) || H->p.precision != MPFC_FP64 || H->p.guess == MPFC_GUESS_LEARNED)
+    return MPFC_ERR_INVALID;
+  const mpfc_params& p = H->p;
+  const int L = H->nlev, lt = tail_first_level(H);
+  const int down = lt < L ? lt : L - 1;   // levels run by per-level launches
+  // per level: nu1 + nu2 sweeps of two colours, restriction, tau, prolongation
+  const int per_level = 2 * p.nu1 + 2 * p.nu2 + 3;
+  // + the tail launch or the coarsest solve, + the residual test
+  if (per_cycle) *per_cycle = down * per_level + 2;
+  // step begin, source and guess, kappa, mu, [phi^k onto the coarse levels], residual test, commit
+  if (per_step) *per_step = 6 + (scheme == 2 ? L - 1 : 0);
+  return MPFC_OK;
+}
+
 extern "C" int mpfc_set_launch_mode(mpfc_t* H, int mode) {
   if (!H || (mode != MPFC_LAUNCH_GRAPH && mode != MPFC_LAUNCH_STREAM)) return MPFC_ERR_INVALID;
   H->launch_mode = mode;

@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_probe_fp64_fma.argtypes = [_VP, _VP, P(ctypes.c_double)]
     lib.mpfc_probe_rcp.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.mpfc_set_launch_mode.argtypes = [_VP, ctypes.c_int]
+    lib.mpfc_launch_counts.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
     lib.mpfc_op_learned_guess.argtypes = [_VP]
     lib.mpfc_batch_workspace_bytes.argtypes = [ctypes.c_int, P(mpfc_params)]
@@ -254,6 +255,12 @@ class Solver:
         if rc != MPFC_OK and raise_on_error:
             raise MPFCError(rc, "mpfc_step")
         return out if raise_on_error else (rc, out)
+
+    def launch_counts(self, scheme: int):
+        """(launches per FP64 step besides the V-cycles, launches per V-cycle)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.mpfc_launch_counts(self.h, scheme, ctypes.byref(a), ctypes.byref(b)), "mpfc_launch_counts")
+        return a.value, b.value
 
     def set_launch_mode(self, mode: int):
         _check(self.lib.mpfc_set_launch_mode(self.h, mode), "mpfc_set_launch_mode")

@@ -424,3 +424,17 @@ def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
         assert cyc == runs[0][0]
         for a, b in zip(st, runs[0][1]):
             assert np.array_equal(a, b)
+
+
+def test_launch_counts(mp):
+    """Kernels per step and per V-cycle under the default launch shape: 64^2 has levels
+    64, 32, 16, 8, 4; the levels of at most 16 x 16 cells run as one launch, so two
+    levels keep their 11 launches (4 + 4 sweeps, restriction, tau, prolongation)."""
+    g = mp.Solver(mp.default_params(m=64, n=64))
+    assert g.launch_counts(1) == (6, 2 * 11 + 2)
+    assert g.launch_counts(2) == (6 + 4, 2 * 11 + 2)
+    g.set_launch_shape(1, 0, 608, 0, 1)   # no tail: every level above the coarsest, and the coarse solve
+    assert g.launch_counts(1) == (6, 4 * 11 + 2)
+    h = mp.Solver(mp.default_params(m=64, n=64, precision=mp.MPFC_FP32_INNER))
+    with pytest.raises(mp.MPFCError):
+        h.launch_counts(1)
