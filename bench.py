@@ -420,6 +420,24 @@ def run_ours(args):
                            "speedup_vs_fp64": (world * K / (ms32 * 1e-3)) / steps_per_s}
     for obj in (s32, a64, a32):
         obj.close()
+    # the FP32 sweep against the HBM roofline, at 2048^2 (the mixed-precision workload's size,
+    # planes 7 x 16 MB): one red-black sweep after an L2 flush, median of 7; 40 algorithmic
+    # bytes per cell (e read and written, r and q read)
+    if rank == 0:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        big = mpfc.Solver(mpfc.default_params(m=2048, n=2048, h=w["h"], precision=mpfc.MPFC_FP32_INNER), stream=stream)
+        big.fp32_time_smooth(0, 1)
+        tsw = []
+        for _ in range(7):
+            flush.fill_(2.0)
+            tsw.append(big.fp32_time_smooth(0, 1))
+        big.close()
+        t = statistics.median(tsw) * 1e-3
+        gbs = 40.0 * 2048 * 2048 / t / 1e9
+        forms["fp32_inner"]["sweep_roofline"] = {
+            "kernel": "k_smooth32, one red+black sweep at 2048^2, L2 flushed before it", "us": t * 1e6,
+            "bound": "hbm", "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
     # batched ensemble: 64 instances, sizes uniform from {128, 256, 512, 1024}^2, eps ~ U[0.02, 0.1],
     # beta ~ U[0.5, 1.5], mean density ~ U[0.05, 0.1], h = 0.5, s = 0.01, noise 0.05 U (seed 4)
@@ -466,6 +484,28 @@ def run_ours(args):
                             "tiles": {str(k): v[:2] for k, v in tiles.items()},
                             "steps": Kb}
         b.close()
+        # 64 instances of the headline workload at 1024^2 in one batch (8 GB of workspace)
+        bp64 = [mpfc.default_params(m=size, n=size, h=w["h"], M=w["M"], epsilon=w["epsilon"], beta=w["beta"], dt=w["dt"],
+                                    tol=w["tol"], omega=w["omega"]) for _ in range(64)]
+        b64 = mpfc.BatchSolver(bp64, stream=stream)
+        for i in range(64):
+            b64.set_state(i, phi0)
+        tuning.autotune(b64, scheme, reps=2)
+        b64.step(scheme, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(3.0)
+        e0.record(stream)
+        _, _, cy64 = b64.step(scheme, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        forms["batched_64x1024"] = {"workload": "64 x the headline workload (1024^2) in one batch, fp64, tol 1e-10",
+                                    "instance_steps_per_s": world * 64 * 2 / (ms64 * 1e-3),
+                                    "cell_updates_per_s": world * 64 * size * size * 2 / (ms64 * 1e-3),
+                                    "vs_single_instance_cell_updates": (64 * size * size * 2 / (ms64 * 1e-3)) /
+                                                                       (steps_per_s / world * size * size),
+                                    "vcycles_per_instance_step": float(np.mean(cy64)) / 2, "steps": 2}
+        b64.close()
 
     # learned initial guess (model trained by paper_1208_2643_gb300.guess on solver data at 256^2)
     if not args.no_learned:

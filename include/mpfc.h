@@ -161,6 +161,13 @@ int mpfc_set_launch_mode(mpfc_t* h, int mode);
  * Either pointer may be null. */
 int mpfc_launch_counts(const mpfc_t* h, int scheme, int* per_step, int* per_cycle);
 
+/* Measurement helper of the mixed-precision form: times `sweeps` red-black FP32
+ * sweeps of the correction equation (two launches each) on level `level` of a handle
+ * created with precision MPFC_FP32_INNER, whatever its planes hold, between CUDA events
+ * on the handle's stream, and writes the milliseconds to *ms (host).  Synchronises.
+ * The planes' contents change; call mpfc_set_state before stepping again. */
+int mpfc_fp32_time_smooth(mpfc_t* h, int level, int sweeps, float* ms);
+
 /* Launch shapes of the time step's per-cell kernels (a tuning choice: results do not
  * depend on it).  Launches of at least small_cells cells use blocks of 32 x rows
  * threads (rows 1, 2, 4 or 8), smaller ones one-warp blocks; grids of at most

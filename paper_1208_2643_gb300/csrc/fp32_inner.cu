@@ -654,6 +654,31 @@ size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base,
   return *off - start;
 }
 
+extern "C" int mpfc_fp32_time_smooth(mpfc_t* H, int level, int sweeps, float* ms) {
+  if (!H || H->p.precision != MPFC_FP32_INNER || level < 0 || level >= H->nlev || sweeps < 1 || !ms)
+    return MPFC_ERR_INVALID;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "cudaEventCreate", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
+  if ((e = cudaEventRecord(e0, H->stream)) == cudaSuccess) {
+    sweeps32(H->shape, H->lev32[level], coef32_of(H->coef[0][level]), sweeps, H->stream);
+    if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(e1, H->stream)) == cudaSuccess &&
+        (e = cudaEventSynchronize(e1)) == cudaSuccess)
+      e = cudaEventElapsedTime(ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "mpfc_fp32_time_smooth", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
+  return MPFC_OK;
+}
+
 int mpfc_fp32_init(mpfc_s* H) {
   if (H->p.precision != MPFC_FP32_INNER) return MPFC_OK;
   H->K3f[0] = H->K3[0];

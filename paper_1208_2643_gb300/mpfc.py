@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_probe_fp64_fma.argtypes = [_VP, _VP, P(ctypes.c_double)]
     lib.mpfc_probe_rcp.argtypes = [_VP, _VP, ctypes.c_int, _VP]
     lib.mpfc_set_launch_mode.argtypes = [_VP, ctypes.c_int]
+    lib.mpfc_fp32_time_smooth.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     lib.mpfc_launch_counts.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
     lib.mpfc_op_learned_guess.argtypes = [_VP]
@@ -261,6 +262,12 @@ class Solver:
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(self.lib.mpfc_launch_counts(self.h, scheme, ctypes.byref(a), ctypes.byref(b)), "mpfc_launch_counts")
         return a.value, b.value
+
+    def fp32_time_smooth(self, level: int = 0, sweeps: int = 1) -> float:
+        """Milliseconds of `sweeps` FP32 red-black sweeps of one level (mixed-precision handles)."""
+        ms = ctypes.c_float()
+        _check(self.lib.mpfc_fp32_time_smooth(self.h, level, sweeps, ctypes.byref(ms)), "mpfc_fp32_time_smooth")
+        return ms.value
 
     def set_launch_mode(self, mode: int):
         _check(self.lib.mpfc_set_launch_mode(self.h, mode), "mpfc_set_launch_mode")
