@@ -345,7 +345,9 @@ def run_ours(args):
         dist.barrier()
     cycles = [r["cycles"] for r in recs]
     steps_per_s = replicas.throughput(K, world, ms)
-    launches = sum(kernel_launches_per_step(solver, scheme, c) for c in cycles)
+    # counted for the FP64 step (the headline); the profiling forms (--form fp32|learned) have none
+    launches = (sum(kernel_launches_per_step(solver, scheme, c) for c in cycles)
+                if args.form == "fp64" else None)
 
     if args.profile:
         if rank == 0:

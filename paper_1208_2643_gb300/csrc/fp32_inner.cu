@@ -396,7 +396,13 @@ size_t coarse32_smem(const Lev32& C) {
 // sweep over shared-memory tiles with a 2-cell halo halves the DRAM reads at 2048^2 but
 // was slower on GB300 at every level size measured: its staging is latency bound.  So
 // was temporal blocking, a level's nu sweeps plus its restriction in one launch over
-// tiles with a (2 nu + 1)-cell halo, at every level from 64^2 to 2048^2.)
+// tiles with a (2 nu + 1)-cell halo, at every level from 64^2 to 2048^2.  A colour-split
+// layout of the FP32 planes (each colour's cells stored apart) cut a half sweep's DRAM
+// reads at 2048^2 from all seven planes, 117 MB, to its own colour's planes plus the
+// other colour's e, and the sweep from 57.9 to 49.8 us; but the transfer kernels and
+// the shared-memory tail slowed down under its addressing, and at the 1024^2 workload,
+// whose planes sit in L2, the form ran 977 against 1018 steps/s, so the layout stays
+// row-major.)
 void sweeps32(const mpfc_launch_shape& sh, const Lev32& F, const Coef32& kf, int sweeps, cudaStream_t s) {
   dim3 g = mpfc_grid_of(sh, F.m / 2, F.n), b = mpfc_blk_for(sh, F.m / 2, F.n);
   for (int sw = 0; sw < sweeps; ++sw) {
