@@ -438,3 +438,38 @@ def test_launch_counts(mp):
     h = mp.Solver(mp.default_params(m=64, n=64, precision=mp.MPFC_FP32_INNER))
     with pytest.raises(mp.MPFCError):
         h.launch_counts(1)
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_launch_shape_does_not_change_results(mp, scheme):
+    """Block shapes, programmatic dependent launch and the coarse tails are a tuning
+    choice: every shape gives the bits of the default one (128 x 96, 4 steps)."""
+    m, n = 128, 96
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 9)
+    shapes = [None, (8, 0, 0, 0, 1), (2, 38912, 0, 1024, 1), (4, 1 << 20, 1 << 20, 256, 8), (1, 0, 608, 64 * 64, 1)]
+    runs = []
+    for sh in shapes:
+        g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=0.05))
+        if sh is not None:
+            g.set_launch_shape(*sh)
+        g.set_state(phi0)
+        infos = g.step(scheme, 4)
+        runs.append(([i["cycles"] for i in infos], g.get_state()))
+        g.close()
+    for cyc, st in runs[1:]:
+        assert cyc == runs[0][0]
+        for a, b in zip(st, runs[0][1]):
+            assert np.array_equal(a, b)
+
+
+def test_launch_shape_rules(mp):
+    g = mp.Solver(mp.default_params(m=64, n=64))
+    for bad in ((3, 0, 0, 0, 1), (1, -1, 0, 0, 1), (1, 0, -1, 0, 1), (1, 0, 0, -5, 1), (1, 0, 0, 0, 4)):
+        with pytest.raises(mp.MPFCError):
+            g.set_launch_shape(*bad)
+    with pytest.raises(mp.MPFCError):   # the FP32 sweep timer wants a mixed-precision handle
+        g.fp32_time_smooth(0, 1)
+    h = mp.Solver(mp.default_params(m=64, n=64, precision=mp.MPFC_FP32_INNER))
+    assert h.fp32_time_smooth(0, 2) > 0.0
+    with pytest.raises(mp.MPFCError):
+        h.fp32_time_smooth(h.levels, 1)
