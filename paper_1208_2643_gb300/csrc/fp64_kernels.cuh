@@ -683,22 +683,10 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NS], double* partials, unsi
   return false;
 }
 
-// Scaled residual norm at the finest level, and the V-cycle loop decision.
+// The V-cycle loop decision from the scaled residual norm res (one thread).
 // mode 0: after the initial guess (sets res0); mode 1: after a V-cycle.
-template <int SCH>
-__global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double* partials, int mode,
-                                                 cudaGraphConditionalHandle hnd, int set_cond) {
-  pdl_enter();
-  double v[1] = {0.0};
-  int G = L.m * L.n;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
-    int i = t % L.m, j = t / L.m;
-    double a, b, c;
-    resid_at<SCH>(L, k, i, j, a, b, c);
-    v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));
-  }
-  if (!grid_sum<1>(v, partials, &ctl->counter)) return;
-  double res = sqrt(v[0] / (3.0 * (double)G));
+__device__ __forceinline__ void resnorm_decide(Ctl* ctl, double res, int mode, cudaGraphConditionalHandle hnd,
+                                               int set_cond) {
   int cond;
   if (mode == 0) {
     ctl->res0 = res;
@@ -715,6 +703,45 @@ __global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double
   else cond = (res > ctl->tol) && (ctl->cycles < ctl->max_cycles);
   if (mode == 0 && !(res == res)) { ctl->status = 2; cond = 0; }
   if (set_cond) cudaGraphSetConditional(hnd, cond ? 1u : 0u);
+}
+
+// Scaled residual norm at the finest level, and the V-cycle loop decision.
+template <int SCH>
+__global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double* partials, int mode,
+                                                 cudaGraphConditionalHandle hnd, int set_cond) {
+  pdl_enter();
+  double v[1] = {0.0};
+  int G = L.m * L.n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
+    int i = t % L.m, j = t / L.m;
+    double a, b, c;
+    resid_at<SCH>(L, k, i, j, a, b, c);
+    v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));
+  }
+  if (!grid_sum<1>(v, partials, &ctl->counter)) return;
+  resnorm_decide(ctl, sqrt(v[0] / (3.0 * (double)G)), mode, hnd, set_cond);
+}
+
+// The same after a V-cycle whose last half sweep was k_smooth_res: the residual of the
+// red cells ((i + j) even), plus the nb per-warp sums that k_smooth_res left in bpart
+// for the black ones, each added by a fixed thread, so the total does not depend on
+// timing.
+template <int SCH>
+__global__ void __launch_bounds__(256) k_resnorm_red(Lev L, Coef k, Ctl* ctl, double* partials, const double* bpart,
+                                                     int nb, cudaGraphConditionalHandle hnd, int set_cond) {
+  pdl_enter();
+  double v[1] = {0.0};
+  const int half = L.m >> 1, G = L.m * L.n, nth = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int t = tid; t < half * L.n; t += nth) {
+    const int j = t / half, i = 2 * (t - j * half) + (j & 1);
+    double a, b, c;
+    resid_at<SCH>(L, k, i, j, a, b, c);
+    v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));
+  }
+  for (int t = tid; t < nb; t += nth) v[0] += bpart[t];
+  if (!grid_sum<1>(v, partials, &ctl->counter)) return;
+  resnorm_decide(ctl, sqrt(v[0] / (3.0 * (double)G)), 1, hnd, set_cond);
 }
 
 // ---------------------------------------------------------------------------

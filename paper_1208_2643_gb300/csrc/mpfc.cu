@@ -150,6 +150,9 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
   size_t G0 = (size_t)p->m * p->n;
   Ctl* ctl = c.take<Ctl>(1);
   double* partials = c.take<double>((size_t)kMaxSums * kMaxPartials);
+  // per-warp residual sums of the finest level's last half sweep (k_smooth_res)
+  const int nbpart = ((p->m / 2 + 31) / 32) * p->n;
+  double* bpart = c.take<double>((size_t)nbpart);
   StepRecord* info = c.take<StepRecord>(kInfoCap);
   double* phik = c.take<double>(G0);
   double* phikm1 = c.take<double>(G0);
@@ -198,6 +201,8 @@ static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
     H->nlev = L;
     H->ctl = ctl;
     H->partials = partials;
+    H->bpart = bpart;
+    H->nbpart = nbpart;
     H->info = info;
     H->phik = phik;
     H->phikm1 = phikm1;
@@ -394,13 +399,18 @@ int mpfc_reduce_blocks(size_t G) {
   return (int)b;
 }
 
+// `sweeps` red-black sweeps; with bpart, the last half sweep is k_smooth_res, which also
+// leaves the residual sums of the cells it updates (the finest level's last sweep).
 template <int SCH>
 static void launch_smooth(const mpfc_launch_shape& sh, const Lev& L, const Coef& k, const Coef& kb, int sweeps,
-                          cudaStream_t s) {
+                          cudaStream_t s, double* bpart = nullptr) {
   dim3 b = mpfc_blk_for(sh, L.m / 2, L.n), g = mpfc_grid_of(sh, L.m / 2, L.n);
   for (int sw = 0; sw < sweeps; ++sw) {
     mpfc_launch(sh, k_smooth<SCH>, g, b, 0, s, L, k, kb, 0);
-    mpfc_launch(sh, k_smooth<SCH>, g, b, 0, s, L, k, kb, 1);
+    if (bpart && sw == sweeps - 1)
+      mpfc_launch(sh, k_smooth_res<SCH>, dim3((L.m / 2 + 31) / 32, L.n), dim3(32), 0, s, L, k, kb, bpart);
+    else
+      mpfc_launch(sh, k_smooth<SCH>, g, b, 0, s, L, k, kb, 1);
   }
 }
 
@@ -452,6 +462,14 @@ static int tail_first_level(const mpfc_s* H) {
   if (lt > L - 2) return L;
   if (L - lt > kMaxTail) lt = L - kMaxTail;
   return lt;
+}
+
+// Whether a V-cycle ends with k_smooth_res on the finest level (which then runs by
+// per-level launches and has post-sweeps), so that its residual test is k_resnorm_red.
+static bool vcycle_fuses_norm(const mpfc_s* H) {
+  const int L = H->nlev, lt = tail_first_level(H);
+  const int down = lt < L ? lt : L - 1;
+  return down >= 1 && H->p.nu2 >= 1;
 }
 
 // Levels lt .. nlev-1 as one launch (k_tail): one CTA, or a cluster of tail_ctas CTAs.
@@ -512,7 +530,8 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
     const Lev& C = H->lev[l + 1];
     ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n, C.nyn};
     mpfc_launch(sh, k_prolong, grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s, A);
-    launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu2, s);
+    launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu2, s,
+                       (l == 0 && vcycle_fuses_norm(H)) ? H->bpart : nullptr);
   }
 }
 
@@ -555,6 +574,12 @@ static void enqueue_commit(mpfc_s* H, cudaStream_t s) {
 template <int SCH>
 static void enqueue_resnorm(mpfc_s* H, int mode, cudaGraphConditionalHandle hnd, int set_cond, cudaStream_t s) {
   const Lev& L0 = H->lev[0];
+  if (mode == 1 && vcycle_fuses_norm(H)) {   // after a V-cycle that ended with k_smooth_res
+    int blocks = mpfc_reduce_blocks((size_t)L0.m * L0.n / 2);
+    mpfc_launch(H->shape, k_resnorm_red<SCH>, dim3(blocks), dim3(256), 0, s, L0, H->coef[SCH - 1][0], H->ctl,
+                H->partials, (const double*)H->bpart, H->nbpart, hnd, set_cond);
+    return;
+  }
   int blocks = mpfc_reduce_blocks((size_t)L0.m * L0.n);
   mpfc_launch(H->shape, k_resnorm<SCH>, dim3(blocks), dim3(256), 0, s, L0, H->coef[SCH - 1][0], H->ctl, H->partials, mode, hnd,
              set_cond);

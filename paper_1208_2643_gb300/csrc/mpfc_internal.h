@@ -55,6 +55,8 @@ struct mpfc_s {
   double* psik = nullptr;
   mpfc::Ctl* ctl = nullptr;
   double* partials = nullptr;
+  double* bpart = nullptr;   // per-warp residual sums of the finest level's last half sweep
+  int nbpart = 0;
   mpfc::StepRecord* info = nullptr;
   float* K3[2] = {nullptr, nullptr};    // coarsest grid, per scheme: I - c theta L^3 then c L (FP32)
   double* px[mpfc::kMaxLevels];
