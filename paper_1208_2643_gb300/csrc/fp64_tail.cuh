@@ -1,16 +1,17 @@
 // The coarse end of the FP64 V-cycle in one launch: one CTA (LD = kLdPlain) or one
-// thread-block cluster (LD = kLdL2) runs the whole sub-cycle from a small level down to the coarsest solve and back up (the FAS
-// V-cycle of App. B, in the order of the per-level launches: nu1 red-black sweeps,
-// restriction with the tau correction, recursion, prolongation, nu2 sweeps).  Phases
-// are separated by __syncthreads or cluster barriers with release/acquire semantics
-// instead of kernel boundaries, and every cell is computed by the same per-cell functions as the
-// per-level kernels, so the results are bit for bit those of the per-level launches.
-// On GB300 a small level's launch costs more than its work; this kernel replaces about
-// eleven launches per level.  Included by fp64_kernels.cuh inside namespace mpfc.
+// thread-block cluster (LD = kLdL2) runs the whole sub-cycle from a small level down to
+// the coarsest solve and back up (the FAS V-cycle of App. B, in the order of the
+// per-level launches: nu1 red-black sweeps, restriction with the tau correction,
+// recursion, prolongation, nu2 sweeps).  Phases are separated by __syncthreads or
+// cluster barriers with release/acquire semantics instead of kernel boundaries, and
+// every cell is computed by the same per-cell functions as the per-level kernels, so the
+// results are bit for bit those of the per-level launches.  On GB300 a small level's
+// launch costs more than its work; this kernel replaces eleven launches per level.
+// Included by fp64_kernels.cuh inside namespace mpfc.
 #pragma once
 
 constexpr int kMaxTail = 8;         // levels one tail launch can cover
-constexpr int kTailThreads = 256;   // threads per CTA of the tail cluster
+constexpr int kTailThreads = 256;   // threads per CTA (of the CTA, or of each CTA of the cluster)
 
 struct TailLev {
   Lev L;
