@@ -131,6 +131,16 @@ def kernel_launches_per_step(solver, scheme, cycles):
     return per_step + cycles * per_cycle
 
 
+def measured_peaks():
+    """HBM GB/s and dense bf16 TFLOP/s of the GB300s from MEASURED_PEAKS.json, with
+    `source` "measured"; if the file is absent, one earlier GB300 measurement ("fallback")."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
 def traffic_for(kernel, size):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source it
     was taken on is unchanged; else None."""
@@ -225,11 +235,11 @@ def conv32_timing(size, launches=10, flush_between=True):
     px = size * size
     flops = 2.0 * 9 * 32 * 32 * px
     bytes_ = (32 * 2 + 32 * 2) * px                 # read the bf16 input once, write the bf16 output
-    peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    peaks = measured_peaks()
     t = out.get("us_flushed", out["us_no_flush"]) * 1e-6
     out.update({"image": f"1 x {size} x {size} x 32 bf16", "tflops": flops / t / 1e12,
-                "frac_of_measured_bf16": flops / t / 1e12 / peaks["bf16_tflops"],
-                "gbs_algorithmic": bytes_ / t / 1e9, "frac_of_measured_hbm": bytes_ / t / 1e9 / peaks["hbm_gbs"],
+                f"frac_of_{peaks['source']}_bf16": flops / t / 1e12 / peaks["bf16_tflops"],
+                "gbs_algorithmic": bytes_ / t / 1e9, f"frac_of_{peaks['source']}_hbm": bytes_ / t / 1e9 / peaks["hbm_gbs"],
                 "bound": "neither: the epilogue (GELU on the MUFU pipe) and the TMA/MMA handoff set the rate"})
     return out
 
@@ -426,7 +436,7 @@ def run_ours(args):
     # planes 7 x 16 MB): one red-black sweep after an L2 flush, median of 7; 40 algorithmic
     # bytes per cell (e read and written, r and q read)
     if rank == 0:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks = measured_peaks()
         big = mpfc.Solver(mpfc.default_params(m=2048, n=2048, h=w["h"], precision=mpfc.MPFC_FP32_INNER), stream=stream)
         big.fp32_time_smooth(0, 1)
         tsw = []
@@ -439,7 +449,8 @@ def run_ours(args):
         forms["fp32_inner"]["sweep_roofline"] = {
             "kernel": "k_smooth32, one red+black sweep at 2048^2, L2 flushed before it", "us": t * 1e6,
             "bound": "hbm", "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+            "peak_source": ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks["source"] == "measured"
+                            else "6.8 TB/s, an earlier GB300 measurement (of fallback)")}
 
     # batched ensemble: 64 instances, sizes uniform from {128, 256, 512, 1024}^2, eps ~ U[0.02, 0.1],
     # beta ~ U[0.5, 1.5], mean density ~ U[0.05, 0.1], h = 0.5, s = 0.01, noise 0.05 U (seed 4)
