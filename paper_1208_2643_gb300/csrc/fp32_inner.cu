@@ -160,10 +160,12 @@ __device__ __forceinline__ void defect32_core(const Coef32& k, float p, float u,
   d3 = fmaf(k.th2, fmaf(-4.f, p, sph), r3 - v);
 }
 
+// kb: the cell system of a Neumann boundary row (three neighbours; the ghost is the
+// cell's own unknown, read once through the clamped index and taken out of the sums).
 template <bool NC>
-__device__ __forceinline__ void smooth32_cell(const Lev32& L, const Coef32& k, int i, int j) {
+__device__ __forceinline__ void smooth32_cell(const Lev32& L, const Coef32& k, const Coef32& kb, int i, int j) {
   int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
   float* __restrict__ ep = L.ephi;
@@ -173,8 +175,13 @@ __device__ __forceinline__ void smooth32_cell(const Lev32& L, const Coef32& k, i
   float ska = (ld32<NC>(ek + w) + ld32<NC>(ek + e)) + (ld32<NC>(ek + s) + ld32<NC>(ek + nn));
   float sph = (ld32<NC>(ep + w) + ld32<NC>(ep + e)) + (ld32<NC>(ep + s) + ld32<NC>(ep + nn));
   float a = ep[c], b = em[c], d = ek[c];
-  smooth32_core(k, smu, ska, sph, ld32<NC>(L.q + c), ld32<NC>(L.r1 + c), ld32<NC>(L.r2 + c), ld32<NC>(L.r3 + c), a, b,
-                d);
+  const float q = ld32<NC>(L.q + c), r1 = ld32<NC>(L.r1 + c), r2 = ld32<NC>(L.r2 + c), r3 = ld32<NC>(L.r3 + c);
+  // one inlined update per coefficient set (selecting between the two structs would copy
+  // them through local memory)
+  if (L.nyn && (j == 0 || j == L.n - 1))
+    smooth32_core(kb, smu - b, ska - d, sph - a, q, r1, r2, r3, a, b, d);
+  else
+    smooth32_core(k, smu, ska, sph, q, r1, r2, r3, a, b, d);
   ep[c] = a;
   em[c] = b;
   ek[c] = d;
@@ -184,12 +191,12 @@ __device__ __forceinline__ void smooth32_cell(const Lev32& L, const Coef32& k, i
 // FP32 red-black half sweep of the correction equation (App. B cell system with
 // the frozen linearisation q = gam + g'(phi)).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_smooth32(Lev32 L, Coef32 k, int color) {
+__global__ void __launch_bounds__(256) k_smooth32(Lev32 L, Coef32 k, Coef32 kb, int color) {
   pdl_enter();
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= (L.m >> 1) || j >= L.n) return;
-  smooth32_cell<true>(L, k, 2 * x + ((j + color) & 1), j);
+  smooth32_cell<true>(L, k, kb, 2 * x + ((j + color) & 1), j);
 }
 
 // defect of the correction equation at one cell: rho = r - J e
@@ -197,7 +204,8 @@ template <bool NC>
 __device__ __forceinline__ void defect32(const Lev32& L, const Coef32& k, int i, int j, float& d1, float& d2,
                                          float& d3) {
   int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = wrapm(j - 1, L.n), jp = wrapm(j + 1, L.n);
+  // a Neumann ghost reads as the cell itself, so the five-point sums are the boundary rule's
+  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
   size_t c = (size_t)j * m + i;
   size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
   const float* ep = L.ephi;
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(kTX * kTY) k_prolong32(Lev32 F, Lev32 C) {
   for (int t = threadIdx.y * kTX + threadIdx.x; t < (kTX + 2) * (kTY + 2); t += kTX * kTY) {
     int ty = t / (kTX + 2), tx = t % (kTX + 2);
     if (I0 + tx - 1 < mc + 1 && J0 + ty - 1 < nc + 1) {
-      size_t id = (size_t)wrapm(J0 + ty - 1, nc) * mc + wrapm(I0 + tx - 1, mc);
+      size_t id = (size_t)ywrap(J0 + ty - 1, nc, C.nyn) * mc + wrapm(I0 + tx - 1, mc);
       E[0][ty][tx] = __ldg(C.ephi + id);
       E[1][ty][tx] = __ldg(C.emu + id);
       E[2][ty][tx] = __ldg(C.eka + id);
@@ -286,10 +294,10 @@ __global__ void __launch_bounds__(kTX * kTY) k_prolong32(Lev32 F, Lev32 C) {
 // solve by Gaussian elimination with partial pivoting in one CTA, then
 // e_kappa = r3 + theta L e_phi, e_mu = r2 + q e_phi + L e_kappa.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float nbsum32(const float* f, int m, int n, int t) {
+__device__ __forceinline__ float nbsum32(const float* f, int m, int n, int t, int nyn) {
   int i = t % m, j = t / m;
   return (f[j * m + wrapm(i - 1, m)] + f[j * m + wrapm(i + 1, m)]) +
-         (f[wrapm(j - 1, n) * m + i] + f[wrapm(j + 1, n) * m + i]);
+         (f[ywrap(j - 1, n, nyn) * m + i] + f[ywrap(j + 1, n, nyn) * m + i]);
 }
 
 // The whole block; smf holds G (G + 1) + 4 G floats.  C's planes may be in global or
@@ -304,11 +312,11 @@ __device__ void coarse32_block(const Lev32& C, const Coef32& k, const float* __r
   __shared__ int s_piv;
   const int tid = threadIdx.x, nt = blockDim.x;
   // t1 = L r3 (with the 1/h^2 of L), t2 = r2 + t1
-  for (int t = tid; t < G; t += nt) t1[t] = k.ih2 * (nbsum32(C.r3, m, n, t) - 4.f * C.r3[t]);
+  for (int t = tid; t < G; t += nt) t1[t] = k.ih2 * (nbsum32(C.r3, m, n, t, C.nyn) - 4.f * C.r3[t]);
   __syncthreads();
   for (int t = tid; t < G; t += nt) t2[t] = C.r2[t] + t1[t];
   __syncthreads();
-  for (int t = tid; t < G; t += nt) A[t * W + G] = C.r1[t] + k.cmu * (nbsum32(t2, m, n, t) - 4.f * t2[t]);
+  for (int t = tid; t < G; t += nt) A[t * W + G] = C.r1[t] + k.cmu * (nbsum32(t2, m, n, t, C.nyn) - 4.f * t2[t]);
   const float* cLf = K3f + G * G;   // c L, after K3 in the coarse block
   auto entry = [&](int r, int col) { return K3f[r * G + col] - cLf[r * G + col] * C.q[col]; };
   if (G <= 31) {
@@ -372,10 +380,10 @@ __device__ void coarse32_block(const Lev32& C, const Coef32& k, const float* __r
       }
     __syncthreads();
   }
-  for (int t = tid; t < G; t += nt) t1[t] = C.r3[t] + k.th2 * (nbsum32(x, m, n, t) - 4.f * x[t]);   // e_kappa
+  for (int t = tid; t < G; t += nt) t1[t] = C.r3[t] + k.th2 * (nbsum32(x, m, n, t, C.nyn) - 4.f * x[t]);   // e_kappa
   __syncthreads();
   for (int t = tid; t < G; t += nt) {
-    C.emu[t] = C.r2[t] + C.q[t] * x[t] + k.ih2 * (nbsum32(t1, m, n, t) - 4.f * t1[t]);
+    C.emu[t] = C.r2[t] + C.q[t] * x[t] + k.ih2 * (nbsum32(t1, m, n, t, C.nyn) - 4.f * t1[t]);
     C.ephi[t] = x[t];
     C.eka[t] = t1[t];
   }
@@ -403,11 +411,12 @@ size_t coarse32_smem(const Lev32& C) {
 // the shared-memory tail slowed down under its addressing, and at the 1024^2 workload,
 // whose planes sit in L2, the form ran 977 against 1018 steps/s, so the layout stays
 // row-major.)
-void sweeps32(const mpfc_launch_shape& sh, const Lev32& F, const Coef32& kf, int sweeps, cudaStream_t s) {
+void sweeps32(const mpfc_launch_shape& sh, const Lev32& F, const Coef32& kf, const Coef32& kb, int sweeps,
+              cudaStream_t s) {
   dim3 g = mpfc_grid_of(sh, F.m / 2, F.n), b = mpfc_blk_for(sh, F.m / 2, F.n);
   for (int sw = 0; sw < sweeps; ++sw) {
-    mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, 0);
-    mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, 1);
+    mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, kb, 0);
+    mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, kb, 1);
   }
 }
 
@@ -430,13 +439,13 @@ struct Tail32Args {
   int nlev, nu1, nu2;
   const float* K3f;
   Lev32 g[kMaxTail32];    // the levels' global planes
-  Coef32 k[kMaxTail32];
+  Coef32 k[kMaxTail32], kb[kMaxTail32];   // interior and Neumann-row cell systems
 };
 
 // e_f += P e_c at one fine cell, with the tile version's order of operations.
-__device__ __forceinline__ void prolong32_fine(const float* ec, float* ef, int mc, int nc, int fi, int fj) {
+__device__ __forceinline__ void prolong32_fine(const float* ec, float* ef, int mc, int nc, int nyn, int fi, int fj) {
   const int I = fi >> 1, J = fj >> 1;
-  const int Ix = wrapm(I + ((fi & 1) ? 1 : -1), mc), Jy = wrapm(J + ((fj & 1) ? 1 : -1), nc);
+  const int Ix = wrapm(I + ((fi & 1) ? 1 : -1), mc), Jy = ywrap(J + ((fj & 1) ? 1 : -1), nc, nyn);
   const float e00 = ec[J * mc + I], ex = ec[J * mc + Ix], ey = ec[Jy * mc + I], exy = ec[Jy * mc + Ix];
   const float w9 = 9.f / 16.f, w3 = 3.f / 16.f, w1 = 1.f / 16.f;
   const int id = fj * (2 * mc) + fi;
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant
       for (int color = 0; color < 2; ++color) {
         for (int t = tid; t < hc; t += nt) {
           const int j = t / half, x = t - j * half;
-          smooth32_cell<false>(F, A.k[l], 2 * x + ((j + color) & 1), j);
+          smooth32_cell<false>(F, A.k[l], A.kb[l], 2 * x + ((j + color) & 1), j);
         }
         __syncthreads();
       }
@@ -516,9 +525,9 @@ __global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant
     const int fc = F.m * F.n;
     for (int t = tid; t < fc; t += nt) {
       const int fi = t % F.m, fj = t / F.m;
-      prolong32_fine(C.ephi, F.ephi, C.m, C.n, fi, fj);
-      prolong32_fine(C.emu, F.emu, C.m, C.n, fi, fj);
-      prolong32_fine(C.eka, F.eka, C.m, C.n, fi, fj);
+      prolong32_fine(C.ephi, F.ephi, C.m, C.n, C.nyn, fi, fj);
+      prolong32_fine(C.emu, F.emu, C.m, C.n, C.nyn, fi, fj);
+      prolong32_fine(C.eka, F.eka, C.m, C.n, C.nyn, fi, fj);
     }
     __syncthreads();
     const int half = F.m >> 1, hc = half * F.n;
@@ -526,7 +535,7 @@ __global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant
       for (int color = 0; color < 2; ++color) {
         for (int t = tid; t < hc; t += nt) {
           const int j = t / half, x = t - j * half;
-          smooth32_cell<false>(F, A.k[l], 2 * x + ((j + color) & 1), j);
+          smooth32_cell<false>(F, A.k[l], A.kb[l], 2 * x + ((j + color) & 1), j);
         }
         __syncthreads();
       }
@@ -565,6 +574,7 @@ void launch_tail32(mpfc_s* H, int scheme, int lt, cudaStream_t s) {
   for (int i = 0; i < A.nlev; ++i) {
     A.g[i] = H->lev32[lt + i];
     A.k[i] = coef32_of(H->coef[scheme - 1][lt + i]);
+    A.kb[i] = coef32_of(H->coefb[scheme - 1][lt + i]);
   }
   mpfc_launch(H->shape, k_tail32, dim3(1), dim3(kTail32Threads), tail32_smem(H->lev32 + lt, A.nlev), s, A);
 }
@@ -579,8 +589,8 @@ void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
   for (int l = 0; l < down; ++l) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
-    Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
-    sweeps32(sh, F, kf, p.nu1, s);
+    Coef32 kf = coef32_of(H->coef[scheme - 1][l]), kb = coef32_of(H->coefb[scheme - 1][l]);
+    sweeps32(sh, F, kf, kb, p.nu1, s);
     mpfc_launch(sh, k_restrict_defect32, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C, kf);
   }
   if (lt < L) {
@@ -593,9 +603,9 @@ void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
   for (int l = down - 1; l >= 0; --l) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
-    Coef32 kf = coef32_of(H->coef[scheme - 1][l]);
+    Coef32 kf = coef32_of(H->coef[scheme - 1][l]), kb = coef32_of(H->coefb[scheme - 1][l]);
     mpfc_launch(sh, k_prolong32, grid_of(C.m, C.n), kBlk, 0, s, F, C);
-    sweeps32(sh, F, kf, p.nu2, s);
+    sweeps32(sh, F, kf, kb, p.nu2, s);
   }
 }
 
@@ -643,6 +653,7 @@ size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base,
     Lev32 v;
     v.m = m;
     v.n = n;
+    v.nyn = p->bc == MPFC_BC_NEUMANN_Y;
     v.h = (float)h;
     v.ephi = take(G);
     v.emu = take(G);
@@ -671,7 +682,8 @@ extern "C" int mpfc_fp32_time_smooth(mpfc_t* H, int level, int sweeps, float* ms
     return MPFC_ERR_CUDA;
   }
   if ((e = cudaEventRecord(e0, H->stream)) == cudaSuccess) {
-    sweeps32(H->shape, H->lev32[level], coef32_of(H->coef[0][level]), sweeps, H->stream);
+    sweeps32(H->shape, H->lev32[level], coef32_of(H->coef[0][level]), coef32_of(H->coefb[0][level]), sweeps,
+             H->stream);
     if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(e1, H->stream)) == cudaSuccess &&
         (e = cudaEventSynchronize(e1)) == cudaSuccess)
       e = cudaEventElapsedTime(ms, e0, e1);

@@ -11,6 +11,7 @@
 // FP32 copy of one level for the inner V-cycles of the mixed-precision form.
 struct Lev32 {
   int m, n;
+  int nyn;                   // homogeneous Neumann in y (ghost row = boundary row), 0: periodic
   float h;
   float *ephi, *emu, *eka;   // correction e = (e_phi, e_mu, e_kappa)
   float *r1, *r2, *r3;       // source of the correction equation (restricted defect)

@@ -72,7 +72,7 @@ def test_fp32_inner_mass_conservation(mp):
     assert abs(g.mass() - m0) < 1e-8 * abs(m0)
 
 
-@pytest.mark.parametrize("m,n", [(64, 64), (128, 128), (96, 160)])
+@pytest.mark.parametrize("m,n", [(64, 64), (128, 128), (96, 160), (64, 96)])
 @pytest.mark.parametrize("scheme", [1, 2])
 def test_fp32_tail_is_bitwise_the_per_level_cycle(mp, m, n, scheme):
     """The inner V-cycles' small levels run in one CTA with the levels in shared memory

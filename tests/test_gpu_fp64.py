@@ -147,7 +147,7 @@ def test_prolong(mp, oracle_mod, level):
 
 
 @pytest.mark.parametrize("scheme", [1, 2])
-@pytest.mark.parametrize("m,n,s", [(64, 64, 0.3), (96, 160, 10.0), (128, 32, 0.01), (64, 96, 1.0)])
+@pytest.mark.parametrize("m,n,s", [(64, 64, 0.3), (96, 160, 10.0), (128, 32, 0.01), (64, 96, 1.0), (64, 64, 200.0)])
 def test_coarse_solve(mp, oracle_mod, scheme, m, n, s):
     g = make(mp, m, n, 0.5, s)
     L = g.levels - 1

@@ -208,8 +208,9 @@ def test_mass_and_energy_neumann(mp, oracle_mod):
 
 
 def test_neumann_rejected_where_not_built(mp):
-    """The mixed conditions are an FP64, single-instance feature: other forms refuse them."""
-    bad = [dict(precision=mp.MPFC_FP32_INNER), dict(guess=mp.MPFC_GUESS_LEARNED)]
+    """The mixed conditions are built for single instances with the analytic guesses (FP64
+    and FP32-inner): the learned guess and the batch refuse them."""
+    bad = [dict(guess=mp.MPFC_GUESS_LEARNED)]
     for kw in bad:
         assert mp.workspace_bytes(mp.default_params(m=64, n=64, bc=mp.MPFC_BC_NEUMANN_Y, **kw)) == 0
     assert mp.workspace_bytes(mp.default_params(m=64, n=64, bc=2)) == 0
@@ -218,3 +219,38 @@ def test_neumann_rejected_where_not_built(mp):
     arr = (mp.mpfc_params * 2)(mp.default_params(m=64, n=64, bc=mp.MPFC_BC_NEUMANN_Y),
                                mp.default_params(m=64, n=64, bc=mp.MPFC_BC_NEUMANN_Y))
     assert lib.mpfc_batch_workspace_bytes(2, arr) == 0
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("m,n,h,s,eps", [(64, 64, 0.5, 0.2, 0.025), (96, 160, 804.0 / 2048, 1.0, 0.25)])
+def test_fp32_inner_neumann(mp, oracle_mod, scheme, m, n, h, s, eps):
+    """The mixed-precision form under the Sec. 4.5 conditions: every step within 1e-8 of
+    the oracle's Neumann step solved to 1e-13 (the form's bound on periodic grids), and
+    the FP32 tail of the inner cycles bit for bit the per-level launches."""
+    if m == 96:
+        phi0 = np.full((n, m), 0.285)
+        rng = np.random.default_rng(5)
+        for cx in (16, 48, 80):
+            phi0[0:6, cx - 3:cx + 3] += 0.3 * rng.uniform(-1, 1, (6, 6))
+    else:
+        phi0 = inputs.noise_field(m, n, 0.07, 0.05, 8)
+    g = neu(mp, m, n, h, s, epsilon=eps, precision=mp.MPFC_FP32_INNER)
+    g.set_state(phi0)
+    o = oracle_mod.Solver(oracle_mod.Params(m=m, n=n, h=h, s=s, eps=eps, ny_neumann=1))
+    o.set_state(phi0)
+    for k in range(4):
+        info = g.step(scheme, 1)[0]
+        assert info["status"] == 0 and info["res"] <= 1e-10
+        assert o.step(scheme, tol=1e-13, guess=1)["status"] == 0
+        assert relerr(g.get_state()[0], o.get_state()[0]) <= 1e-8, k
+    runs = []
+    for tail_cells in (0, 32 * 32):
+        a = neu(mp, m, n, h, s, epsilon=eps, precision=mp.MPFC_FP32_INNER)
+        a.set_launch_shape(4, 0, 4 * 152, tail_cells, 1)
+        a.set_state(phi0)
+        infos = a.step(scheme, 3)
+        runs.append(([i["cycles"] for i in infos], a.get_state()))
+        a.close()
+    assert runs[0][0] == runs[1][0]
+    for x, y in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(x, y)
