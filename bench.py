@@ -626,6 +626,18 @@ def run_ours(args):
             "vcycles_per_step": float(np.mean([r["cycles"] for r in rece])),
             "cell_updates_per_s": world * Ke * mE * nE / (mse_ * 1e-3), "steps": Ke}
         se.close()
+        # the same run in the mixed-precision form
+        pe.precision = mpfc.MPFC_FP32_INNER
+        se = mpfc.Solver(pe, stream=stream)
+        se.set_pinning(Wp, target)
+        se.set_state(np.where(inside, slab, liquid))
+        mse32, rece32 = timed_steps(se, Ke, 3, sch=2)
+        mse32 = replicas.job_time_ms(mse32, device="cuda")
+        forms["pinning_strained_crystal"]["fp32_inner"] = {
+            "steps_per_s": world * Ke / (mse32 * 1e-3),
+            "outer_iterations_per_step": float(np.mean([r["cycles"] for r in rece32])),
+            "speedup_vs_fp64": mse_ / mse32}
+        se.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -79,7 +79,8 @@ typedef struct {
   int inner_cycles;  /* MPFC_FP32_INNER: FP32 V-cycles per FP64 outer iteration (0 = 2)   */
   int bc;            /* MPFC_BC_PERIODIC (default) or MPFC_BC_NEUMANN_Y                   */
   int pinning;       /* 1: reserve the pinning weight and target of Sec. 4.6 in the
-                        workspace (mpfc_set_pinning); MPFC_FP64 with PREV/EXTRAP guess only */
+                        workspace (mpfc_set_pinning); PREV/EXTRAP guess only (FP64 or
+                        FP32-inner)                                                      */
   int model;         /* MPFC_MODEL_MPFC (default) or MPFC_MODEL_PFC                        */
 } mpfc_params;
 

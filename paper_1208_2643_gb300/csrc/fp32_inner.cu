@@ -70,7 +70,9 @@ __global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl
     E.r1[t] = fabs(a) < 1.2e-38 ? 0.f : f64_to_f32_rn(a);
     E.r2[t] = fabs(b) < 1.2e-38 ? 0.f : f64_to_f32_rn(b);
     E.r3[t] = fabs(c) < 1.2e-38 ? 0.f : f64_to_f32_rn(c);
-    E.q[t] = f64_to_f32_rn(k.gam + dg_of<SCH>(p, pk));
+    // q = gam + g'(phi), plus the pinning weight (Sec. 4.6, scheme 2: gam -> gam + W)
+    const double wq = (SCH == 2 && L.W) ? L.W[t] : 0.0;
+    E.q[t] = f64_to_f32_rn(k.gam + wq + dg_of<SCH>(p, pk));
     E.ephi[t] = 0.f;
     E.emu[t] = 0.f;
     E.eka[t] = 0.f;

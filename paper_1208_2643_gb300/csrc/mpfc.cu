@@ -82,7 +82,7 @@ static bool params_valid(const mpfc_params* p) {
   if (p->bc != MPFC_BC_PERIODIC && p->bc != MPFC_BC_NEUMANN_Y) return false;
   if (p->pinning != 0 && p->pinning != 1) return false;
   if (p->model != MPFC_MODEL_MPFC && p->model != MPFC_MODEL_PFC) return false;
-  if (p->pinning && (p->precision != MPFC_FP64 || p->guess == MPFC_GUESS_LEARNED)) return false;
+  if (p->pinning && p->guess == MPFC_GUESS_LEARNED) return false;
   // the mixed conditions are built for the FP64 and FP32-inner paths with the analytic guesses
   if (p->bc == MPFC_BC_NEUMANN_Y && p->guess == MPFC_GUESS_LEARNED) return false;
   int L = mpfc_num_levels(p->m, p->n, p->coarsest);

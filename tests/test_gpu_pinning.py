@@ -196,5 +196,33 @@ def test_pinning_rules(mp, setup):
     p.step(2, 2)
     q.step(2, 2)
     assert np.abs(p.get_state()[0] - q.get_state()[0]).max() == 0.0
-    for kw in (dict(precision=mp.MPFC_FP32_INNER), dict(guess=mp.MPFC_GUESS_LEARNED)):
+    for kw in (dict(guess=mp.MPFC_GUESS_LEARNED),):
         assert mp.workspace_bytes(mp.default_params(m=m, n=m, pinning=1, **kw)) == 0
+
+
+def test_fp32_inner_pinned_strained_crystal(mp, oracle_mod):
+    """The mixed-precision form with the pinning term (its FP32 linearisation takes
+    gam + W + g'): each step within 1e-8 of the oracle's pinned step solved to 1e-13."""
+    m, n = 64, 48
+    h = 4 * np.pi / (16 * np.sqrt(3.0))
+    s = 0.025 * h * h
+    eps, Mob, beta = 0.6, 15.0 ** 2, 0.2
+    slab = inputs.one_mode_crystal(m, n, h, 0.395, eps)
+    rows = np.arange(n)[:, None] * np.ones((1, m))
+    inside = (rows >= 8) & (rows < n - 8)
+    phi0 = np.where(inside, slab, 0.57)
+    W = np.zeros((n, m))
+    band = int(round(np.pi / h))
+    W[8:8 + band] = 2.0
+    W[n - 8 - band:n - 8] = 2.0
+    phihat = np.where(inside, inputs.one_mode_crystal(m, n, h, 0.395, eps, shift=0.04 * 2 * np.pi), 0.57)
+    g = pinned(mp, m, n, h, s, W, phihat, epsilon=eps, M=Mob, beta=beta, precision=mp.MPFC_FP32_INNER)
+    g.set_state(phi0)
+    o = oracle_mod.Solver(oracle_mod.Params(m=m, n=n, h=h, s=s, eps=eps, M=Mob, beta=beta))
+    o.set_pinning(W, phihat)
+    o.set_state(phi0)
+    for k in range(4):
+        info = g.step(2, 1)[0]
+        assert info["status"] == 0 and info["res"] <= 1e-10
+        assert o.step(2, tol=1e-13, guess=1)["status"] == 0
+        assert relerr(g.get_state()[0], o.get_state()[0]) <= 1e-8, k
