@@ -705,8 +705,21 @@ __device__ __forceinline__ void resnorm_decide(Ctl* ctl, double res, int mode, c
   if (set_cond) cudaGraphSetConditional(hnd, cond ? 1u : 0u);
 }
 
-// Scaled residual norm at the finest level, and the V-cycle loop decision.
-template <int SCH>
+// Row 1 of the residual alone, r1 = S1 - phi + c Delta_h mu (as in resid_at).
+__device__ __forceinline__ double resid1_at(const Lev& L, const Coef& k, int i, int j) {
+  const int m = L.m;
+  const int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
+  const size_t c = (size_t)j * m + i;
+  const double* mu = L.mu;
+  const double smu = (__ldg(mu + (size_t)j * m + im) + __ldg(mu + (size_t)j * m + ip)) +
+                     (__ldg(mu + (size_t)jm * m + i) + __ldg(mu + (size_t)jp * m + i));
+  return fma(k.cmu, fma(-4.0, __ldg(mu + c), smu), __ldg(L.S1 + c) - __ldg(L.phi + c));
+}
+
+// Scaled residual norm at the finest level, and the V-cycle loop decision.  R1ONLY:
+// right after the initial guess, whose kappa and mu are defined by rows 3 and 2 of
+// N(u) = S (those residuals are rounding, below the norm's resolution), only row 1.
+template <int SCH, bool R1ONLY = false>
 __global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double* partials, int mode,
                                                  cudaGraphConditionalHandle hnd, int set_cond) {
   pdl_enter();
@@ -714,6 +727,11 @@ __global__ void __launch_bounds__(256) k_resnorm(Lev L, Coef k, Ctl* ctl, double
   int G = L.m * L.n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
     int i = t % L.m, j = t / L.m;
+    if (R1ONLY) {
+      const double a = resid1_at(L, k, i, j);
+      v[0] = fma(a, a, v[0]);
+      continue;
+    }
     double a, b, c;
     resid_at<SCH>(L, k, i, j, a, b, c);
     v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));

@@ -581,8 +581,12 @@ static void enqueue_resnorm(mpfc_s* H, int mode, cudaGraphConditionalHandle hnd,
     return;
   }
   int blocks = mpfc_reduce_blocks((size_t)L0.m * L0.n);
-  mpfc_launch(H->shape, k_resnorm<SCH>, dim3(blocks), dim3(256), 0, s, L0, H->coef[SCH - 1][0], H->ctl, H->partials, mode, hnd,
-             set_cond);
+  if (mode == 0)   // right after the initial guess: rows 2 and 3 hold by construction
+    mpfc_launch(H->shape, k_resnorm<SCH, true>, dim3(blocks), dim3(256), 0, s, L0, H->coef[SCH - 1][0], H->ctl,
+                H->partials, mode, hnd, set_cond);
+  else
+    mpfc_launch(H->shape, k_resnorm<SCH>, dim3(blocks), dim3(256), 0, s, L0, H->coef[SCH - 1][0], H->ctl, H->partials,
+                mode, hnd, set_cond);
 }
 
 // Body of the FP64 WHILE node: one V-cycle, then the residual test that sets the

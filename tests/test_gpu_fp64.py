@@ -478,3 +478,22 @@ def test_launch_shape_rules(mp):
     assert h.fp32_time_smooth(0, 2) > 0.0
     with pytest.raises(mp.MPFCError):
         h.fp32_time_smooth(h.levels, 1)
+
+
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_initial_residual_equals_oracle(mp, oracle_mod, scheme):
+    """After the initial guess only row 1 of the residual is evaluated (rows 2 and 3 hold
+    by construction); the reported initial norm equals the oracle's full residual norm
+    after its own guess, step after step, also under the Neumann rule."""
+    for kw, okw in (({}, {}), ({"bc": mp.MPFC_BC_NEUMANN_Y}, {"ny_neumann": 1})):
+        m, n, h, s = 64, 96, 0.5, 0.05
+        phi0 = inputs.noise_field(m, n, 0.07, 0.05, 12)
+        g = mp.Solver(mp.default_params(m=m, n=n, h=h, dt=s, **kw))
+        g.set_state(phi0)
+        o = oracle_mod.Solver(oracle_mod.Params(m=m, n=n, h=h, s=s, **okw))
+        o.set_state(phi0)
+        for k in range(3):
+            ro = o.step(scheme, tol=1e-10, guess=1)
+            rg = g.step_cycles(scheme, ro["cycles"])
+            assert abs(rg["res0"] - ro["res0"]) <= 1e-9 * ro["res0"], (k, rg["res0"], ro["res0"])
+        g.close()
