@@ -18,7 +18,7 @@
  * of App. A, (A.7): phi_{i,0} = phi_{i,1}, phi_{i,n+1} = phi_{i,n}, i.e. a ghost row
  * holds the value of the boundary row next to it.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - smoother: red-black ordering, red = (i+j) even first; one local Newton
  *    linearisation of the cubic per cell visit (App. B.1 offers Newton or Picard;
  *    Picard is kept as an option); the cell update may be under-relaxed,
