@@ -477,7 +477,6 @@ __global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant
       v.r2 = p + 4 * G;
       v.r3 = p + 5 * G;
       v.q = p + 6 * G;
-      v.b1 = v.b2 = v.b3 = nullptr;
       sl[l] = v;
       p += 7 * G;
     }
@@ -664,7 +663,6 @@ size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base,
     v.r2 = take(G);
     v.r3 = take(G);
     v.q = take(G);
-    v.b1 = v.b2 = v.b3 = nullptr;
     if (H && base) H->lev32[l] = v;
     m /= 2;
     n /= 2;

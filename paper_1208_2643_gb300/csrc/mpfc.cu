@@ -10,6 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/mpfc.h"
@@ -422,8 +423,8 @@ static size_t coarse_smem(const Lev& C) {
 // Largest tail cluster this GPU runs: 16 CTAs where a non-portable cluster of that size
 // can be resident (one query, then cached), else the portable 8.
 int mpfc_tail_max_ctas() {
-  static int cached = 0;
-  if (cached) return cached;
+  static std::atomic<int> cached{0};   // 0: not queried yet (concurrent first calls agree)
+  if (int c = cached.load()) return c;
   int best = 8;
   if (cudaFuncSetAttribute(k_tail<1, kLdL2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
       cudaFuncSetAttribute(k_tail<2, kLdL2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
@@ -442,8 +443,8 @@ int mpfc_tail_max_ctas() {
     if (cudaOccupancyMaxActiveClusters(&n, k_tail<1, kLdL2>, &cfg) == cudaSuccess && n > 0) best = 16;
   }
   (void)cudaGetLastError();
-  cached = best;
-  return cached;
+  cached.store(best);
+  return best;
 }
 
 template <int SCH>

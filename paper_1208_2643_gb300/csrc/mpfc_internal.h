@@ -15,7 +15,6 @@ struct Lev32 {
   float h;
   float *ephi, *emu, *eka;   // correction e = (e_phi, e_mu, e_kappa)
   float *r1, *r2, *r3;       // source of the correction equation (restricted defect)
-  float *b1, *b2, *b3;       // unused by the correction scheme (nullptr)
   float* q;                  // gam + g'(phi) of the FP64 iterate, restricted
 };
 
