@@ -9,142 +9,112 @@
 // scheme).  Thread (x, j) visits cell i = 2x + ((j + color) & 1) of colour
 // `color` (0 = red, (i+j) even).  Cells of one colour only read the other colour,
 // so a half sweep is exactly parallel.
+//
+// The cell's 3x3 system (the cubic linearised about the current value p) is solved for
+// the correction d = A^-1 r, with r = S - N(u) the cell's residual at its current values
+// (rows 1 and 3 of N are linear; in row 2 the Newton term q p of the linearisation cancels,
+// leaving g(p)), and u <- u + omega d.  The result is that of solving A x = R and relaxing
+// towards x, but every rounding error, that of the single-precision-seeded reciprocal
+// included, now scales the correction and vanishes with it: the iteration's fixed point is
+// the discrete solution to roundoff at any h.  (Forming kappa from the updated phi through
+// R3 - b3 phi instead put the reciprocal's 2^-44 times (4/h^2)(4 theta/h^2) phi into row 2
+// at the fixed point: a residual floor near 6e-10 at h = 1/16.)
 // ---------------------------------------------------------------------------
 // EDGE: a row next to a Neumann boundary, where the ghost neighbour is the cell's own
 // unknown (App. A, (A.7)): it leaves the neighbour sums and k holds the coefficients
 // of three neighbours.
+struct CellNew {
+  double phi, mu, ka;      // updated values
+  double R1, R3, X2;       // S1 + c h^-2 sum mu, S3 + theta h^-2 sum phi, S2 + h^-2 sum kappa
+  double pk, wv;           // phi^k (scheme 2) and the pinning weight at the cell
+};
+
 template <int SCH, bool EDGE, int LD>
-__device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, int i, int j) {
-  int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
-  size_t c = (size_t)j * m + i;
-  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
-  double* __restrict__ phi = L.phi;
-  double* __restrict__ mu = L.mu;
-  double* __restrict__ ka = L.ka;
+__device__ __forceinline__ CellNew cell_update(const Lev& L, const Coef& k, size_t c, size_t w, size_t e, size_t s,
+                                               size_t nn) {
+  const double* __restrict__ phi = L.phi;
+  const double* __restrict__ mu = L.mu;
+  const double* __restrict__ ka = L.ka;
   // neighbours belong to the other colour: read-only during this launch
   double smu = (ldv<LD>(mu + w) + ldv<LD>(mu + e)) + (ldv<LD>(mu + s) + ldv<LD>(mu + nn));
   double ska = (ldv<LD>(ka + w) + ldv<LD>(ka + e)) + (ldv<LD>(ka + s) + ldv<LD>(ka + nn));
   double sph = (ldv<LD>(phi + w) + ldv<LD>(phi + e)) + (ldv<LD>(phi + s) + ldv<LD>(phi + nn));
-  double p = ldown<LD>(phi + c);
+  const double p = ldown<LD>(phi + c), m0 = ldown<LD>(mu + c), k0 = ldown<LD>(ka + c);
   if (EDGE) {   // the ghost was read as the cell's current value: take it out again
-    smu -= ldown<LD>(mu + c);
-    ska -= ldown<LD>(ka + c);
+    smu -= m0;
+    ska -= k0;
     sph -= p;
   }
-  double R1 = fma(k.cmu, smu, ldv<LD>(L.S1 + c));
-  double R3 = fma(k.th2, sph, ldv<LD>(L.S3 + c));
-  // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
-  // q = g'(p) enters the determinant and the Cramer numerator of mu, and
-  // e = g(p) - g'(p) p the right-hand side of row 2
-  double R2, detw, Qq;   // detw = det / omega
+  CellNew o;
+  o.pk = 0.0;
+  o.wv = 0.0;
+  o.R1 = fma(k.cmu, smu, ldv<LD>(L.S1 + c));
+  o.R3 = fma(k.th2, sph, ldv<LD>(L.S3 + c));
+  o.X2 = fma(k.ih2, ska, ldv<LD>(L.S2 + c));
+  // residual rows: r1 = R1 - phi - a mu, r3 = R3 - b3 phi - kappa,
+  // r2 = S2 + h^-2 sum kappa - mu + g(phi) + (gam + W) phi - b kappa
+  const double r1 = fma(-k.a, m0, o.R1 - p);
+  const double r3 = fma(-k.b3, p, o.R3) - k0;
+  const double x2 = o.X2 - m0;
+  // q = g'(p) (+ W) enters the determinant and the Cramer numerator of mu
+  double r2, detw, Qq;   // detw = det / omega
   if (SCH == 1) {
-    double p2 = p * p;
-    R2 = fma(k.ih2, ska, fma(-2.0, p2 * p, ldv<LD>(L.S2 + c)));   // e = -2 p^3
-    detw = fma(k.a3w, p2, k.D0w);                                   // q = 3 p^2
+    const double p2 = p * p;
+    r2 = fma(-k.b, k0, fma(k.gam, p, fma(p2, p, x2)));   // g = p^3
+    detw = fma(k.a3w, p2, k.D0w);                        // q = 3 p^2
     Qq = fma(3.0, p2, k.Q0);
   } else {
-    double pk = ldv<LD>(L.pk + c);
-    double q = dg_of<2>(p, pk);
-    R2 = fma(k.ih2, ska, ldv<LD>(L.S2 + c) + (g_of<2>(p, pk) - q * p));
-    if (L.W) q += ldv<LD>(L.W + c);   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
+    o.pk = ldv<LD>(L.pk + c);
+    double q = dg_of<2>(p, o.pk);
+    if (L.W) {   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
+      o.wv = ldv<LD>(L.W + c);
+      q += o.wv;
+    }
+    r2 = fma(-k.b, k0, fma(k.gam + o.wv, p, x2 + g_of<2>(p, o.pk)));
     detw = fma(k.aw, q, k.D0w);
     Qq = k.Q0 + q;
   }
-  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]] with t = b R3 - R2:
-  //   phi* = (R1 + a t) / det,  mu* = ((Q0 + q) R1 - t) / det,  kappa* = R3 - b3 phi*;
-  // then u <- (1 - omega) u + omega u*, with wr = omega / det
+  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]] d = r with t = b r3 - r2:
+  //   d_phi = (r1 + a t) / det,  d_mu = ((Q0 + q) r1 - t) / det,  d_kappa = r3 - b3 d_phi;
+  // wr = omega / det carries the relaxation
   const double wr = rcp_nr(detw);
-  const double t = fma(k.b, R3, -R2);
-  const double nphi = fma(k.a, t, R1);
-  const double nmu = fma(Qq, R1, -t);
-  if (k.relax) {
-    double wphi = nphi * wr;
-    double m0 = ldown<LD>(mu + c), k0 = ldown<LD>(ka + c);
-    phi[c] = fma(k.omw, p, wphi);
-    mu[c] = fma(k.omw, m0, nmu * wr);
-    ka[c] = fma(-k.b3, wphi, fma(k.omega, R3, k.omw * k0));
-  } else {
-    double phin = nphi * wr;
-    phi[c] = phin;
-    mu[c] = nmu * wr;
-    ka[c] = fma(-k.b3, phin, R3);
-  }
+  const double t = fma(k.b, r3, -r2);
+  const double dphi = fma(k.a, t, r1) * wr;
+  o.phi = p + dphi;
+  o.mu = fma(fma(Qq, r1, -t), wr, m0);
+  o.ka = fma(-k.b3, dphi, fma(k.omega, r3, k0));
+  return o;
+}
+
+template <int SCH, bool EDGE, int LD>
+__device__ __forceinline__ void smooth_cell_body(const Lev& L, const Coef& k, int i, int j) {
+  const int m = L.m;
+  const int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
+  const size_t c = (size_t)j * m + i;
+  const CellNew o = cell_update<SCH, EDGE, LD>(L, k, c, (size_t)j * m + im, (size_t)j * m + ip, (size_t)jm * m + i,
+                                               (size_t)jp * m + i);
+  L.phi[c] = o.phi;
+  L.mu[c] = o.mu;
+  L.ka[c] = o.ka;
 }
 
 // The same update, also returning the residual of the cell after it (r1^2 + r2^2 + r3^2),
-// for the finest level's last half sweep of a V-cycle (k_smooth_res).
+// for the finest level's last half sweep of a V-cycle (k_smooth_res).  Its neighbours
+// belong to the other colour and did not change, so the residual follows from the new
+// values in registers and the neighbour sums already formed.
 template <int SCH, bool EDGE, int LD>
 __device__ __forceinline__ double smooth_cell_body_res(const Lev& L, const Coef& k, int i, int j) {
-  int m = L.m;
-  int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
-  size_t c = (size_t)j * m + i;
-  size_t w = (size_t)j * m + im, e = (size_t)j * m + ip, s = (size_t)jm * m + i, nn = (size_t)jp * m + i;
-  double* __restrict__ phi = L.phi;
-  double* __restrict__ mu = L.mu;
-  double* __restrict__ ka = L.ka;
-  // neighbours belong to the other colour: read-only during this launch
-  double smu = (ldv<LD>(mu + w) + ldv<LD>(mu + e)) + (ldv<LD>(mu + s) + ldv<LD>(mu + nn));
-  double ska = (ldv<LD>(ka + w) + ldv<LD>(ka + e)) + (ldv<LD>(ka + s) + ldv<LD>(ka + nn));
-  double sph = (ldv<LD>(phi + w) + ldv<LD>(phi + e)) + (ldv<LD>(phi + s) + ldv<LD>(phi + nn));
-  double p = ldown<LD>(phi + c);
-  if (EDGE) {   // the ghost was read as the cell's current value: take it out again
-    smu -= ldown<LD>(mu + c);
-    ska -= ldown<LD>(ka + c);
-    sph -= p;
-  }
-  double R1 = fma(k.cmu, smu, ldv<LD>(L.S1 + c));
-  double R3 = fma(k.th2, sph, ldv<LD>(L.S3 + c));
-  const double s2 = ldv<LD>(L.S2 + c);
-  // local Newton linearisation of the cubic about p: g ~ g(p) + g'(p)(phi - p);
-  // q = g'(p) enters the determinant and the Cramer numerator of mu, and
-  // e = g(p) - g'(p) p the right-hand side of row 2
-  double R2, detw, Qq, pk = 0.0, wv = 0.0;   // detw = det / omega
-  if (SCH == 1) {
-    double p2 = p * p;
-    R2 = fma(k.ih2, ska, fma(-2.0, p2 * p, s2));   // e = -2 p^3
-    detw = fma(k.a3w, p2, k.D0w);                  // q = 3 p^2
-    Qq = fma(3.0, p2, k.Q0);
-  } else {
-    pk = ldv<LD>(L.pk + c);
-    double q = dg_of<2>(p, pk);
-    R2 = fma(k.ih2, ska, s2 + (g_of<2>(p, pk) - q * p));
-    if (L.W) {   // pinning: a pointwise linear term of row 2 (gam -> gam + W)
-      wv = ldv<LD>(L.W + c);
-      q += wv;
-    }
-    detw = fma(k.aw, q, k.D0w);
-    Qq = k.Q0 + q;
-  }
-  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]] with t = b R3 - R2:
-  //   phi* = (R1 + a t) / det,  mu* = ((Q0 + q) R1 - t) / det,  kappa* = R3 - b3 phi*;
-  // then u <- (1 - omega) u + omega u*, with wr = omega / det
-  const double wr = rcp_nr(detw);
-  const double t = fma(k.b, R3, -R2);
-  const double nphi = fma(k.a, t, R1);
-  const double nmu = fma(Qq, R1, -t);
-  double pn, un, vn;
-  if (k.relax) {
-    double wphi = nphi * wr;
-    double m0 = ldown<LD>(mu + c), k0 = ldown<LD>(ka + c);
-    pn = fma(k.omw, p, wphi);
-    un = fma(k.omw, m0, nmu * wr);
-    vn = fma(-k.b3, wphi, fma(k.omega, R3, k.omw * k0));
-  } else {
-    pn = nphi * wr;
-    un = nmu * wr;
-    vn = fma(-k.b3, pn, R3);
-  }
-  phi[c] = pn;
-  mu[c] = un;
-  ka[c] = vn;
-  // the residual S - N(u) of the cell just updated, from the values in registers
-  // (its neighbours belong to the other colour and did not change): r1 = R1 - phi - a mu,
-  // r2 = S2 + h^-2 sum_nb kappa - b kappa - mu + g(phi) + (gam + W) phi,
-  // r3 = R3 - kappa - b3 phi; returns r1^2 + r2^2 + r3^2
-  const double r1 = fma(-k.a, un, R1 - pn);
-  const double r3 = fma(-k.b3, pn, R3 - vn);
-  const double r2 = fma(-k.b, vn, fma(k.ih2, ska, s2) - un) + fma(k.gam + wv, pn, g_of<SCH>(pn, pk));
+  const int m = L.m;
+  const int im = wrapm(i - 1, m), ip = wrapm(i + 1, m), jm = ywrap(j - 1, L.n, L.nyn), jp = ywrap(j + 1, L.n, L.nyn);
+  const size_t c = (size_t)j * m + i;
+  const CellNew o = cell_update<SCH, EDGE, LD>(L, k, c, (size_t)j * m + im, (size_t)j * m + ip, (size_t)jm * m + i,
+                                               (size_t)jp * m + i);
+  L.phi[c] = o.phi;
+  L.mu[c] = o.mu;
+  L.ka[c] = o.ka;
+  const double r1 = fma(-k.a, o.mu, o.R1 - o.phi);
+  const double r3 = fma(-k.b3, o.phi, o.R3 - o.ka);
+  const double r2 = fma(-k.b, o.ka, o.X2 - o.mu) + fma(k.gam + o.wv, o.phi, g_of<SCH>(o.phi, o.pk));
   return fma(r1, r1, fma(r2, r2, r3 * r3));
 }
 

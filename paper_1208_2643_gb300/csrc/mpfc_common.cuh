@@ -91,7 +91,9 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 // f(r) = 1/r - x) from the correctly rounded single-precision reciprocal of x rounded
 // down to single.  The seed's relative error is below 2^-22.4; one step squares it:
 // |r x - 1| < 2^-44 for x in the normal single range.  The smoother's cell solve needs
-// no more: its error only perturbs an iterate, not the fixed point.
+// no more because it scales a correction with it (the correction d = A^-1 r of the
+// cell's residual r), so its error shrinks with the residual and leaves the fixed point
+// alone.
 __device__ __forceinline__ double rcp_nr(double x) {
   double r = f32_to_f64(__frcp_rn(f64_to_f32_trunc(x)));
   return fma(r, fma(-x, r, 1.0), r);
