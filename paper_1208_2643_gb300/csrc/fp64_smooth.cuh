@@ -54,14 +54,17 @@ __device__ __forceinline__ CellNew cell_update(const Lev& L, const Coef& k, size
   // residual rows: r1 = R1 - phi - a mu, r3 = R3 - b3 phi - kappa,
   // r2 = S2 + h^-2 sum kappa - mu + g(phi) + (gam + W) phi - b kappa
   const double r1 = fma(-k.a, m0, o.R1 - p);
-  const double r3 = fma(-k.b3, p, o.R3) - k0;
-  const double x2 = o.X2 - m0;
+  const double y3 = fma(-k.b3, p, o.R3);
+  const double r3 = y3 - k0;
+  // t = b r3 - r2 with the b kappa terms of the two rows cancelled:
+  //   t = b (R3 - b3 p) + mu - (S2 + h^-2 sum kappa) - g(p) - (gam + W) p
+  const double z = fma(k.b, y3, m0 - o.X2);
   // q = g'(p) (+ W) enters the determinant and the Cramer numerator of mu
-  double r2, detw, Qq;   // detw = det / omega
+  double t, detw, Qq;   // detw = det / omega
   if (SCH == 1) {
     const double p2 = p * p;
-    r2 = fma(-k.b, k0, fma(k.gam, p, fma(p2, p, x2)));   // g = p^3
-    detw = fma(k.a3w, p2, k.D0w);                        // q = 3 p^2
+    t = fma(-k.gam, p, fma(-p2, p, z));   // g = p^3
+    detw = fma(k.a3w, p2, k.D0w);         // q = 3 p^2
     Qq = fma(3.0, p2, k.Q0);
   } else {
     o.pk = ldv<LD>(L.pk + c);
@@ -70,15 +73,14 @@ __device__ __forceinline__ CellNew cell_update(const Lev& L, const Coef& k, size
       o.wv = ldv<LD>(L.W + c);
       q += o.wv;
     }
-    r2 = fma(-k.b, k0, fma(k.gam + o.wv, p, x2 + g_of<2>(p, o.pk)));
+    t = fma(-(k.gam + o.wv), p, z - g_of<2>(p, o.pk));
     detw = fma(k.aw, q, k.D0w);
     Qq = k.Q0 + q;
   }
-  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]] d = r with t = b r3 - r2:
+  // Cramer's rule on [[1, a, 0], [-(gam+q), 1, b], [b3, 0, 1]] d = r:
   //   d_phi = (r1 + a t) / det,  d_mu = ((Q0 + q) r1 - t) / det,  d_kappa = r3 - b3 d_phi;
   // wr = omega / det carries the relaxation
   const double wr = rcp_nr(detw);
-  const double t = fma(k.b, r3, -r2);
   const double dphi = fma(k.a, t, r1) * wr;
   o.phi = p + dphi;
   o.mu = fma(fma(Qq, r1, -t), wr, m0);
