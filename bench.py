@@ -103,12 +103,20 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        lines = open(self.path).read().splitlines()
+        os.unlink(self.path)
+        return self.parse(lines)
+
+    @staticmethod
+    def parse(lines):
+        """Median SM clock, maximum clock and the throttle reasons seen in nvidia-smi CSV
+        lines of FIELDS (noheader, nounits)."""
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         rows = []
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) >= 9:
                 rows.append(parts)
-        os.unlink(self.path)
         if not rows:
             return out
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
