@@ -14,11 +14,11 @@
 // the correction d = A^-1 r, with r = S - N(u) the cell's residual at its current values
 // (rows 1 and 3 of N are linear; in row 2 the Newton term q p of the linearisation cancels,
 // leaving g(p)), and u <- u + omega d.  The result is that of solving A x = R and relaxing
-// towards x, but every rounding error, that of the single-precision-seeded reciprocal
-// included, now scales the correction and vanishes with it: the iteration's fixed point is
-// the discrete solution to roundoff at any h.  (Forming kappa from the updated phi through
-// R3 - b3 phi instead put the reciprocal's 2^-44 times (4/h^2)(4 theta/h^2) phi into row 2
-// at the fixed point: a residual floor near 6e-10 at h = 1/16.)
+// towards x, but the single-precision-seeded reciprocal's error now scales the correction
+// and vanishes with it, so the residual floor is the one the evaluation of r itself sets,
+// as in the oracle, at any h.  (Forming kappa from the updated phi through R3 - b3 phi
+// instead put the reciprocal's 2^-44 times (4/h^2)(4 theta/h^2) phi into row 2 at the
+// fixed point: a residual floor near 6e-10 at h = 1/16.)
 // ---------------------------------------------------------------------------
 // EDGE: a row next to a Neumann boundary, where the ghost neighbour is the cell's own
 // unknown (App. A, (A.7)): it leaves the neighbour sums and k holds the coefficients
