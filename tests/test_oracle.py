@@ -308,6 +308,14 @@ def test_table2_first_row(oracle_mod):
     assert abs(d - _golden()[(2, 32)]) <= 1e-4 * _golden()[(2, 32)], d
 
 
+@pytest.mark.slow
+def test_table2_second_row(oracle_mod):
+    """Table 2 (scheme 2, s = 0.05 h): 64 vs 128 cells gives 6.6800e-5 (about 90 s: 800
+    steps at 128^2)."""
+    d = _table_difference(oracle_mod, 2, 64)
+    assert abs(d - _golden()[(2, 64)]) <= 1e-4 * _golden()[(2, 64)], d
+
+
 def test_table1_first_row(oracle_mod):
     """Table 1 (scheme 1, s = 0.025 h^2): 32 vs 64 cells; the paper prints 2.4306e-4.
     This oracle gives 2.5766e-4 (the same reading reproduces Table 2 to five digits);
