@@ -290,7 +290,8 @@ int mpfc_op_source(mpfc_t* h, int scheme, const double* phik, const double* phik
 
 /* `sweeps` nonlinear red-black block Gauss-Seidel sweeps (App. B), red cells
  * ((i+j) even) first; each cell: one local Newton linearisation of the cubic and a
- * 3x3 solve by Cramer's rule, relaxed by omega. */
+ * 3x3 solve by Cramer's rule for the correction of the cell's residual, applied
+ * with relaxation omega (u <- u + omega A^-1 r). */
 int mpfc_op_smooth(mpfc_t* h, int scheme, int level, double* phi, double* mu, double* kappa, const double* S1,
                    const double* S2, const double* S3, const double* phik, int sweeps);
 
