@@ -89,7 +89,9 @@ static bool params_valid(const mpfc_params* p) {
   int L = mpfc_num_levels(p->m, p->n, p->coarsest);
   int mc = p->m >> (L - 1), nc = p->n >> (L - 1);
   if (mc * nc > kMaxCoarseCells) return false;
-  if ((size_t)p->m * (size_t)p->n > ((size_t)1 << 31)) return false;
+  // the kernels index cells and stride their grid loops in 32-bit ints: at most 2^30
+  // cells keeps every index, every cell count and every index-plus-stride below 2^31
+  if ((size_t)p->m * (size_t)p->n > ((size_t)1 << 30)) return false;
   return true;
 }
 

@@ -54,7 +54,8 @@ def test_default_params_and_workspace(lib):
                                 dict(nu1=0, nu2=0), dict(precision=7), dict(guess=9), dict(max_cycles=0),
                                 dict(coarsest=1),
                                 dict(m=2, n=2),                 # below the 4-cell minimum per side
-                                dict(m=65536, n=65536),         # more than 2^31 cells
+                                dict(m=65536, n=65536),         # more than 2^30 cells
+                                dict(m=65536, n=32768),         # 2^31 cells: past the 32-bit index range
                                 dict(m=254, n=254),             # coarsening stops at 127^2 > 64 cells
                                 dict(epsilon=1.5), dict(inner_cycles=65), dict(bc=5), dict(model=3),
                                 dict(pinning=2),
@@ -65,9 +66,10 @@ def test_invalid_params_rejected(lib, kw):
     assert mpfc.workspace_bytes(mpfc.default_params(**kw)) == 0
 
 
-@pytest.mark.parametrize("m,n", [(4, 4), (4, 6), (6, 6), (8, 12), (32768, 32768), (65536, 32768)])
+@pytest.mark.parametrize("m,n", [(4, 4), (4, 6), (6, 6), (8, 12), (32768, 32768), (65536, 16384)])
 def test_smallest_and_largest_grids_accepted(lib, m, n):
-    """A single-level grid (the coarsest solve alone) and grids up to 2^31 cells."""
+    """A single-level grid (the coarsest solve alone) and grids up to 2^30 cells (the kernels
+    index cells in 32-bit ints, and cell index plus grid stride must stay below 2^31)."""
     from paper_1208_2643_gb300 import mpfc
     b = mpfc.workspace_bytes(mpfc.default_params(m=m, n=n))
     assert b >= m * n * 8 * 10
