@@ -1,5 +1,5 @@
-"""Host logic of bench.py that needs no GPU: the clock-record parser and the recorded
-DRAM-traffic lookup."""
+"""Host logic of bench.py that needs no GPU: the clock-record parser, the recorded
+DRAM-traffic lookup and the reference arm (the oracle timed on the host)."""
 import json
 
 import pytest
@@ -42,3 +42,38 @@ def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
     assert bench.traffic_for("other", 1024) is None
     src.write_bytes(b"kernel source v2")
     assert bench.traffic_for("k", 1024) is None
+
+
+def _run_bench(args, env_extra=None):
+    import os
+    import subprocess
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py")] + args, capture_output=True,
+                         text=True, timeout=600, env=env, cwd=bench.ROOT)
+    return out
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`--impl reference` times the oracle on the named workload and prints one JSON line
+    with the contract's keys (here on a 64^2 grid to keep it short)."""
+    out = _run_bench(["--impl", "reference", "--size", "64", "--steps", "2", "--warmup", "1"])
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] >= 1 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["dtype"] == "f64" and d["data"] == "synthetic" and "64x64" in d["config"]["workload"]
+    cpu = d["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] == d["value"] and cpu["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    out = _run_bench(["--impl", "reference", "--size", "64", "--steps", "1", "--warmup", "0"], {"RANK": "1"})
+    assert out.returncode == 0 and not out.stdout.strip()
