@@ -303,9 +303,13 @@ def _golden():
 
 
 def test_table2_first_row(oracle_mod):
-    """Table 2 (scheme 2, s = 0.05 h): 32 vs 64 cells gives 2.5301e-4."""
+    """Table 2 (scheme 2, s = 0.05 h): 32 vs 64 cells gives 2.5301e-4, with (2) as written
+    (beta = 0.9, M = 1); the form that reproduces Table 1 (beta = M = 1/0.9) misses it by
+    5.5 percent, so each table fixes its own reading."""
     d = _table_difference(oracle_mod, 2, 32)
     assert abs(d - _golden()[(2, 32)]) <= 1e-4 * _golden()[(2, 32)], d
+    d_other = _table_difference(oracle_mod, 2, 32, beta=1 / 0.9, M=1 / 0.9)
+    assert abs(d_other - _golden()[(2, 32)]) > 0.03 * _golden()[(2, 32)], d_other
 
 
 @pytest.mark.slow
