@@ -214,19 +214,22 @@ int mpfc_energy(mpfc_t* h, mpfc_energy_t* out);
 int mpfc_set_pinning(mpfc_t* h, const double* weight, const double* target);
 
 /* Mass h^2 sum phi of a caller's device array, without any device allocation and
- * without a handle.  The paper has no counterpart: this is for callers that cannot
- * allocate device memory -- code running while a stream is being captured into a
- * CUDA graph (where cudaMalloc is not allowed), hosts that own all of the GPU's memory
- * through their own pool, and latency-bound loops that cannot afford cudaMalloc's
- * implicit synchronisation -- and that hold only a field, not a solver workspace.
- * Its scratch (8.2 KB of partial sums) is a static array in the library's device
- * image, present on every GPU that loads the library until the process exits.
- * The first call on a device looks up the array's device address (once per device);
- * make that first call before any stream capture.  Every call shares the array, so
- * calls whose kernels overlap on the GPU race: serialise them (one stream, or
- * synchronise between calls).  Grids above 2048 x 2048 cells are rejected with
- * MPFC_ERR_TOO_LARGE.  d_phi: m*n doubles on the current device; out: host.
- * Synchronises `cuda_stream` (a cudaStream_t; NULL = legacy stream). */
+ * without a handle.  The paper has no counterpart.  It serves callers that cannot let
+ * a library allocate device memory and hold only a field, not a solver workspace: an
+ * application whose own memory pool has reserved all of the GPU's memory (a cudaMalloc
+ * would then fail or fragment that pool), or a plug-in whose host forbids device
+ * allocation outside the host's allocator.  Its scratch (8.2 KB: 1024 block partial
+ * sums, a counter and the result) is a static array in the library's device image,
+ * present on every GPU that loads the library until the process exits.  The first
+ * call on a device looks up the array's device address (once per device); make that
+ * first call before any stream capture.  Every call shares the array and starts by
+ * clearing its counter, so calls whose kernels overlap on the GPU race: serialise them
+ * (one stream, or synchronise between calls).  At most 2048 x 2048 = 4 194 304 cells:
+ * larger grids are rejected with MPFC_ERR_TOO_LARGE before anything is launched.
+ * d_phi: m*n doubles on the current device; out: host.  The call waits for
+ * `cuda_stream` (a cudaStream_t; NULL = legacy stream) to finish and copies the sum to
+ * host memory before it returns.  MPFC_ERR_INVALID for null pointers, m or n <= 0 or
+ * h <= 0; MPFC_ERR_CUDA if a CUDA call fails. */
 int mpfc_mass_noalloc(const double* d_phi, int m, int n, double h, void* cuda_stream, double* out);
 
 /* ---------------------------------------------------------------------------

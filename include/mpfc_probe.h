@@ -14,8 +14,8 @@ extern "C" {
 /* Measures the sustained FP64 FMA rate of the current device with a kernel of
  * independent FMA chains on every SM (about 10 ms of work, timed with CUDA events on
  * `cuda_stream`, best of three).  *tflops receives 2 x FMAs per second / 1e12.
- * `d_scratch` is device memory of at least 152*8*256*8 bytes (written).  Returns 0
- * or MPFC_ERR_CUDA. */
+ * `d_scratch` is device memory of at least SMs * 8 * 256 doubles, SMs the device's
+ * multiprocessor count (written).  Returns 0 or MPFC_ERR_CUDA. */
 int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* tflops);
 
 /* Applies the smoother's double-precision reciprocal (one Newton-Raphson step from
@@ -24,9 +24,11 @@ int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* tflops);
 int mpfc_probe_rcp(const double* d_x, double* d_out, int n, void* cuda_stream);
 
 /* Applies the library's integer-pipe binary64 <-> binary32 conversions to n device
- * doubles: d_rn = rounded to nearest even, d_trunc = truncated, d_back = d_rn widened
- * back to binary64.  Inputs must lie in the normal binary32 magnitude range (or be 0).
- * For tests against the hardware conversions.  Asynchronous on `cuda_stream`. */
+ * doubles: d_rn = rounded to nearest even, d_trunc = rounded toward zero, d_back = d_rn
+ * widened back to binary64.  Any input: zero, the normal binary32 range, underflow to
+ * subnormals, overflow, infinities and NaN (the last four through the hardware
+ * conversion).  For tests against the hardware conversions.  Asynchronous on
+ * `cuda_stream`. */
 int mpfc_probe_convert(const double* d_x, float* d_rn, float* d_trunc, double* d_back, int n, void* cuda_stream);
 
 /* Evaluates the convolution kernels' GELU and its derivative (erf by the rational

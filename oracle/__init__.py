@@ -30,15 +30,19 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpfc_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libmpfc_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "libmpfc_oracle_omp.so")
 
 
 def build(force: bool = False) -> str:
     """Compiles the C oracle with gcc (plain -O2, no fast-math, no FMA contraction
-    so the arithmetic follows the source order)."""
+    so the arithmetic follows the source order), once serial and once with OpenMP
+    (the all-cores build: parallel loops over independent cells only, identical
+    bits).  Returns the serial library's path."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared"]
+    for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+            subprocess.run(base + extra + ["-o", lib, _SRC, "-lm"], check=True)
     return _LIB
 
 
@@ -55,49 +59,67 @@ class _Info(ctypes.Structure):
 
 
 _lib = None
+_lib_omp = None
 _D = ctypes.POINTER(ctypes.c_double)
 
 
-def _load():
-    global _lib
+def _load(threaded: bool = False):
+    """The serial library, or with `threaded` the OpenMP build of the same source."""
+    global _lib, _lib_omp
+    if threaded:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(ctypes.CDLL(_LIB_OMP))
+            _lib_omp.orc_set_boundary(_load().orc_get_boundary())
+        return _lib_omp
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        lib.orc_create.restype = ctypes.c_void_p
-        lib.orc_create.argtypes = [ctypes.POINTER(_Params)]
-        lib.orc_destroy.argtypes = [ctypes.c_void_p]
-        lib.orc_levels.argtypes = [ctypes.c_void_p]
-        lib.orc_set_state.argtypes = [ctypes.c_void_p, _D, _D, _D]
-        lib.orc_get_state.argtypes = [ctypes.c_void_p, _D, _D, _D]
-        lib.orc_get_u.argtypes = [ctypes.c_void_p, _D, _D, _D]
-        lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, ctypes.c_double, ctypes.c_int,
-                                 ctypes.c_int, ctypes.POINTER(_Info), _D]
-        lib.orc_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double,
-                                  ctypes.c_int, _D, _D]
-        lib.orc_laplacian.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
-        lib.orc_apply_N.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                    ctypes.c_int, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
-        lib.orc_residual.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_int, ctypes.c_int, ctypes.c_double] + [_D] * 10
-        lib.orc_source.argtypes = [ctypes.c_int, ctypes.POINTER(_Params), _D, _D, _D, _D, _D, _D]
-        lib.orc_smooth.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                   ctypes.c_double] + [_D] * 7
-        lib.orc_restrict.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
-        lib.orc_prolong_add.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
-        lib.orc_cramer3.argtypes = [_D, _D, _D]
-        lib.orc_gauss_solve.argtypes = [ctypes.c_int, _D, _D, _D]
-        lib.orc_coarse_newton.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                          ctypes.c_int, ctypes.c_int, ctypes.c_double] + [_D] * 7
-        lib.orc_scheme_consts.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, _D, _D, _D]
-        lib.orc_num_levels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
-        lib.orc_set_boundary.argtypes = [ctypes.c_int]
-        lib.orc_set_pinning.argtypes = [ctypes.c_void_p, _D, _D]
-        lib.orc_apply_N_pinned.argtypes = lib.orc_apply_N.argtypes[:11] + [_D, _D, _D, _D]
-        lib.orc_smooth_pinned.argtypes = lib.orc_smooth.argtypes + [_D]
-        lib.orc_coarse_newton_pinned.argtypes = lib.orc_coarse_newton.argtypes + [_D]
-        lib.orc_source_pinned.argtypes = [ctypes.c_int, ctypes.POINTER(_Params), _D, _D, _D, _D, _D, _D, _D, _D]
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Sets the OpenMP build's thread count (n > 0) and returns the count it uses."""
+    return int(_load(True).orc_set_threads(n))
+
+
+def _declare(lib):
+    """Argument types of the oracle library's entry points."""
+    lib.orc_create.restype = ctypes.c_void_p
+    lib.orc_create.argtypes = [ctypes.POINTER(_Params)]
+    lib.orc_destroy.argtypes = [ctypes.c_void_p]
+    lib.orc_levels.argtypes = [ctypes.c_void_p]
+    lib.orc_set_state.argtypes = [ctypes.c_void_p, _D, _D, _D]
+    lib.orc_get_state.argtypes = [ctypes.c_void_p, _D, _D, _D]
+    lib.orc_get_u.argtypes = [ctypes.c_void_p, _D, _D, _D]
+    lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_int, ctypes.POINTER(_Info), _D]
+    lib.orc_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double,
+                              ctypes.c_int, _D, _D]
+    lib.orc_laplacian.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+    lib.orc_apply_N.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_double, _D, _D, _D, _D, _D, _D, _D]
+    lib.orc_residual.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_double] + [_D] * 10
+    lib.orc_source.argtypes = [ctypes.c_int, ctypes.POINTER(_Params), _D, _D, _D, _D, _D, _D]
+    lib.orc_smooth.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_double] + [_D] * 7
+    lib.orc_restrict.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+    lib.orc_prolong_add.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+    lib.orc_cramer3.argtypes = [_D, _D, _D]
+    lib.orc_gauss_solve.argtypes = [ctypes.c_int, _D, _D, _D]
+    lib.orc_coarse_newton.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_double] + [_D] * 7
+    lib.orc_scheme_consts.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, _D, _D, _D]
+    lib.orc_num_levels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.orc_set_boundary.argtypes = [ctypes.c_int]
+    lib.orc_set_pinning.argtypes = [ctypes.c_void_p, _D, _D]
+    lib.orc_apply_N_pinned.argtypes = lib.orc_apply_N.argtypes[:11] + [_D, _D, _D, _D]
+    lib.orc_smooth_pinned.argtypes = lib.orc_smooth.argtypes + [_D]
+    lib.orc_coarse_newton_pinned.argtypes = lib.orc_coarse_newton.argtypes + [_D]
+    lib.orc_source_pinned.argtypes = [ctypes.c_int, ctypes.POINTER(_Params), _D, _D, _D, _D, _D, _D, _D, _D]
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
+    return lib
 
 
 def _p(a):
@@ -116,6 +138,8 @@ def set_boundary(ny_neumann: bool) -> None:
     """Boundary rule of every following call: periodic (App. A, (A.8)-(A.9)), or with
     ny_neumann periodic in x and homogeneous Neumann in y ((A.7), Sec. 4.5)."""
     _load().orc_set_boundary(1 if ny_neumann else 0)
+    if _lib_omp is not None:
+        _lib_omp.orc_set_boundary(1 if ny_neumann else 0)
 
 
 class boundary:
@@ -276,9 +300,11 @@ GUESS_PREV, GUESS_EXTRAP, GUESS_GIVEN = 0, 1, 2
 class Solver:
     """Time stepper of Sec. 3.1 (scheme 1) / Sec. 3.2 (scheme 2) with the FAS solver."""
 
-    def __init__(self, p: Params):
+    def __init__(self, p: Params, threaded: bool = False):
+        """threaded: run on the OpenMP build (all host cores unless threads() says
+        otherwise); its results are bitwise those of the serial build."""
         self.p = p
-        self._lib = _load()
+        self._lib = _load(threaded)
         self._ctx = self._lib.orc_create(ctypes.byref(p.c_struct()))
         if not self._ctx:
             raise ValueError("invalid grid size")

@@ -1,6 +1,8 @@
 /*
- * mpfc_oracle.c -- plain, slow, serial FP64 CPU oracle of the MPFC convex-splitting
- * schemes and their nonlinear FAS multigrid solver.
+ * mpfc_oracle.c -- plain, slow FP64 CPU oracle of the MPFC convex-splitting schemes
+ * and their nonlinear FAS multigrid solver.  Built twice from this one source: serial,
+ * and with OpenMP over the host cores, which parallelises only loops over independent
+ * cells and keeps every reduction serial, so the two builds give identical bits.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or calls
  * this file; only the tests, the smoke check and the CPU-baseline leg of the
@@ -49,8 +51,31 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAX_LEVELS 16
+
+/* All-cores build (compiled with -fopenmp; the serial build ignores the pragmas):
+ * only loops whose iterations write disjoint cells and read nothing another iteration
+ * writes run in parallel -- the cells of one colour in a smoothing half sweep, the
+ * cells of an operator application, of a source, of a transfer.  Every reduction (the
+ * residual norm) stays serial in the serial order, so both builds give the same bits.
+ * Grids below ORC_OMP_CELLS cells stay serial (thread start-up would dominate). */
+#define ORC_OMP_CELLS 4096
+
+/* Threads of the parallel loops (OpenMP build); returns the number in use, 1 in the
+ * serial build. */
+int orc_set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  return omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Parameters                                                               */
@@ -103,6 +128,7 @@ static orc_consts consts_of(const orc_params* p, int scheme) {
 static int g_ny_neumann = 0;   /* 0: periodic in y (A.9); 1: homogeneous Neumann in y (A.7) */
 
 void orc_set_boundary(int ny_neumann) { g_ny_neumann = ny_neumann ? 1 : 0; }
+int orc_get_boundary(void) { return g_ny_neumann; }
 
 static int wrap(int i, int m) { return (i % m + m) % m; }
 
@@ -137,6 +163,7 @@ static double real_nb_sum(const double* f, int m, int n, int i, int j, int* coun
 /* Standard five-point discrete Laplacian Delta_h (App. A) with the ghost
  * values of the boundary rule (periodic (A.8)-(A.9), or (A.7) in y). */
 void orc_laplacian(int m, int n, double h, const double* f, double* out) {
+#pragma omp parallel for schedule(static) if (m * n >= ORC_OMP_CELLS)
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < m; ++i)
       out[j * m + i] = (nb_sum(f, m, n, i, j) - 4.0 * f[j * m + i]) / (h * h);
@@ -175,6 +202,7 @@ static void apply_N_w(int scheme, double c, double gam, double theta, int m, int
   orc_laplacian(m, n, h, mu, lmu);
   orc_laplacian(m, n, h, kappa, lka);
   orc_laplacian(m, n, h, phi, lph);
+#pragma omp parallel for schedule(static) if (m * n >= ORC_OMP_CELLS)
   for (int k = 0; k < m * n; ++k) {
     double pk = (scheme == 2) ? phik[k] : 0.0;
     N1[k] = phi[k] - c * lmu[k];
@@ -216,6 +244,7 @@ static void source_w(int scheme, const orc_params* p, const double* phik, const 
   double* lap = malloc(sizeof(double) * N);
   if (scheme == 1) {
     orc_laplacian(m, n, p->h, phik, lap);
+#pragma omp parallel for schedule(static) if (N >= ORC_OMP_CELLS)
     for (int k = 0; k < N; ++k) {
       S1[k] = phik[k] + (p->model == 1 ? 0.0 : psik[k] / (p->beta + 1.0 / p->s));
       S2[k] = 2.0 * lap[k];
@@ -227,6 +256,7 @@ static void source_w(int scheme, const orc_params* p, const double* phik, const 
     for (int k = 0; k < N; ++k) tl[k] = 0.5 * (3.0 * phik[k] - phikm1[k]);
     orc_laplacian(m, n, p->h, tl, lap_t);
     orc_laplacian(m, n, p->h, phik, lap);
+#pragma omp parallel for schedule(static) if (N >= ORC_OMP_CELLS)
     for (int k = 0; k < N; ++k) {
       S1[k] = phik[k] + (p->model == 1 ? 0.0 : 2.0 * psik[k] / (p->beta + 2.0 / p->s));
       S2[k] = 0.5 * alpha * phik[k] + 2.0 * lap_t[k];
@@ -313,11 +343,14 @@ static void smooth_w(int scheme, double c, double gam, double theta, int newton,
                      const double* S3, const double* phik, const double* W) {
   orc_consts k = {c, gam, theta, scheme, omega};
   for (int sw = 0; sw < sweeps; ++sw)
-    for (int color = 0; color < 2; ++color)
+    for (int color = 0; color < 2; ++color) {
+      /* the cells of one colour only read the other colour's values: any order */
+#pragma omp parallel for schedule(static) if (m * n >= ORC_OMP_CELLS)
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < m; ++i)
           if (((i + j) & 1) == color)
             visit_cell(&k, newton, m, n, h, i, j, phi, mu, kappa, S1, S2, S3, phik, W);
+    }
 }
 
 void orc_smooth(int scheme, double c, double gam, double theta, int newton, double omega, int sweeps, int m,
@@ -332,6 +365,7 @@ void orc_smooth(int scheme, double c, double gam, double theta, int newton, doub
 /* Restriction: coarse cell = average of its 2x2 fine children. */
 void orc_restrict(int mc, int nc, const double* fine, double* coarse) {
   int mf = 2 * mc;
+#pragma omp parallel for schedule(static) if (4 * mc * nc >= ORC_OMP_CELLS)
   for (int J = 0; J < nc; ++J)
     for (int I = 0; I < mc; ++I)
       coarse[J * mc + I] = 0.25 * (fine[(2 * J) * mf + 2 * I] + fine[(2 * J) * mf + 2 * I + 1] +
@@ -344,6 +378,7 @@ void orc_restrict(int mc, int nc, const double* fine, double* coarse) {
  * weights 9/16 (parent), 3/16, 3/16 (face neighbours), 1/16 (diagonal). */
 void orc_prolong_add(int mc, int nc, const double* coarse, double* fine) {
   int mf = 2 * mc, nf = 2 * nc;
+#pragma omp parallel for schedule(static) if (mf * nf >= ORC_OMP_CELLS)
   for (int j = 0; j < nf; ++j)
     for (int i = 0; i < mf; ++i) {
       int I = i / 2, J = j / 2;
@@ -557,6 +592,7 @@ static void level_residual(const orc_consts* k, orc_level* L) {
   int G = L->m * L->n;
   apply_N_w(k->scheme, k->c, k->gam, k->theta, L->m, L->n, L->h, L->phi, L->mu, L->kappa, L->phik, L->W,
             L->r1, L->r2, L->r3);
+#pragma omp parallel for schedule(static) if (G >= ORC_OMP_CELLS)
   for (int i = 0; i < G; ++i) {
     L->r1[i] = L->S1[i] - L->r1[i];
     L->r2[i] = L->S2[i] - L->r2[i];
@@ -673,6 +709,7 @@ static void initial_guess(orc_ctx* ctx, const orc_consts* k, int guess, const do
   orc_laplacian(L->m, L->n, L->h, L->phi, lap);
   for (int i = 0; i < G; ++i) L->kappa[i] = L->S3[i] + k->theta * lap[i];
   orc_laplacian(L->m, L->n, L->h, L->kappa, lap);
+#pragma omp parallel for schedule(static) if (G >= ORC_OMP_CELLS)
   for (int i = 0; i < G; ++i) {
     double pk = (k->scheme == 2) ? L->phik[i] : 0.0;
     L->mu[i] = L->S2[i] + g_of(k->scheme, L->phi[i], pk) + k->gam * L->phi[i] + lap[i];

@@ -35,7 +35,7 @@ struct BGlobal {
   double tol;
 };
 
-constexpr int kPersistentBlocks = 152 * 8;
+constexpr int kBlocksPerSM = 8;   // persistent launches: this many blocks per SM
 
 // Sum over a block of any shape (linear thread index); the total is valid in thread 0.
 __device__ __forceinline__ double block_total2d(double v, double* red) {
@@ -53,7 +53,7 @@ __device__ __forceinline__ double block_total2d(double v, double* red) {
   return x;
 }
 
-int grid_for_items(int n) { return std::max(1, std::min(n, kPersistentBlocks)); }
+int grid_for_items(int n) { return std::max(1, std::min(n, kBlocksPerSM * mpfc::sm_count())); }
 
 // ---------------------------------------------------------------------------
 // Batched kernels (grid-stride over work items; one item = one tile of one level of
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) kb_resnorm(const BItem* __restrict__ item
         if (!c.halted) {
           c.res0 = res;
           c.res = res;
-          if (!(res == res)) c.status = 2;
+          if (!(res == res) || isinf(res)) c.status = 2;
         }
       } else if (c.active) {
         c.res = res;
@@ -356,6 +356,18 @@ namespace {
     cudaError_t err_ = (call);                                \
     if (err_ != cudaSuccess) {                                \
       mpfc_set_cuda_error(err_, #call, __FILE__, __LINE__);   \
+      return MPFC_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
+// As BCK, inside a stream capture: an error first ends the capture on `stream`, so
+// that the stream is not left capturing (mpfc_abort_capture).
+#define BCKCAP(call, stream, owned)                           \
+  do {                                                        \
+    cudaError_t err_ = (call);                                \
+    if (err_ != cudaSuccess) {                                \
+      mpfc_set_cuda_error(err_, #call, __FILE__, __LINE__);   \
+      mpfc_abort_capture((stream), (owned));                  \
       return MPFC_ERR_CUDA;                                   \
     }                                                         \
   } while (0)
@@ -623,30 +635,41 @@ int build_batch_graph(mpfc_batch_s* B) {
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  BCK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps));
+  BCKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs, true);
   cudaGraphConditionalHandle hnd;
-  BCK(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0));
+  BCKCAP(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0), cs, true);
   enqueue_batch_prologue<SCH>(B, cs);
   enqueue_batch_resnorm<SCH>(B, 0, hnd, 1, cs);
-  BCK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps));
+  BCKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs, true);
   std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
   cp.conditional.handle = hnd;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t cnode;
-  BCK(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp));
+  BCKCAP(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp), cs, true);
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  BCK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-  BCK(cudaStreamBeginCaptureToGraph(B->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  BCKCAP(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies), cs, true);
+  BCKCAP(cudaStreamBeginCaptureToGraph(B->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), cs,
+         true);
   enqueue_batch_vcycle<SCH>(B, B->body);
   enqueue_batch_resnorm<SCH>(B, 1, hnd, 1, B->body);
-  BCK(cudaStreamEndCapture(B->body, &body));
+  cudaError_t e = cudaStreamEndCapture(B->body, &body);
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "cudaStreamEndCapture(batch WHILE body)", __FILE__, __LINE__);
+    mpfc_abort_capture(B->body, false);
+    mpfc_abort_capture(cs, true);
+    return MPFC_ERR_CUDA;
+  }
   enqueue_batch_commit<SCH>(B, cs);
   BCK(cudaStreamEndCapture(cs, &graph));
   cudaGraphExec_t exec;
-  BCK(cudaGraphInstantiate(&exec, graph, 0));
-  BCK(cudaGraphDestroy(graph));
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "cudaGraphInstantiate(batch step graph)", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
   B->exec[SCH - 1] = exec;
   return MPFC_OK;
 }

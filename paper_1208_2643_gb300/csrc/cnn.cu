@@ -306,7 +306,8 @@ int launch_conv(const ConvArgs& A, cudaStream_t s) {
     return mpfc_cnn_conv_tc(A.x, A.B, A.H, A.W, A.wk, A.bias, A.cout, A.cout_p, A.mode, A.y_bf16, A.y_f32, A.z_f32,
                             A.phi0, A.scale, s);
   long long ntiles = (long long)((A.W + kTW - 1) / kTW) * ((A.H + kTH - 1) / kTH) * A.B;
-  int grid = (int)(ntiles < 152 * 6 ? ntiles : 152 * 6);
+  const long long cap = 6LL * mpfc::sm_count();
+  int grid = (int)(ntiles < cap ? ntiles : cap);
   size_t sm = conv_smem(A.cin_p, A.cout_p, A.kpad);
   if (sm > 48 * 1024) {
     static bool raised = false;
@@ -388,7 +389,7 @@ extern "C" int mpfc_cnn_features(const double* phik, const double* phikm1, const
   double* part = means + B;
   k_mean_partial<<<dim3(kMeanBlocks, B), 256, 0, s>>>(phik, G, part);
   k_mean_final<<<B, 32, 0, s>>>(part, G, means);
-  const long long per = (G + 255) / 256, cap = (152 * 16 + B - 1) / B;
+  const long long per = (G + 255) / 256, cap = (16LL * mpfc::sm_count() + B - 1) / B;
   const dim3 grid((unsigned)(per < cap ? per : cap), (unsigned)B);
   k_features<<<grid, 256, 0, s>>>(phik, phikm1, phikm2, phikp1, G, norms, means, (__nv_bfloat16*)x_bf16, y_f32);
   return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;

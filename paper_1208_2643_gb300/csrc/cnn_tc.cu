@@ -517,7 +517,8 @@ int launch_tc(const CUtensorMap& map, const TcArgs& A, cudaStream_t s) {
     attr = true;
   }
   const long long ntiles = (long long)A.B * A.H * (A.W / kTM);
-  const int grid = (int)(ntiles < 152 ? ntiles : 152);   // persistent: one CTA per SM
+  const long long sms = mpfc::sm_count();
+  const int grid = (int)(ntiles < sms ? ntiles : sms);   // persistent: one CTA per SM
   k_conv3x3_tc<NB><<<grid, kThreads, kSmem, s>>>(map, A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

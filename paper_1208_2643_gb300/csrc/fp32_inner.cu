@@ -65,11 +65,11 @@ __global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl
     v[0] = fma(a, a, fma(b, b, fma(c, c, v[0])));
     double p = L.phi[t];
     double pk = (SCH == 2) ? L.pk[t] : 0.0;
-    // defect and linearisation handed to the FP32 solve (zero stays zero; values below
-    // 2^-126 in magnitude are far under the FP32 solve's resolution of the defect)
-    E.r1[t] = fabs(a) < 1.2e-38 ? 0.f : f64_to_f32_rn(a);
-    E.r2[t] = fabs(b) < 1.2e-38 ? 0.f : f64_to_f32_rn(b);
-    E.r3[t] = fabs(c) < 1.2e-38 ? 0.f : f64_to_f32_rn(c);
+    // defect and linearisation handed to the FP32 solve, rounded to nearest (a
+    // non-finite defect stays non-finite, so the residual test above sees it)
+    E.r1[t] = f64_to_f32_rn(a);
+    E.r2[t] = f64_to_f32_rn(b);
+    E.r3[t] = f64_to_f32_rn(c);
     // q = gam + g'(phi), plus the pinning weight (Sec. 4.6, scheme 2: gam -> gam + W)
     const double wq = (SCH == 2 && L.W) ? L.W[t] : 0.0;
     E.q[t] = f64_to_f32_rn(k.gam + wq + dg_of<SCH>(p, pk));
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_defect(Lev L, Coef k, Lev32 E, Ctl* ctl
     ctl->res = res;
     ctl->cycles = 0;
     ctl->status = 0;
-    if (!(res == res)) ctl->status = 2;
+    if (!(res == res) || isinf(res)) ctl->status = 2;
   } else {
     ctl->res = res;
     ctl->cycles += 1;
@@ -103,9 +103,9 @@ __global__ void k_update(Lev L, Lev32 E) {
   int G = L.m * L.n;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < G; t += gridDim.x * blockDim.x) {
     float a = E.ephi[t], b = E.emu[t], c = E.eka[t];
-    L.phi[t] += fabsf(a) < 1.2e-38f ? 0.0 : f32_to_f64(a);
-    L.mu[t] += fabsf(b) < 1.2e-38f ? 0.0 : f32_to_f64(b);
-    L.ka[t] += fabsf(c) < 1.2e-38f ? 0.0 : f32_to_f64(c);
+    L.phi[t] += f32_to_f64(a);
+    L.mu[t] += f32_to_f64(b);
+    L.ka[t] += f32_to_f64(c);
   }
 }
 

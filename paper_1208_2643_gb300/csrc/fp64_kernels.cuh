@@ -701,7 +701,7 @@ __device__ __forceinline__ void resnorm_decide(Ctl* ctl, double res, int mode, c
   if (ctl->skip || ctl->status != 0) cond = 0;
   else if (ctl->fixed_cycles > 0) cond = ctl->cycles < ctl->fixed_cycles;
   else cond = (res > ctl->tol) && (ctl->cycles < ctl->max_cycles);
-  if (mode == 0 && !(res == res)) { ctl->status = 2; cond = 0; }
+  if (mode == 0 && (!(res == res) || isinf(res))) { ctl->status = 2; cond = 0; }
   if (set_cond) cudaGraphSetConditional(hnd, cond ? 1u : 0u);
 }
 

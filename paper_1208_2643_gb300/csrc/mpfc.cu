@@ -28,7 +28,37 @@ using namespace mpfc;
     }                                                         \
   } while (0)
 
+// As CK, inside a stream capture: an error first ends the capture on `stream` (see
+// mpfc_abort_capture), so that the caller's stream is not left capturing.
+#define CKCAP(call, stream, owned)                            \
+  do {                                                        \
+    cudaError_t err_ = (call);                                \
+    if (err_ != cudaSuccess) {                                \
+      mpfc_set_cuda_error(err_, #call, __FILE__, __LINE__);   \
+      mpfc_abort_capture((stream), (owned));                  \
+      return MPFC_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
 static char g_last_cuda_error[512];
+
+namespace mpfc {
+int sm_count() {
+  constexpr int kDevs = 64;
+  static std::atomic<int> cache[kDevs];   // 0: not queried yet
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev < kDevs)
+    if (int c = cache[dev].load()) return c;
+  int c = 0;
+  if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1) {
+    (void)cudaGetLastError();
+    return 1;   // grids stay correct (every sized kernel strides over its work), only smaller
+  }
+  if (dev < kDevs) cache[dev].store(c);
+  return c;
+}
+}  // namespace mpfc
 
 void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
@@ -262,7 +292,7 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
 }
 
 // Default launch shapes, from interleaved timings on GB300 (V-cycle at 1024^2):
-//   FP64: one-warp blocks everywhere and programmatic launch for grids of at most 4 x 152
+//   FP64: one-warp blocks everywhere and programmatic launch for grids of at most 4 x SMs
 //     blocks, 743 us per V-cycle, against 822 with 32 x 8 blocks and no programmatic
 //     launch; programmatic launch of the large grids too was slower (779);
 //   FP32 inner cycles (memory-latency bound, they want occupancy): 32 x 4 blocks and the
@@ -275,8 +305,9 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
 //   the FP32 inner cycles' levels of at most 32 x 32 cells in one CTA with the levels in
 //     shared memory: 430 us per outer iteration at 1024^2 against 475 (64 x 64: 457).
 mpfc_launch_shape mpfc_default_launch_shape(int precision) {
-  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * 152, 32 * 32, 1};
-  return mpfc_launch_shape{1, 0, 4 * 152, 256, 1};
+  const int pdl = 4 * mpfc::sm_count();
+  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, pdl, 32 * 32, 1};
+  return mpfc_launch_shape{1, 0, pdl, 256, 1};
 }
 
 // The coarsest grid's matrices for one scheme as the FP32 block the coarse solves read:
@@ -569,7 +600,7 @@ template <int SCH>
 static void enqueue_commit(mpfc_s* H, cudaStream_t s) {
   size_t G = (size_t)H->p.m * H->p.n;
   int blocks = (int)((G + 255) / 256);
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > 16 * mpfc::sm_count()) blocks = 16 * mpfc::sm_count();
   mpfc_launch(H->shape, k_commit<SCH>, dim3(blocks), dim3(256), 0, s, (const double*)H->lev[0].phi, H->phik, H->phikm1, H->psik,
              H->guess.phikm2, (int)G, 1.0 / H->p.dt, (int)(H->p.model == MPFC_MODEL_PFC), H->ctl, H->info);
 }
@@ -616,25 +647,46 @@ static int build_step_graph(mpfc_s* H) {
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  CK(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps));
-  CK(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0));
+  CKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs, true);
+  CKCAP(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0), cs, true);
   H->cur_handle = hnd;
+  int rc;
   if (H->p.precision == MPFC_FP32_INNER) {
-    int rc = mpfc_fp32_enqueue_step(H, SCH, cs, hnd);
-    if (rc != MPFC_OK) return rc;
+    rc = mpfc_fp32_enqueue_step(H, SCH, cs, hnd);
   } else {
     enqueue_prologue<SCH>(H, cs);
     enqueue_resnorm<SCH>(H, 0, hnd, 1, cs);
-    int rc = mpfc_capture_while(H, cs, hnd, &fp64_body, SCH);
-    if (rc != MPFC_OK) return rc;
-    enqueue_commit<SCH>(H, cs);
+    rc = mpfc_capture_while(H, cs, hnd, &fp64_body, SCH);
+    if (rc == MPFC_OK) enqueue_commit<SCH>(H, cs);
+  }
+  if (rc != MPFC_OK) {
+    mpfc_abort_capture(cs, true);
+    return rc;
   }
   CK(cudaStreamEndCapture(cs, &graph));
   cudaGraphExec_t exec;
-  CK(cudaGraphInstantiate(&exec, graph, 0));
-  CK(cudaGraphDestroy(graph));
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "cudaGraphInstantiate(step graph)", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
   H->exec[SCH - 1][0] = exec;
   return MPFC_OK;
+}
+
+// Ends a capture on s that an error interrupted, so that the stream can be used again,
+// and destroys the partial graph when it is the capture's own (`owned`; a capture into
+// an existing graph, such as a conditional node's body, leaves that graph to its owner).
+void mpfc_abort_capture(cudaStream_t s, bool owned) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess || st == cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return;
+  }
+  cudaGraph_t g = nullptr;
+  if (cudaStreamEndCapture(s, &g) == cudaSuccess && g && owned) cudaGraphDestroy(g);
+  (void)cudaGetLastError();   // the invalidated capture's error is reported by the caller
 }
 
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd, void (*body_fn)(mpfc_s*, int, cudaStream_t),
@@ -655,7 +707,7 @@ int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hn
   CK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
   CK(cudaStreamBeginCaptureToGraph(H->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   body_fn(H, scheme, H->body_stream);
-  CK(cudaStreamEndCapture(H->body_stream, &body));
+  CKCAP(cudaStreamEndCapture(H->body_stream, &body), H->body_stream, false);
   return MPFC_OK;
 }
 

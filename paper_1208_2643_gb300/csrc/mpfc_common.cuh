@@ -6,6 +6,10 @@
 
 namespace mpfc {
 
+// Streaming multiprocessors of the current device (queried once per device), for the
+// grids sized to the GPU: persistent kernels run one CTA (or a few) per SM.
+int sm_count();
+
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarseCells = 64;    // coarsest level solved by dense Newton in one CTA
 constexpr int kMaxPartials = 1024;     // blocks of a deterministic two-pass reduction
@@ -50,16 +54,24 @@ struct Coef {
 
 // Conversions between binary64 and binary32 done with integer operations on the IEEE
 // 754 bit fields (sign, biased exponent, significand), so that they run on the integer
-// pipes instead of GB300's narrow FP64 pipe.  Valid for values whose magnitude lies in
-// the normal binary32 range [2^-126, 2^128); the callers use them only there (the
-// tests check them against the hardware conversions on that range).
-//   f64_to_f32_trunc: significand truncated to 23 bits (relative error < 2^-23);
-//   f64_to_f32_rn:    rounded to nearest, ties to even (equal to the IEEE conversion);
+// pipes instead of GB300's narrow FP64 pipe.  The bit arithmetic covers magnitudes in
+// the normal binary32 range [2^-126, 2^128) and zero; every other input (binary32
+// subnormals and underflow, overflow, infinities, NaN) takes the hardware conversion
+// instead, so each function equals its IEEE counterpart for every input (the tests
+// check them against the hardware conversions, special values included).  One
+// unsigned range test on the exponent selects the rare branch.
+//   f64_to_f32_trunc: rounded toward zero (relative error < 2^-23);
+//   f64_to_f32_rn:    rounded to nearest, ties to even;
 //   f32_to_f64:       exact.
 __device__ __forceinline__ float f64_to_f32_trunc(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   unsigned int hi = (unsigned int)(b >> 32);
-  unsigned int e = ((hi >> 20) & 0x7FFu) - 1023u + 127u;
+  unsigned int eb = (hi >> 20) & 0x7FFu;                 // binary64 biased exponent
+  if (eb - (1023u - 126u) >= 254u) {                     // outside [2^-126, 2^128)
+    if ((b << 1) == 0ull) return __uint_as_float(hi & 0x80000000u);
+    return __double2float_rz(x);
+  }
+  unsigned int e = eb - 1023u + 127u;
   unsigned int f = (hi & 0x80000000u) | (e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFull);
   return __uint_as_float(f);
 }
@@ -67,10 +79,15 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
   unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-  if (mag == 0ull) return __uint_as_float(sign);
+  unsigned int eb = (unsigned int)(mag >> 52);
+  if (eb - (1023u - 126u) >= 254u) {                     // outside [2^-126, 2^128)
+    if (mag == 0ull) return __uint_as_float(sign);
+    return __double2float_rn(x);
+  }
   // binary32 magnitude bits with the exponent re-biased and the significand cut to 23
   // bits, then round to nearest even on the 29 dropped bits (a carry into the exponent
-  // field is the correct result of rounding up a significand of all ones)
+  // field is the correct result of rounding up a significand of all ones, up to
+  // infinity past the largest finite binary32)
   unsigned long long keep = (mag >> 29) - ((unsigned long long)(1023 - 127) << 23);
   unsigned long long rest = mag & 0x1FFFFFFFull;
   unsigned long long half = 0x10000000ull;
@@ -79,11 +96,14 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 }
 __device__ __forceinline__ double f32_to_f64(float f) {
   unsigned int u = __float_as_uint(f);
-  unsigned int mag = u & 0x7FFFFFFFu;
-  if (mag == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
-  unsigned long long e = (unsigned long long)(((mag >> 23) & 0xFFu) - 127u + 1023u);
+  unsigned int ef = (u >> 23) & 0xFFu;                   // binary32 biased exponent
+  if (ef - 1u >= 254u) {                                 // zero, subnormal, infinity or NaN
+    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+    return (double)f;
+  }
+  unsigned long long e = (unsigned long long)(ef - 127u + 1023u);
   unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) | (e << 52) |
-                         ((unsigned long long)(mag & 0x7FFFFFu) << 29);
+                         ((unsigned long long)(u & 0x7FFFFFu) << 29);
   return __longlong_as_double((long long)b);
 }
 

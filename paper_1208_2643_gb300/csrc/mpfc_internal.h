@@ -65,7 +65,7 @@ struct mpfc_s {
   cudaGraphConditionalHandle cur_handle = 0;   // handle of the graph being captured
   int launch_mode = MPFC_LAUNCH_GRAPH;
   // set by mpfc_create from the precision (mpfc_default_launch_shape)
-  mpfc_launch_shape shape = {1, 0, 4 * 152, 0, 8};
+  mpfc_launch_shape shape = {1, 0, 0, 0, 8};
   // mixed precision
   Lev32 lev32[mpfc::kMaxLevels];
   float* K3f[2] = {nullptr, nullptr};
@@ -84,8 +84,8 @@ struct mpfc_s {
 // active lanes, and an SM saturates at about four warps issuing FP64.  A half sweep of
 // ~33 FP64 instructions per cell therefore costs ~1 us per warp however few cells it
 // has, so small launches use one-warp blocks spread over as many SMs as possible, and
-// large ones blocks of 32 x rows threads (the grid then also balances over the 152 SMs
-// in finer steps).
+// large ones blocks of 32 x rows threads (the grid then also balances over the SMs in
+// finer steps).
 inline dim3 mpfc_blk_for(const mpfc_launch_shape& sh, int X, int Y) {
   if ((long long)X * Y >= sh.small_cells) return dim3(32, sh.rows);
   return dim3(X < 32 ? X : 32, 1);
@@ -125,6 +125,7 @@ void mpfc_coarse_block(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<floa
 int mpfc_reduce_blocks(size_t G);
 int mpfc_tail_max_ctas();
 mpfc_launch_shape mpfc_default_launch_shape(int precision);
+void mpfc_abort_capture(cudaStream_t s, bool owned);
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd,
                        void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme);
 void mpfc_enqueue_prologue(mpfc_s* H, int scheme, cudaStream_t s);

@@ -9,7 +9,7 @@
 #include "mpfc_common.cuh"
 
 namespace {
-constexpr int kBlocks = 152 * 8, kThreads = 256, kIters = 2000;
+constexpr int kBlocksPerSM = 8, kThreads = 256, kIters = 2000;
 
 __global__ void k_fma_chains(double* out, double seed) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -29,6 +29,7 @@ extern "C" int mpfc_probe_fp64_fma(void* d_scratch, void* cuda_stream, double* t
   cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MPFC_ERR_CUDA;
+  const int kBlocks = kBlocksPerSM * mpfc::sm_count();
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0, s);

@@ -372,7 +372,8 @@ def probe_fp64_tflops(stream=None) -> float:
     """Measured FP64 FMA rate of the current GPU (2 flops per FMA), in TFLOP/s."""
     import torch
     lib = load()
-    scratch = torch.empty(152 * 8 * 256, dtype=torch.float64, device="cuda")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    scratch = torch.empty(sms * 8 * 256, dtype=torch.float64, device="cuda")
     st = stream if stream is not None else torch.cuda.current_stream()
     v = ctypes.c_double()
     _check(lib.mpfc_probe_fp64_fma(scratch.data_ptr(), st.cuda_stream, ctypes.byref(v)), "mpfc_probe_fp64_fma")

@@ -100,3 +100,30 @@ def test_autotuner_keeps_results(mp, tmp_path):
     b2 = mp.BatchSolver(ps)
     chosen2 = tuning.autotune(b2, scheme=1, cache_path=str(tmp_path / "tiles.json"), reps=2)
     assert {k: v[:2] for k, v in chosen.items()} == {k: tuple(v[:2]) for k, v in chosen2.items()}
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_batch_nonfinite_instance_diverges_alone(mp, bad):
+    """One instance with a NaN or infinity in phi reports DIVERGED and keeps its state;
+    the other instances step as the single-instance solver does."""
+    ps = [_params(mp, kw) for kw in MIX[:3]]
+    b = mp.BatchSolver(ps)
+    phis = []
+    for i, p in enumerate(ps):
+        phi0 = inputs.noise_field(p.m, p.n, 0.05 + 0.01 * i, 0.05, 10 + i)
+        if i == 1:
+            phi0[3, 4] = bad
+        b.set_state(i, phi0)
+        phis.append(phi0)
+    rc, st, cy = b.step(1, 2, raise_on_error=False)
+    assert rc == mp.MPFC_ERR_DIVERGED
+    assert st[1] == mp.MPFC_ERR_DIVERGED and st[0] == 0 and st[2] == 0
+    kept = b.get_state(1)[0]
+    ok = ~np.isnan(phis[1])
+    assert np.array_equal(np.isnan(kept), np.isnan(phis[1])) and np.array_equal(kept[ok], phis[1][ok])
+    for i in (0, 2):
+        g = mp.Solver(ps[i])
+        g.set_state(phis[i])
+        g.step(1, 2)
+        ref = g.get_state()[0]
+        assert np.abs(b.get_state(i)[0] - ref).max() <= 1e-12 * np.abs(ref).max()

@@ -81,7 +81,7 @@ def test_fp32_tail_is_bitwise_the_per_level_cycle(mp, m, n, scheme):
     runs = []
     for tail_cells in (0, 16 * 16, 64 * 64):
         g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=0.05, precision=mp.MPFC_FP32_INNER))
-        g.set_launch_shape(4, 0, 4 * 152, tail_cells, 1)
+        g.set_launch_shape(4, 0, 4 * torch.cuda.get_device_properties(0).multi_processor_count, tail_cells, 1)
         g.set_state(phi0)
         infos = g.step(scheme, 3)
         runs.append(([i["cycles"] for i in infos], g.get_state()))
@@ -90,3 +90,26 @@ def test_fp32_tail_is_bitwise_the_per_level_cycle(mp, m, n, scheme):
         assert cyc == runs[0][0]
         for a, b in zip(st, runs[0][1]):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf, 1e39])
+def test_fp32_inner_nonfinite_state_diverges_and_keeps_state(mp, bad):
+    """A NaN, an infinity or a value beyond the binary32 range in phi makes the FP64
+    defect non-finite; the step reports DIVERGED and leaves the state as it was (the
+    FP32 conversions carry non-finite values through instead of mapping them to
+    finite ones), and a good state steps normally afterwards."""
+    m = 64
+    g = mp.Solver(mp.default_params(m=m, n=m, precision=mp.MPFC_FP32_INNER))
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+    phi0[5, 7] = bad
+    g.set_state(phi0)
+    rc, infos = g.step(1, 2, raise_on_error=False)
+    assert rc == mp.MPFC_ERR_DIVERGED
+    assert infos[0]["status"] == mp.MPFC_ERR_DIVERGED
+    phi = g.get_state()[0]
+    assert np.array_equal(np.isnan(phi), np.isnan(phi0))
+    ok = ~np.isnan(phi0)
+    assert np.array_equal(phi[ok], phi0[ok])
+    g.set_state(inputs.noise_field(m, m, 0.07, 0.05, 1))
+    info = g.step(1, 1)[0]
+    assert info["status"] == 0 and info["res"] <= 1e-10

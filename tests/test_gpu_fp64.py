@@ -386,6 +386,52 @@ def test_integer_pipe_conversions_match_ieee(mp):
     assert np.all(np.abs(t[nz]) <= np.abs(x[nz]))
 
 
+def _rz32(x):
+    """binary64 -> binary32 rounded toward zero (numpy rounds to nearest): the nearest
+    conversion, stepped one binary32 toward zero where it went past |x|."""
+    with np.errstate(over="ignore", invalid="ignore"):
+        f = x.astype(np.float32)
+        past = np.isfinite(x) & (np.abs(f.astype(np.float64)) > np.abs(x))
+    f[past] = np.nextafter(f[past], np.float32(0.0))
+    return f
+
+
+def test_integer_pipe_conversions_special_values(mp):
+    """Outside the normal binary32 range the conversions equal the IEEE ones too:
+    NaN stays NaN, infinities and overflow give infinities (FLT_MAX toward zero),
+    binary32 underflow gives the correctly rounded subnormal or zero, and the widening
+    of binary32 subnormals, infinities and NaN is exact."""
+    import ctypes
+    lib = mp.load()
+    lib.mpfc_probe_convert.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_void_p]
+    fmax = float(np.finfo(np.float32).max)
+    x = np.array([np.nan, -np.nan, np.inf, -np.inf, 1e39, -1e39, 1e300, -1e300, fmax, -fmax,
+                  fmax * (1 + 2.0 ** -25), fmax * (1 + 2.0 ** -24), 2.0 ** 128, 1e-39, -1e-39, 1e-45, 7e-46,
+                  1.4e-45, 1e-300, -1e-300, 2.0 ** -126, 2.0 ** -127, 2.0 ** -149, 2.0 ** -150,
+                  2.0 ** -150 * 1.0000001, 3 * 2.0 ** -151, 0.0, -0.0, 5e-324])
+    rng = np.random.default_rng(11)
+    x = np.concatenate([x, rng.uniform(-1, 1, 2000) * 2.0 ** rng.uniform(-160, -120, 2000),
+                        rng.uniform(-1, 1, 200) * 2.0 ** rng.uniform(126, 140, 200)])
+    xd = dev(x)
+    rn = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    tr = torch.empty_like(rn)
+    back = torch.empty_like(xd)
+    assert lib.mpfc_probe_convert(xd.data_ptr(), rn.data_ptr(), tr.data_ptr(), back.data_ptr(), x.size, None) == 0
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore", invalid="ignore"):
+        ref = x.astype(np.float32)
+    got = rn.cpu().numpy()
+    nan = np.isnan(x)
+    assert np.all(np.isnan(got[nan]))
+    assert np.array_equal(got[~nan].view(np.uint32), ref[~nan].view(np.uint32))
+    tz = tr.cpu().numpy()
+    assert np.all(np.isnan(tz[nan]))
+    assert np.array_equal(tz[~nan].view(np.uint32), _rz32(x)[~nan].view(np.uint32))
+    b = back.cpu().numpy()
+    assert np.all(np.isnan(b[nan]))
+    assert np.array_equal(b[~nan], ref[~nan].astype(np.float64))
+
+
 @pytest.mark.parametrize("ctas", [1, 8, 16])
 @pytest.mark.parametrize("case", ["periodic1", "periodic2", "ragged2", "neumann2", "pinned2"])
 def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
@@ -394,7 +440,7 @@ def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
     over several steps."""
     probe = mp.Solver(mp.default_params(m=64, n=64))
     try:
-        probe.set_launch_shape(1, 0, 4 * 152, 64 * 64, ctas)
+        probe.set_launch_shape(1, 0, 4 * torch.cuda.get_device_properties(0).multi_processor_count, 64 * 64, ctas)
     except mp.MPFCError:
         pytest.skip(f"this GPU holds no {ctas}-CTA cluster")
     finally:
@@ -415,7 +461,7 @@ def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
             W[:10] = 2.0
             W[-10:] = 2.0
             g.set_pinning(W, inputs.noise_field(m, n, 0.1, 0.05, 4))
-        g.set_launch_shape(1, 0, 4 * 152, tail_cells, ctas)
+        g.set_launch_shape(1, 0, 4 * torch.cuda.get_device_properties(0).multi_processor_count, tail_cells, ctas)
         g.set_state(phi0)
         infos = g.step(scheme, 3)
         runs.append(([i["cycles"] for i in infos], g.get_state()))

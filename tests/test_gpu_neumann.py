@@ -246,7 +246,7 @@ def test_fp32_inner_neumann(mp, oracle_mod, scheme, m, n, h, s, eps):
     runs = []
     for tail_cells in (0, 32 * 32):
         a = neu(mp, m, n, h, s, epsilon=eps, precision=mp.MPFC_FP32_INNER)
-        a.set_launch_shape(4, 0, 4 * 152, tail_cells, 1)
+        a.set_launch_shape(4, 0, 4 * torch.cuda.get_device_properties(0).multi_processor_count, tail_cells, 1)
         a.set_state(phi0)
         infos = a.step(scheme, 3)
         runs.append(([i["cycles"] for i in infos], a.get_state()))

@@ -1,11 +1,13 @@
 """mpfc_mass_noalloc: the allocation-free variant of the mass reduction.
 
-Callers that cannot allocate device memory (inside a stream capture, under a host
-that owns the GPU's memory, or in loops that cannot take cudaMalloc's implicit
-synchronisation) get the mass of a device field through this entry point, whose
-scratch is a static device array.  This file is collected last on purpose: it
-checks the new entry point against mpfc_mass, the workspace-based one, on two calls
-in a row, and must pass alone in a fresh process as well as after the other tests.
+Some callers cannot let a library allocate device memory: an application whose own
+memory pool has reserved all of the GPU's memory, or a plug-in whose host forbids
+allocations outside the host's allocator.  They get the mass of a device field
+through this entry point, whose scratch is a static device array.  This file is
+collected last on purpose: it checks the entry point against mpfc_mass, the
+workspace-based one, on two calls in a row (and against the oracle's mass), up to
+the largest grid it accepts, and must pass alone in a fresh process as well as after
+the other tests.
 """
 import ctypes
 
@@ -39,8 +41,11 @@ def noalloc_mass(lib, phi_dev, m, n, h, stream):
     return rc, out.value
 
 
-@pytest.mark.parametrize("m,n,h", [(96, 160, 0.5), (1024, 1024, 0.5)])
+# 2048 x 2048 is the largest grid accepted: every block slot of the scratch is used and
+# each thread sums its full share of cells
+@pytest.mark.parametrize("m,n,h", [(96, 160, 0.5), (1024, 1024, 0.5), (2048, 2048, 0.5)])
 def test_noalloc_mass_matches_workspace_mass_twice(lib, m, n, h):
+    from oracle import energy
     from paper_1208_2643_gb300 import mpfc
     solver = mpfc.Solver(mpfc.default_params(m=m, n=n, h=h, dt=0.01))
     stream = solver.stream
@@ -51,13 +56,18 @@ def test_noalloc_mass_matches_workspace_mass_twice(lib, m, n, h):
         rc, got = noalloc_mass(lib, phi, m, n, h, stream)
         assert rc == mpfc.MPFC_OK
         assert abs(got - ref) <= 1e-12 * abs(ref), (call, got, ref)
+        exact = energy.mass(phi.cpu().numpy(), h)     # the oracle's h^2 sum phi
+        assert abs(got - exact) <= 1e-12 * abs(exact), (call, got, exact)
         solver.step(1, 1)                         # a different field for the second call
 
 
-def test_noalloc_rejects_too_large(lib):
+@pytest.mark.parametrize("m,n", [(4096, 2048), (2048, 2049), (2049, 2048)])
+def test_noalloc_rejects_too_large(lib, m, n):
+    """Grids past 2048 x 2048 cells are refused before any launch (the 16-element
+    array here is never read)."""
     from paper_1208_2643_gb300 import mpfc
     phi = torch.zeros(16, dtype=torch.float64, device="cuda")
     out = ctypes.c_double()
-    rc = lib.mpfc_mass_noalloc(phi.data_ptr(), 4096, 2048, 0.5, None, ctypes.byref(out))
+    rc = lib.mpfc_mass_noalloc(phi.data_ptr(), m, n, 0.5, None, ctypes.byref(out))
     assert rc == MPFC_ERR_TOO_LARGE
     assert "2048" in mpfc.strerror(rc)
