@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-polycrystal", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the second-order and mixed-precision runs")
     ap.add_argument("--profile", action="store_true", help="steps only, no flush and no extras (ncu launch list)")
     ap.add_argument("--form", choices=["fp64", "fp32", "learned"], default="fp64",
                     help="with --profile: which solver form the launch list runs")
@@ -477,7 +478,7 @@ def run_ours(args):
             b.set_state(i, e["phi0"])
         tiles = tuning.autotune(b, scheme, reps=3)
         b.step(scheme, 2)
-        Kb = max(2, K // 10)
+        Kb = 100   # the workload list's length for the ensemble (config 4)
         eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         flush.fill_(3.0)
         eb0.record(stream)
@@ -488,7 +489,7 @@ def run_ours(args):
         cells_b = sum(bp.m * bp.n for bp in bps)
         # the same instances one by one through the single-instance solver, same protocol
         seq_ms = 0.0
-        for i, bp in enumerate(bps[:16]):
+        for i, bp in enumerate(bps[:16]):   # a quarter of the instances, the same steps
             g1 = mpfc.Solver(bp, stream=stream)
             g1.set_state(ens[i]["phi0"])
             g1.step(scheme, 2)
@@ -543,8 +544,19 @@ def run_ours(args):
             sl = mpfc.Solver(pl, stream=stream)
             gmod.attach(sl, blob)
             sl.set_state(phi0)
-            msl, recl = timed_steps(sl, K, max(args.warmup, 0))
+            Kl = 1000   # the workload list's inference length (config 5)
+            msl, recl = timed_steps(sl, Kl, max(args.warmup, 0))
             msl = replicas.job_time_ms(msl, device="cuda")
+            # the plain extrapolated guess over the same 1000 steps from the same state
+            sx = mpfc.Solver(p, stream=stream)
+            sx.set_state(phi0)
+            msx, recx = timed_steps(sx, Kl, max(args.warmup, 0))
+            msx = replicas.job_time_ms(msx, device="cuda")
+            sx.close()
+
+            def hist(recs_):
+                cyc = [r["cycles"] for r in recs_]
+                return {str(c): cyc.count(c) for c in sorted(set(cyc))}
             # the network's own cost: the five convolutions and the features, timed alone
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -552,12 +564,19 @@ def run_ours(args):
                 sl.lib.mpfc_op_learned_guess(sl.h)
             ev1.record(stream)
             torch.cuda.synchronize()
-            forms["learned"] = {"steps_per_s": world * K / (msl * 1e-3),
+            forms["learned"] = {"workload": "the headline workload, 1000 steps after the warm-up, learned guess "
+                                            "against the extrapolated one over the same steps",
+                                "steps": Kl,
+                                "steps_per_s": world * Kl / (msl * 1e-3),
                                 "vcycles_per_step": float(np.mean([r["cycles"] for r in recl])),
+                                "vcycle_histogram": hist(recl),
                                 "res0_mean": float(np.mean([r["res0"] for r in recl])),
-                                "res0_mean_extrapolated": float(np.mean([r["res0"] for r in recs_main])),
+                                "extrapolated": {"steps_per_s": world * Kl / (msx * 1e-3),
+                                                 "vcycles_per_step": float(np.mean([r["cycles"] for r in recx])),
+                                                 "vcycle_histogram": hist(recx),
+                                                 "res0_mean": float(np.mean([r["res0"] for r in recx]))},
                                 "network_ms_per_step": ev0.elapsed_time(ev1) / 10,
-                                "speedup_vs_fp64": (world * K / (msl * 1e-3)) / steps_per_s,
+                                "speedup_vs_fp64": msx / msl,
                                 "conv32": conv32_timing(size),
                                 "model": "5 x conv3x3 (3-32-32-32-32-1), GELU, bf16/fp32-acc; the 32-input-channel "
                                          "layers on tcgen05 (TMEM accumulators, TMA), the first on mma.sync; "
@@ -651,6 +670,74 @@ def run_ours(args):
             "outer_iterations_per_step": float(np.mean([r["cycles"] for r in rece32])),
             "speedup_vs_fp64": mse_ / mse32}
         se.close()
+
+    # the workload list's second-order run (config 2): 512^2, h = pi/4, eps = 0.25,
+    # beta = 0.9, mean -0.285, s = 0.05, three crystallites of radius 20h with 1e-3 noise,
+    # 500 steps, FP64
+    if not args.no_configs:
+        m2 = 512
+        p2 = mpfc.default_params(m=m2, n=m2, h=np.pi / 4, epsilon=0.25, beta=0.9, dt=0.05, tol=w["tol"],
+                                 omega=w["omega"], guess=mpfc.MPFC_GUESS_EXTRAP)
+        s2 = mpfc.Solver(p2, stream=stream)
+        s2.set_state(inputs.crystallite_field(m2, m2, np.pi / 4, -0.285, 0.25, count=3, radius_cells=20, noise=1e-3,
+                                              seed=replicas.instance_seed(2, rank)))
+        ms2, rec2 = timed_steps(s2, 500, 3, sch=2)
+        ms2 = replicas.job_time_ms(ms2, device="cuda")
+        forms["second_order_crystallites_512"] = {
+            "workload": "512^2, h = pi/4, scheme 2, eps = 0.25, beta = 0.9, mean -0.285, s = 0.05, three crystallites "
+                        "of radius 20h + 1e-3 noise, 500 timed steps after 3 warm-up steps, FP64, tol 1e-10",
+            "steps": 500, "steps_per_s": world * 500 / (ms2 * 1e-3),
+            "cell_updates_per_s": world * 500 * m2 * m2 / (ms2 * 1e-3),
+            "vcycles_per_step": float(np.mean([r["cycles"] for r in rec2]))}
+        s2.close()
+        # the workload list's mixed-precision run (config 3): 2048^2, scheme 1, s = 0.02,
+        # 200 steps; then, step by step from the FP64 path's states, the largest relative
+        # max-norm difference of the mixed form's step from the FP64 step
+        m3 = 2048
+        p3 = mpfc.default_params(m=m3, n=m3, h=0.5, dt=0.02, tol=w["tol"], omega=w["omega"],
+                                 guess=mpfc.MPFC_GUESS_EXTRAP, precision=mpfc.MPFC_FP32_INNER)
+        phi3 = inputs.noise_field(m3, m3, 0.07, 0.05, replicas.instance_seed(3, rank))
+        s3 = mpfc.Solver(p3, stream=stream)
+        s3.set_state(phi3)
+        ms3, rec3 = timed_steps(s3, 200, 3, sch=1)
+        ms3 = replicas.job_time_ms(ms3, device="cuda")
+        p3.precision = mpfc.MPFC_FP64
+        r3 = mpfc.Solver(p3, stream=stream)
+        r3.set_state(phi3)
+        s3.set_state(phi3)
+        ms3_64 = 0.0
+        err3 = 0.0
+        for _ in range(200):
+            st3 = r3.get_state(device=True)
+            s3.set_state(*st3)
+            s3.step(1, 1)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(4.0)
+            ea.record(stream)
+            r3.step_async(1, 1)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            ms3_64 += ea.elapsed_time(eb)
+            a3, b3 = s3.get_state(device=True)[0], r3.get_state(device=True)[0]
+            err3 = max(err3, float((a3 - b3).abs().max() / b3.abs().max()))
+        rc3, _, _ = r3.records(1024)
+        if rc3 != mpfc.MPFC_OK:
+            raise mpfc.MPFCError(rc3, "config-3 FP64 steps")
+        ms3_64 = replicas.job_time_ms(ms3_64, device="cuda")
+        forms["mixed_precision_2048"] = {
+            "workload": "2048^2, h = 0.5, scheme 1, eps = 0.025, beta = 0.9, s = 0.02, noise 0.07 + 0.05 U, 200 steps, "
+                        "FP32 inner V-cycles in FP64 outer defect correction, tol 1e-10 (200 timed steps after 3 warm-up steps)",
+            "steps": 200, "steps_per_s": world * 200 / (ms3 * 1e-3),
+            "cell_updates_per_s": world * 200 * m3 * m3 / (ms3 * 1e-3),
+            "outer_iterations_per_step": float(np.mean([r["cycles"] for r in rec3])),
+            "fp64_steps_per_s": world * 200 / (ms3_64 * 1e-3),
+            "speedup_vs_fp64": ms3_64 / ms3,
+            "max_rel_error_vs_fp64_per_step": err3,
+            "error_note": "each of the 200 steps taken by both forms from the FP64 path's state; the FP64 path is the "
+                          "oracle's in lockstep (tests), and the mixed form is within 1e-8 of the oracle on a "
+                          "3-step prefix (tests)"}
+        s3.close()
+        r3.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -166,11 +166,23 @@ int mpfc_set_launch_mode(mpfc_t* h, int mode);
 int mpfc_launch_counts(const mpfc_t* h, int scheme, int* per_step, int* per_cycle);
 
 /* Measurement helper of the mixed-precision form: times `sweeps` red-black FP32
- * sweeps of the correction equation (two launches each) on level `level` of a handle
+ * sweeps of the correction equation (as the inner cycles run them, mpfc_set_fp32_sweep)
+ * on level `level` of a handle
  * created with precision MPFC_FP32_INNER, whatever its planes hold, between CUDA events
  * on the handle's stream, and writes the milliseconds to *ms (host).  Synchronises.
  * The planes' contents change; call mpfc_set_state before stepping again. */
 int mpfc_fp32_time_smooth(mpfc_t* h, int level, int sweeps, float* ms);
+
+/* How the mixed-precision form's inner red-black sweeps run on levels launched per
+ * level (a tuning choice: results do not depend on it, bit for bit).  tile_rows 0: each
+ * sweep is two launches, one per colour, updating e in place.  tile_rows 4, 8, 16 or
+ * 32: on levels of at least min_cells cells whose width is a multiple of 4, each sweep
+ * is one launch over tiles of 64 x tile_rows cells staged in shared memory (e with a
+ * two-cell halo), reading e from one copy in the workspace and writing the other, in
+ * pairs so that e ends where it started.  Default 0 (two launches per sweep).  Drops
+ * the handle's captured graphs.  MPFC_ERR_INVALID for other values or handles that are
+ * not MPFC_FP32_INNER. */
+int mpfc_set_fp32_sweep(mpfc_t* h, int tile_rows, int min_cells);
 
 /* Launch shapes of the time step's per-cell kernels (a tuning choice: results do not
  * depend on it).  Launches of at least small_cells cells use blocks of 32 x rows

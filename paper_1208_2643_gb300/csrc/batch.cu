@@ -362,12 +362,12 @@ namespace {
 
 // As BCK, inside a stream capture: an error first ends the capture on `stream`, so
 // that the stream is not left capturing (mpfc_abort_capture).
-#define BCKCAP(call, stream, owned)                           \
+#define BCKCAP(call, stream)                                  \
   do {                                                        \
     cudaError_t err_ = (call);                                \
     if (err_ != cudaSuccess) {                                \
       mpfc_set_cuda_error(err_, #call, __FILE__, __LINE__);   \
-      mpfc_abort_capture((stream), (owned));                  \
+      mpfc_abort_capture(stream);                             \
       return MPFC_ERR_CUDA;                                   \
     }                                                         \
   } while (0)
@@ -635,30 +635,29 @@ int build_batch_graph(mpfc_batch_s* B) {
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  BCKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs, true);
+  BCKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs);
   cudaGraphConditionalHandle hnd;
-  BCKCAP(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0), cs, true);
+  BCKCAP(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0), cs);
   enqueue_batch_prologue<SCH>(B, cs);
   enqueue_batch_resnorm<SCH>(B, 0, hnd, 1, cs);
-  BCKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs, true);
+  BCKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs);
   std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
   cp.conditional.handle = hnd;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t cnode;
-  BCKCAP(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp), cs, true);
+  BCKCAP(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp), cs);
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  BCKCAP(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies), cs, true);
-  BCKCAP(cudaStreamBeginCaptureToGraph(B->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), cs,
-         true);
+  BCKCAP(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies), cs);
+  BCKCAP(cudaStreamBeginCaptureToGraph(B->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal), cs);
   enqueue_batch_vcycle<SCH>(B, B->body);
   enqueue_batch_resnorm<SCH>(B, 1, hnd, 1, B->body);
   cudaError_t e = cudaStreamEndCapture(B->body, &body);
   if (e != cudaSuccess) {
     mpfc_set_cuda_error(e, "cudaStreamEndCapture(batch WHILE body)", __FILE__, __LINE__);
-    mpfc_abort_capture(B->body, false);
-    mpfc_abort_capture(cs, true);
+    mpfc_abort_capture(B->body);
+    mpfc_abort_capture(cs);
     return MPFC_ERR_CUDA;
   }
   enqueue_batch_commit<SCH>(B, cs);

@@ -221,6 +221,126 @@ __global__ void __launch_bounds__(256) k_wgrad_partial(const __nv_bfloat16* __re
   if (tap == 4 && tid < cout) dbpart[(size_t)chunk * kMaxCout + tid] = dbacc;
 }
 
+// Weight gradient of the 32-channel layers on tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation): the implicit GEMM
+//   D[co][tap, ci] = sum_p dz[p][co] x[p + off(tap)][ci],  M = 32 (co), N = 9 x 32, K = pixels.
+// A CTA takes a segment of kWgTX pixels of kWgRows consecutive image rows; it keeps the
+// three input rows a tap reaches in a ring of shared-memory rows (periodic halo pixels
+// included) and the dz row, converted to BF16, beside them; warp w computes tap w's
+// 32 x 32 block for all of the CTA's pixels.  Both operands are read with
+// ldmatrix.trans from pixel-major rows (a tap's pixel shift is a row offset).  The
+// shared-memory pixel stride of 80 bytes makes the eight 16-byte rows of an ldmatrix
+// fall in distinct banks.  Pixels past the image edge carry dz = 0.  The bias gradient
+// sums the FP32 dz in a fixed order per thread, then over threads in index order.  The
+// CTA's partial sums go to part[chunk] like the CUDA-core kernel's, and the same
+// reduction adds them in chunk order.
+constexpr int kWgTX = 64, kWgRows = 16, kWgS = 40, kWgThreads = 288;
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const __nv_bfloat16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_mma(const __nv_bfloat16* __restrict__ x, const float* __restrict__ dz,
+                                                          int B, int H, int W, int cout, float* __restrict__ part,
+                                                          float* __restrict__ dbpart) {
+  __shared__ __align__(16) __nv_bfloat16 xs[3][kWgTX + 2][kWgS];
+  __shared__ __align__(16) __nv_bfloat16 ds[kWgTX][kWgS];
+  __shared__ float dbs[kWgThreads][4];
+  const int strips = (W + kWgTX - 1) / kWgTX, rch = (H + kWgRows - 1) / kWgRows;
+  const int chunk = blockIdx.x;
+  const int b = chunk / (strips * rch), rem = chunk - b * strips * rch;
+  const int y0 = (rem / strips) * kWgRows, x0 = (rem % strips) * kWgTX;
+  const int y1 = min(H, y0 + kWgRows);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int dy = warp / 3 - 1, dx = warp % 3 - 1;
+  float acc[2][4][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+  float db4[4] = {0.f, 0.f, 0.f, 0.f};
+  // input row yy (periodic) into ring slot `slot`: pixels x0-1 .. x0+kWgTX, 4 x 16 bytes each
+  auto stage_x = [&](int yy, int slot) {
+    const size_t rowbase = ((size_t)b * H + wrapi(yy, H)) * W;
+    for (int t = tid; t < (kWgTX + 2) * 4; t += kWgThreads) {
+      const int px = t >> 2, c = (t & 3) * 8;
+      const uint4 v = *reinterpret_cast<const uint4*>(x + (rowbase + wrapi(x0 - 1 + px, W)) * 32 + c);
+      *reinterpret_cast<uint4*>(&xs[slot][px][c]) = v;
+    }
+  };
+  stage_x(y0 - 1, 0);
+  stage_x(y0, 1);
+  for (int y = y0; y < y1; ++y) {
+    stage_x(y + 1, (y - y0 + 2) % 3);
+    {   // dz row y as BF16; thread tid always holds channels (tid & 7) * 4 .. +3
+      const size_t rowbase = ((size_t)b * H + y) * W;
+      for (int t = tid; t < kWgTX * 8; t += kWgThreads) {
+        const int px = t >> 3, c = (t & 7) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (x0 + px < W) v = *reinterpret_cast<const float4*>(dz + (rowbase + x0 + px) * 32 + c);
+        db4[0] += v.x;
+        db4[1] += v.y;
+        db4[2] += v.z;
+        db4[3] += v.w;
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+        uint2 pk;
+        pk.x = *reinterpret_cast<unsigned*>(&lo);
+        pk.y = *reinterpret_cast<unsigned*>(&hi);
+        *reinterpret_cast<uint2*>(&ds[px][c]) = pk;
+      }
+    }
+    __syncthreads();
+    const int slot = (y + dy - y0 + 1) % 3;
+    const int j = lane >> 3, r = lane & 7;
+#pragma unroll
+    for (int k0 = 0; k0 < kWgTX; k0 += 16) {
+      unsigned a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) ldsm_x4_t(a[mt], &ds[k0 + r + 8 * (j >> 1)][mt * 16 + 8 * (j & 1)]);
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        unsigned bq[4];
+        ldsm_x4_t(bq, &xs[slot][k0 + r + 8 * (j & 1) + dx + 1][np * 16 + 8 * (j >> 1)]);
+        const unsigned b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma_bf16_16816(acc[mt][2 * np], a[mt], b0);
+          mma_bf16_16816(acc[mt][2 * np + 1], a[mt], b1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // D[co][ci] of tap `warp`: element e of tile (mt, nt) is co = 16 mt + g (+8 for e >= 2),
+  // ci = 8 nt + 2 t (+1 for odd e), g = lane / 4, t = lane % 4
+  const int g = lane >> 2, t4 = lane & 3;
+  float* pt = part + ((size_t)chunk * 9 + warp) * kMaxCin * kMaxCout;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int co = 16 * mt + g + 8 * (e >> 1), ci = 8 * nt + 2 * t4 + (e & 1);
+        if (co < cout) pt[ci * kMaxCout + co] = acc[mt][nt][e];
+      }
+  dbs[tid][0] = db4[0];
+  dbs[tid][1] = db4[1];
+  dbs[tid][2] = db4[2];
+  dbs[tid][3] = db4[3];
+  __syncthreads();
+  if (tid < cout) {
+    float sdb = 0.f;
+    for (int q = tid >> 2; q < kWgThreads; q += 8) sdb += dbs[q][tid & 3];
+    dbpart[(size_t)chunk * kMaxCout + tid] = sdb;
+  }
+}
+
 // dW[tap][ci][co] = sum over chunks in chunk order (deterministic); db likewise.
 __global__ void k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ dbpart, int nchunk, int cin,
                                int cout, float* __restrict__ dw, float* __restrict__ db) {
@@ -459,9 +579,18 @@ extern "C" int mpfc_cnn_conv_backward_data(const void* dz, int B, int H, int W, 
   return launch_conv(A, (cudaStream_t)stream);
 }
 
+// Partial-sum slots of the two weight-gradient kernels for a B x H x W batch.
+long long wgrad_chunks_scalar(int B, int H, int W) {
+  const long long npix = (long long)B * H * W;
+  return (npix + kWgChunk - 1) / kWgChunk;
+}
+long long wgrad_chunks_mma(int B, int H, int W) {
+  return (long long)B * ((H + kWgRows - 1) / kWgRows) * ((W + kWgTX - 1) / kWgTX);
+}
+
 extern "C" size_t mpfc_cnn_wgrad_scratch_bytes(int B, int H, int W) {
-  long long npix = (long long)B * H * W;
-  long long nchunk = (npix + kWgChunk - 1) / kWgChunk;
+  const long long a = wgrad_chunks_scalar(B, H, W), b = wgrad_chunks_mma(B, H, W);
+  const long long nchunk = a > b ? a : b;
   return (size_t)nchunk * (9 * kMaxCin * kMaxCout + kMaxCout) * sizeof(float);
 }
 
@@ -471,11 +600,21 @@ extern "C" int mpfc_cnn_conv_backward_weight(const void* x, int B, int H, int W,
   if (!x || !dz || !dw || !db || !scratch || cin < 1 || cin > cin_p || cin > kMaxCin || cout < 1 ||
       cout > cout_p || cout > kMaxCout || !cp_ok(cin_p))
     return MPFC_ERR_INVALID;
-  long long npix = (long long)B * H * W;
-  int nchunk = (int)((npix + kWgChunk - 1) / kWgChunk);
-  float* part = (float*)scratch;
-  float* dbpart = part + (size_t)nchunk * 9 * kMaxCin * kMaxCout;
   cudaStream_t s = (cudaStream_t)stream;
+  float* part = (float*)scratch;
+  int nchunk;
+  if (cin == 32 && cin_p == 32 && cout_p == 32) {
+    // the 32 -> 32 layers: tensor cores
+    nchunk = (int)wgrad_chunks_mma(B, H, W);
+    float* dbpart = part + (size_t)nchunk * 9 * kMaxCin * kMaxCout;
+    k_wgrad_mma<<<nchunk, kWgThreads, 0, s>>>((const __nv_bfloat16*)x, dz, B, H, W, cout, part, dbpart);
+    const int total = 9 * cin * cout + cout;
+    k_wgrad_reduce<<<(total + 255) / 256, 256, 0, s>>>(part, dbpart, nchunk, cin, cout, dw, db);
+    return cudaGetLastError() == cudaSuccess ? MPFC_OK : MPFC_ERR_CUDA;
+  }
+  // layers with 4-channel inputs or 1-channel outputs: CUDA cores, FP32 dz
+  nchunk = (int)wgrad_chunks_scalar(B, H, W);
+  float* dbpart = part + (size_t)nchunk * 9 * kMaxCin * kMaxCout;
   k_wgrad_partial<<<dim3(nchunk, 9), 256, 0, s>>>((const __nv_bfloat16*)x, dz, B, H, W, cin_p, cin, cout_p, cout,
                                                  part, dbpart);
   int total = 9 * cin * cout + cout;

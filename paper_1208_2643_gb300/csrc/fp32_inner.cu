@@ -13,6 +13,8 @@
 // only limits how much each outer iteration gains.
 #include <string.h>
 
+#include <atomic>
+
 #include <vector>
 
 #include "fp64_kernels.cuh"
@@ -402,6 +404,205 @@ size_t coarse32_smem(const Lev32& C) {
   return sizeof(float) * ((size_t)G * (G + 1) + 4 * (size_t)G);
 }
 
+// ---------------------------------------------------------------------------
+// One full red-black sweep in one launch, out of place (e read from one copy, written
+// to the other), over tiles of kSwX x ty cells staged in shared memory: e with a
+// two-cell halo, q and r with a one-cell halo.  A tile updates the red cells of
+// itself and of its one-cell ring (from the old black values), then its black cells
+// (from the new red values), and writes itself to the destination copy.  Each plane's
+// lines are read once per sweep instead of once per colour.  A ring cell's red update
+// is computed by both tiles that hold it, from the same inputs with the same
+// operations (smooth32_core), so the result is bit for bit that of the two half-sweep
+// launches; reading and writing different copies lets the tiles run in any order.
+// The kernel is persistent: each CTA walks its tiles with two shared-memory stages,
+// the next tile's asynchronous copies (cp.async, wrapped periodic addresses) in flight
+// while the current one is computed.
+// ---------------------------------------------------------------------------
+constexpr int kSwX = 64;                    // tile width in cells (rows are float4-aligned)
+constexpr int kSwPad = 4;                   // columns staged left and right of the tile (>= 2)
+constexpr int kSwW = kSwX + 2 * kSwPad;     // staged row length (floats)
+constexpr int kSwThreads = 256;
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// floats of one stage: e (3 planes, ty + 4 rows) then q, r1, r2, r3 (ty + 2 rows)
+__host__ __device__ __forceinline__ int sweep_stage_floats(int ty) { return kSwW * (3 * (ty + 4) + 4 * (ty + 2)); }
+
+__device__ __forceinline__ int sw_col(int x, int m) { x %= m; return x < 0 ? x + m : x; }
+__device__ __forceinline__ int sw_row(int y, int n, int nyn) {
+  if (nyn) return y < 0 ? 0 : (y >= n ? n - 1 : y);   // ghost rows read as the boundary row (A.7)
+  y %= n;
+  return y < 0 ? y + n : y;
+}
+
+struct SweepSrc {
+  const float *ephi, *emu, *eka;   // source copy of e
+  float *dphi, *dmu, *dka;         // destination copy
+};
+
+__device__ __forceinline__ void sweep_tile_load(const Lev32& L, const SweepSrc& S, int x0, int y0, int ty, float* st) {
+  const int m = L.m, n = L.n, q4 = kSwW / 4, RE = ty + 4, RQ = ty + 2;
+  for (int t = threadIdx.x; t < RE * q4; t += blockDim.x) {
+    const int r = t / q4, c4 = t - r * q4;
+    const size_t g = (size_t)sw_row(y0 - 2 + r, n, L.nyn) * m + sw_col(x0 - kSwPad + 4 * c4, m);
+    float* d = st + r * kSwW + 4 * c4;
+    cp_async16(d, S.ephi + g);
+    cp_async16(d + RE * kSwW, S.emu + g);
+    cp_async16(d + 2 * RE * kSwW, S.eka + g);
+  }
+  float* qb = st + 3 * RE * kSwW;
+  for (int t = threadIdx.x; t < RQ * q4; t += blockDim.x) {
+    const int r = t / q4, c4 = t - r * q4;
+    const size_t g = (size_t)sw_row(y0 - 1 + r, n, L.nyn) * m + sw_col(x0 - kSwPad + 4 * c4, m);
+    float* d = qb + r * kSwW + 4 * c4;
+    cp_async16(d, L.q + g);
+    cp_async16(d + RQ * kSwW, L.r1 + g);
+    cp_async16(d + 2 * RQ * kSwW, L.r2 + g);
+    cp_async16(d + 3 * RQ * kSwW, L.r3 + g);
+  }
+}
+
+// The cell update of smooth32_cell on staged values: ce indexes the cell in the e
+// arrays (row stride kSwW), cq in the q / r arrays; same sums, same core.
+__device__ __forceinline__ void sweep_tile_cell(const Coef32& k, const Coef32& kb, bool bnd, float* E0, float* E1,
+                                                float* E2, int ce, const float* Qs, int RQW, int cq) {
+  const float smu = (E1[ce - 1] + E1[ce + 1]) + (E1[ce - kSwW] + E1[ce + kSwW]);
+  const float ska = (E2[ce - 1] + E2[ce + 1]) + (E2[ce - kSwW] + E2[ce + kSwW]);
+  const float sph = (E0[ce - 1] + E0[ce + 1]) + (E0[ce - kSwW] + E0[ce + kSwW]);
+  float a = E0[ce], b = E1[ce], d = E2[ce];
+  const float q = Qs[cq], r1 = Qs[RQW + cq], r2 = Qs[2 * RQW + cq], r3 = Qs[3 * RQW + cq];
+  if (bnd)
+    smooth32_core(kb, smu - b, ska - d, sph - a, q, r1, r2, r3, a, b, d);
+  else
+    smooth32_core(k, smu, ska, sph, q, r1, r2, r3, a, b, d);
+  E0[ce] = a;
+  E1[ce] = b;
+  E2[ce] = d;
+}
+
+__global__ void __launch_bounds__(kSwThreads) k_sweep32_tiles(Lev32 L, SweepSrc S, Coef32 k, Coef32 kb, int ty) {
+  extern __shared__ float4 sw_smem[];
+  pdl_enter();
+  const int m = L.m, n = L.n;
+  const int tiles_x = (m + kSwX - 1) / kSwX, ntiles = tiles_x * ((n + ty - 1) / ty);
+  const int SF = sweep_stage_floats(ty), RE = ty + 4, RQ = ty + 2;
+  float* const base = reinterpret_cast<float*>(sw_smem);   // stage s at base + s * SF
+  int tile = blockIdx.x;
+  if (tile < ntiles) sweep_tile_load(L, S, (tile % tiles_x) * kSwX, (tile / tiles_x) * ty, ty, base);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles)
+      sweep_tile_load(L, S, (next % tiles_x) * kSwX, (next / tiles_x) * ty, ty, base + ((it + 1) & 1) * SF);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+    float* E0 = base + (it & 1) * SF;
+    float* E1 = E0 + RE * kSwW;
+    float* E2 = E1 + RE * kSwW;
+    const float* Qs = E2 + RE * kSwW;
+    const int x0 = (tile % tiles_x) * kSwX, y0 = (tile / tiles_x) * ty;
+    const int tw = min(kSwX, m - x0), th = min(ty, n - y0);
+    // red cells ((x + y) even) of the tile and its ring: rows y0-1 .. y0+th, columns x0-1 .. x0+tw
+    {
+      const int rw = tw + 2, per = (rw + 1) >> 1;
+      for (int t = threadIdx.x; t < (th + 2) * per; t += blockDim.x) {
+        const int rr = t / per, y = y0 - 1 + rr;
+        const int cc = 2 * (t - rr * per) + ((x0 - 1 + y) & 1);
+        if (cc >= rw || (L.nyn && (y < 0 || y >= n))) continue;   // Neumann ghost rows hold no cells
+        const bool bnd = L.nyn && (y == 0 || y == n - 1);
+        sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, RQ * kSwW,
+                        rr * kSwW + cc + kSwPad - 1);
+      }
+    }
+    __syncthreads();
+    // black cells ((x + y) odd) of the tile
+    {
+      const int per = tw >> 1;
+      for (int t = threadIdx.x; t < th * per; t += blockDim.x) {
+        const int rr = t / per, y = y0 + rr;
+        const int cc = 2 * (t - rr * per) + ((x0 + y + 1) & 1);
+        const bool bnd = L.nyn && (y == 0 || y == n - 1);
+        sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, RQ * kSwW,
+                        (rr + 1) * kSwW + cc + kSwPad);
+      }
+    }
+    __syncthreads();
+    // the tile to the destination copy, float4 rows
+    {
+      const int q4 = tw >> 2;
+      for (int t = threadIdx.x; t < th * q4; t += blockDim.x) {
+        const int rr = t / q4, c4 = t - rr * q4;
+        const size_t g = (size_t)(y0 + rr) * m + x0 + 4 * c4;
+        const int se = (rr + 2) * kSwW + kSwPad + 4 * c4;
+        *reinterpret_cast<float4*>(S.dphi + g) = *reinterpret_cast<const float4*>(E0 + se);
+        *reinterpret_cast<float4*>(S.dmu + g) = *reinterpret_cast<const float4*>(E1 + se);
+        *reinterpret_cast<float4*>(S.dka + g) = *reinterpret_cast<const float4*>(E2 + se);
+      }
+    }
+    __syncthreads();   // the stage is reloaded two tiles on
+  }
+}
+
+int sweep_tiles_per_sm(int ty);
+
+// Whether level F takes the one-launch tiled sweep (its second copy of e exists and it
+// is large enough for the handle's setting).
+bool sweep_tiled(const mpfc_s* H, const Lev32& F) {
+  return H->sweep_tile_rows > 0 && F.xphi && (long long)F.m * F.n >= H->sweep_tile_cells &&
+         sweep_tiles_per_sm(H->sweep_tile_rows) > 0;
+}
+
+// Resident CTAs per SM of the tiled sweep with tiles of ty rows on the current device,
+// cached per device and tile height.  The kernel's dynamic shared-memory limit is raised
+// once per device to what the tallest tiles (32 rows) need, so that no later setting
+// can leave it below a height whose occupancy is cached.
+int sweep_tiles_per_sm(int ty) {
+  constexpr int kDevs = 64;
+  static std::atomic<int> cache[kDevs][6];   // tile heights 1 << idx; 0: not queried yet
+  static std::atomic<int> raised[kDevs];
+  int dev = 0, idx = 0;
+  while ((1 << idx) < ty && idx < 5) ++idx;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) dev = -1;
+  if (dev >= 0)
+    if (int c = cache[dev][idx].load()) return c;
+  const int max_smem = (int)(2 * sizeof(float) * (size_t)sweep_stage_floats(32));
+  if (dev < 0 || !raised[dev].load()) {
+    if (cudaFuncSetAttribute(k_sweep32_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return 0;
+    }
+    if (dev >= 0) raised[dev].store(1);
+  }
+  const size_t smem = 2 * sizeof(float) * (size_t)sweep_stage_floats(ty);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep32_tiles, kSwThreads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  if (dev >= 0) cache[dev][idx].store(per_sm);
+  return per_sm;
+}
+
+// Launches one tiled sweep reading e from (fp, fm, fk) and writing it to (tp, tm, tk).
+void launch_sweep_tiles(const mpfc_s* H, const Lev32& F, const float* fp, const float* fm, const float* fk, float* tp,
+                        float* tm, float* tk, const Coef32& kf, const Coef32& kb, cudaStream_t s) {
+  const int ty = H->sweep_tile_rows;
+  const size_t smem = 2 * sizeof(float) * (size_t)sweep_stage_floats(ty);
+  const int per_sm = sweep_tiles_per_sm(ty);   // >= 1 (sweeps32 falls back when it is 0)
+  const long long ntiles = (long long)((F.m + kSwX - 1) / kSwX) * ((F.n + ty - 1) / ty);
+  const long long cap = (long long)per_sm * mpfc::sm_count();
+  const int grid = (int)(ntiles < cap ? ntiles : cap);
+  SweepSrc S = {fp, fm, fk, tp, tm, tk};
+  mpfc_launch(H->shape, k_sweep32_tiles, dim3(grid), dim3(kSwThreads), smem, s, F, S, kf, kb, ty);
+}
+
 // `sweeps` red-black sweeps of one level, one launch per colour.  (A single-launch
 // sweep over shared-memory tiles with a 2-cell halo halves the DRAM reads at 2048^2 but
 // was slower on GB300 at every level size measured: its staging is latency bound.  So
@@ -413,10 +614,16 @@ size_t coarse32_smem(const Lev32& C) {
 // the shared-memory tail slowed down under its addressing, and at the 1024^2 workload,
 // whose planes sit in L2, the form ran 977 against 1018 steps/s, so the layout stays
 // row-major.)
-void sweeps32(const mpfc_launch_shape& sh, const Lev32& F, const Coef32& kf, const Coef32& kb, int sweeps,
-              cudaStream_t s) {
+void sweeps32(const mpfc_s* H, const Lev32& F, const Coef32& kf, const Coef32& kb, int sweeps, cudaStream_t s) {
+  const mpfc_launch_shape& sh = H->shape;
+  int done = 0;
+  if (sweep_tiled(H, F))   // pairs of one-launch sweeps, there and back: e ends in its own planes
+    for (; done + 2 <= sweeps; done += 2) {
+      launch_sweep_tiles(H, F, F.ephi, F.emu, F.eka, F.xphi, F.xmu, F.xka, kf, kb, s);
+      launch_sweep_tiles(H, F, F.xphi, F.xmu, F.xka, F.ephi, F.emu, F.eka, kf, kb, s);
+    }
   dim3 g = mpfc_grid_of(sh, F.m / 2, F.n), b = mpfc_blk_for(sh, F.m / 2, F.n);
-  for (int sw = 0; sw < sweeps; ++sw) {
+  for (; done < sweeps; ++done) {
     mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, kb, 0);
     mpfc_launch(sh, k_smooth32, g, b, 0, s, F, kf, kb, 1);
   }
@@ -591,7 +798,7 @@ void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
     const Lev32& F = H->lev32[l];
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]), kb = coef32_of(H->coefb[scheme - 1][l]);
-    sweeps32(sh, F, kf, kb, p.nu1, s);
+    sweeps32(H, F, kf, kb, p.nu1, s);
     mpfc_launch(sh, k_restrict_defect32, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C, kf);
   }
   if (lt < L) {
@@ -606,7 +813,7 @@ void enqueue_inner_vcycle(mpfc_s* H, int scheme, cudaStream_t s) {
     const Lev32& C = H->lev32[l + 1];
     Coef32 kf = coef32_of(H->coef[scheme - 1][l]), kb = coef32_of(H->coefb[scheme - 1][l]);
     mpfc_launch(sh, k_prolong32, grid_of(C.m, C.n), kBlk, 0, s, F, C);
-    sweeps32(sh, F, kf, kb, p.nu2, s);
+    sweeps32(H, F, kf, kb, p.nu2, s);
   }
 }
 
@@ -663,12 +870,29 @@ size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base,
     v.r2 = take(G);
     v.r3 = take(G);
     v.q = take(G);
+    // second copy of e for the one-launch sweeps (float4 rows need m a multiple of 4)
+    v.xphi = v.xmu = v.xka = nullptr;
+    if (m % 4 == 0) {
+      v.xphi = take(G);
+      v.xmu = take(G);
+      v.xka = take(G);
+    }
     if (H && base) H->lev32[l] = v;
     m /= 2;
     n /= 2;
     h *= 2.0;
   }
   return *off - start;
+}
+
+extern "C" int mpfc_set_fp32_sweep(mpfc_t* H, int tile_rows, int min_cells) {
+  if (!H || H->p.precision != MPFC_FP32_INNER || min_cells < 0 ||
+      (tile_rows != 0 && tile_rows != 4 && tile_rows != 8 && tile_rows != 16 && tile_rows != 32))
+    return MPFC_ERR_INVALID;
+  H->sweep_tile_rows = tile_rows;
+  H->sweep_tile_cells = min_cells;
+  mpfc_drop_graphs(H);
+  return MPFC_OK;
 }
 
 extern "C" int mpfc_fp32_time_smooth(mpfc_t* H, int level, int sweeps, float* ms) {
@@ -682,8 +906,7 @@ extern "C" int mpfc_fp32_time_smooth(mpfc_t* H, int level, int sweeps, float* ms
     return MPFC_ERR_CUDA;
   }
   if ((e = cudaEventRecord(e0, H->stream)) == cudaSuccess) {
-    sweeps32(H->shape, H->lev32[level], coef32_of(H->coef[0][level]), coef32_of(H->coefb[0][level]), sweeps,
-             H->stream);
+    sweeps32(H, H->lev32[level], coef32_of(H->coef[0][level]), coef32_of(H->coefb[0][level]), sweeps, H->stream);
     if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaEventRecord(e1, H->stream)) == cudaSuccess &&
         (e = cudaEventSynchronize(e1)) == cudaSuccess)
       e = cudaEventElapsedTime(ms, e0, e1);

@@ -30,12 +30,12 @@ using namespace mpfc;
 
 // As CK, inside a stream capture: an error first ends the capture on `stream` (see
 // mpfc_abort_capture), so that the caller's stream is not left capturing.
-#define CKCAP(call, stream, owned)                            \
+#define CKCAP(call, stream)                                   \
   do {                                                        \
     cudaError_t err_ = (call);                                \
     if (err_ != cudaSuccess) {                                \
       mpfc_set_cuda_error(err_, #call, __FILE__, __LINE__);   \
-      mpfc_abort_capture((stream), (owned));                  \
+      mpfc_abort_capture(stream);                             \
       return MPFC_ERR_CUDA;                                   \
     }                                                         \
   } while (0)
@@ -647,8 +647,8 @@ static int build_step_graph(mpfc_s* H) {
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  CKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs, true);
-  CKCAP(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0), cs, true);
+  CKCAP(cudaStreamGetCaptureInfo(cs, &st, nullptr, &graph, &deps, nullptr, &ndeps), cs);
+  CKCAP(cudaGraphConditionalHandleCreate(&hnd, graph, 0, 0), cs);
   H->cur_handle = hnd;
   int rc;
   if (H->p.precision == MPFC_FP32_INNER) {
@@ -660,7 +660,7 @@ static int build_step_graph(mpfc_s* H) {
     if (rc == MPFC_OK) enqueue_commit<SCH>(H, cs);
   }
   if (rc != MPFC_OK) {
-    mpfc_abort_capture(cs, true);
+    mpfc_abort_capture(cs);
     return rc;
   }
   CK(cudaStreamEndCapture(cs, &graph));
@@ -675,17 +675,18 @@ static int build_step_graph(mpfc_s* H) {
   return MPFC_OK;
 }
 
-// Ends a capture on s that an error interrupted, so that the stream can be used again,
-// and destroys the partial graph when it is the capture's own (`owned`; a capture into
-// an existing graph, such as a conditional node's body, leaves that graph to its owner).
-void mpfc_abort_capture(cudaStream_t s, bool owned) {
+// Ends a capture on s that an error interrupted, so that the stream can be used again.
+// The partial graph is left undestroyed: after a failed capture into a conditional
+// node's body, that body's state is not one the runtime documents as safe to destroy,
+// and an error path that loses a graph is better than one that can crash the process.
+void mpfc_abort_capture(cudaStream_t s) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &st) != cudaSuccess || st == cudaStreamCaptureStatusNone) {
     (void)cudaGetLastError();
     return;
   }
   cudaGraph_t g = nullptr;
-  if (cudaStreamEndCapture(s, &g) == cudaSuccess && g && owned) cudaGraphDestroy(g);
+  (void)cudaStreamEndCapture(s, &g);
   (void)cudaGetLastError();   // the invalidated capture's error is reported by the caller
 }
 
@@ -707,7 +708,7 @@ int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hn
   CK(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
   CK(cudaStreamBeginCaptureToGraph(H->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   body_fn(H, scheme, H->body_stream);
-  CKCAP(cudaStreamEndCapture(H->body_stream, &body), H->body_stream, false);
+  CKCAP(cudaStreamEndCapture(H->body_stream, &body), H->body_stream);
   return MPFC_OK;
 }
 

@@ -16,6 +16,7 @@ struct Lev32 {
   float *ephi, *emu, *eka;   // correction e = (e_phi, e_mu, e_kappa)
   float *r1, *r2, *r3;       // source of the correction equation (restricted defect)
   float* q;                  // gam + g'(phi) of the FP64 iterate, restricted
+  float *xphi, *xmu, *xka;   // second copy of e for out-of-place sweeps (nullptr: none)
 };
 
 // Learned-guess buffers in the workspace (MPFC_GUESS_LEARNED).
@@ -69,6 +70,8 @@ struct mpfc_s {
   // mixed precision
   Lev32 lev32[mpfc::kMaxLevels];
   float* K3f[2] = {nullptr, nullptr};
+  int sweep_tile_rows = 0;         // FP32 one-launch sweeps: tile height (0: two launches per sweep)
+  long long sweep_tile_cells = 0;  // ... on levels of at least this many cells
   int outer_max = 0;
   // learned initial guess
   MpfcGuess guess;
@@ -125,7 +128,7 @@ void mpfc_coarse_block(const mpfc::Lev& C, const mpfc::Coef& k, std::vector<floa
 int mpfc_reduce_blocks(size_t G);
 int mpfc_tail_max_ctas();
 mpfc_launch_shape mpfc_default_launch_shape(int precision);
-void mpfc_abort_capture(cudaStream_t s, bool owned);
+void mpfc_abort_capture(cudaStream_t s);
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd,
                        void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme);
 void mpfc_enqueue_prologue(mpfc_s* H, int scheme, cudaStream_t s);

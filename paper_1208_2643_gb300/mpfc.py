@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_fp32_time_smooth.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     lib.mpfc_launch_counts.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
+    lib.mpfc_set_fp32_sweep.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
     lib.mpfc_op_learned_guess.argtypes = [_VP]
     lib.mpfc_batch_workspace_bytes.argtypes = [ctypes.c_int, P(mpfc_params)]
     lib.mpfc_batch_workspace_bytes.restype = ctypes.c_size_t
@@ -278,6 +279,11 @@ class Solver:
         levels (at most tail_cells cells) run as one launch of tail_ctas CTAs."""
         _check(self.lib.mpfc_set_launch_shape(self.h, rows, small_cells, pdl_blocks, tail_cells, tail_ctas),
                "mpfc_set_launch_shape")
+
+    def set_fp32_sweep(self, tile_rows: int, min_cells: int = 0):
+        """Mixed-precision handles: inner sweeps as one launch over 64 x tile_rows tiles
+        on levels of at least min_cells cells (tile_rows 0: two launches per sweep)."""
+        _check(self.lib.mpfc_set_fp32_sweep(self.h, tile_rows, min_cells), "mpfc_set_fp32_sweep")
 
     def step_async(self, scheme: int, nsteps: int = 1):
         """Enqueues steps without synchronising (records via records())."""

@@ -113,3 +113,48 @@ def test_fp32_inner_nonfinite_state_diverges_and_keeps_state(mp, bad):
     g.set_state(inputs.noise_field(m, m, 0.07, 0.05, 1))
     info = g.step(1, 1)[0]
     assert info["status"] == 0 and info["res"] <= 1e-10
+
+
+@pytest.mark.parametrize("case", ["periodic1", "periodic2", "ragged2", "neumann2", "pinned2", "odd_sweeps1"])
+def test_fp32_tiled_sweeps_are_bitwise_the_two_launch_sweeps(mp, case):
+    """One-launch red-black sweeps over shared-memory tiles (out of place, in pairs)
+    give exactly the bits of two in-place half-sweep launches, for every tile height,
+    over whole steps (same outer counts, same state)."""
+    scheme = int(case[-1])
+    m, n = (96, 160) if case.startswith("ragged") else (128, 128) if case != "neumann2" else (128, 64)
+    kw = dict(m=m, n=n, h=0.5, dt=0.05, precision=mp.MPFC_FP32_INNER)
+    if case.startswith("neumann"):
+        kw["bc"] = mp.MPFC_BC_NEUMANN_Y
+    if case.startswith("pinned"):
+        kw["pinning"] = 1
+    if case.startswith("odd"):
+        kw.update(nu1=3, nu2=1)
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 7)
+    runs = []
+    for rows in (0, 4, 8, 16, 32):
+        g = mp.Solver(mp.default_params(**kw))
+        g.set_launch_shape(4, 0, 4 * torch.cuda.get_device_properties(0).multi_processor_count, 0, 1)
+        g.set_fp32_sweep(rows, 0)
+        if case.startswith("pinned"):
+            W = np.zeros((n, m))
+            W[n // 4: n // 2, :] = 2.0
+            g.set_pinning(W, 0.5 * phi0)
+        g.set_state(phi0)
+        infos = g.step(scheme, 3)
+        assert all(i["status"] == 0 for i in infos)
+        runs.append(([i["cycles"] for i in infos], g.get_state()))
+        g.close()
+    for cyc, st in runs[1:]:
+        assert cyc == runs[0][0]
+        for a, b in zip(st, runs[0][1]):
+            assert np.array_equal(a, b)
+
+
+def test_fp32_sweep_setting_checked(mp):
+    g = mp.Solver(mp.default_params(m=64, n=64, precision=mp.MPFC_FP32_INNER))
+    for bad in (3, 12, 64, -1):
+        with pytest.raises(mp.MPFCError):
+            g.set_fp32_sweep(bad, 0)
+    f = mp.Solver(mp.default_params(m=64, n=64))
+    with pytest.raises(mp.MPFCError):
+        f.set_fp32_sweep(16, 0)
