@@ -179,7 +179,10 @@ int mpfc_fp32_time_smooth(mpfc_t* h, int level, int sweeps, float* ms);
  * 32: on levels of at least min_cells cells whose width is a multiple of 4, each sweep
  * is one launch over tiles of 64 x tile_rows cells staged in shared memory (e with a
  * two-cell halo), reading e from one copy in the workspace and writing the other, in
- * pairs so that e ends where it started.  Default 0 (two launches per sweep).  Drops
+ * pairs so that e ends where it started.  Default: 16 rows on levels of at least
+ * 2048 x 2048 cells, whose planes do not stay in L2 between sweeps (there the tiled
+ * sweep reads each plane once instead of twice; smaller levels, served from L2, run
+ * faster as two launches).  Drops
  * the handle's captured graphs.  MPFC_ERR_INVALID for other values or handles that are
  * not MPFC_FP32_INNER. */
 int mpfc_set_fp32_sweep(mpfc_t* h, int tile_rows, int min_cells);

@@ -84,6 +84,17 @@ int mpfc_cnn_adam(float* param, const float* grad, float* m, float* v, int n, fl
  * Process-wide; applies to convolutions launched, and step graphs captured, afterwards. */
 int mpfc_cnn_set_tensor_path(int use_tcgen05);
 
+/* Test hook of the tcgen05 convolution's failure handling (no counterpart in the paper;
+ * for tests of the bounded waits without a GPU fault).  withhold = 1: in every following
+ * tcgen05 convolution, CTA 0 skips the tensor copy of its first input row (it touches
+ * no memory out of bounds), so the MMA issuer's wait on that row runs out after
+ * spin_cycles clock cycles; the CTA then stops all its roles, waits (bounded) for the
+ * copies and MMAs it already issued, frees its tensor memory and returns, and the launch
+ * leaves that CTA's tiles unwritten; mpfc_cnn_tensor_path_status then reports the
+ * failure.  withhold = 0, spin_cycles = 0 restore normal operation (waits limited to
+ * about 0.1 s).  Process-wide, synchronous.  MPFC_ERR_INVALID for other values. */
+int mpfc_cnn_test_withhold_load(int withhold, long long spin_cycles);
+
 /* Reports (and clears) whether a tcgen05 convolution gave up waiting for its MMAs
  * since the last call: MPFC_OK if none did, MPFC_ERR_NOT_CONVERGED if one did (its
  * output is then incomplete), MPFC_ERR_CUDA on a CUDA error.  Synchronous. */

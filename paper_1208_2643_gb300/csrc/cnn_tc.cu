@@ -87,7 +87,7 @@ constexpr int kSmem = kOffMisc + 16 + 1024;
 static_assert(kPlaneLead + 130 * kPixBytes <= kSlotBytes + kPlaneLead, "plane layout");
 static_assert(kSlotBytes % 1024 == 0 && kOffB % 1024 == 0 && kOffOut % 1024 == 0, "alignment");
 static_assert(kSmem <= 227 * 1024, "shared memory");
-constexpr long long kSpinLimit = 200000000ll;   // clock cycles (about 0.1 s) per wait
+constexpr long long kSpinLimit = 200000000ll;   // clock cycles (about 0.1 s) per wait, by default
 
 // Epilogue modes (same meaning as the mma.sync kernel's).
 constexpr int kModeGelu = 0, kModeLinear = 1, kModeGeluGrad = 2, kModeGuess = 3;
@@ -130,20 +130,34 @@ __device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
 
 // Set to 1 by a CTA whose wait gave up; read and cleared by mpfc_cnn_tensor_path_status.
 __device__ int g_tc_fail = 0;
+// The wait limit in clock cycles, and the failure-injection switch of the test hook
+// (mpfc_cnn_test_withhold_load): when set, CTA 0 skips the tensor copy of its first
+// input row, so that the MMA issuer's wait on that row runs out.
+__device__ long long g_tc_spin_limit = kSpinLimit;
+__device__ int g_tc_withhold = 0;
 
 // Bounded wait on an mbarrier phase; false if the CTA aborts (this wait timed out, or
 // another role's did).
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  const long long t0 = clock64();
+  const long long t0 = clock64(), limit = g_tc_spin_limit;
   while (true) {
     if (try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > kSpinLimit) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicExch(&g_tc_fail, 1);
       return false;
     }
   }
+}
+
+// Bounded wait that ignores the abort flag: the drains before a CTA exits, which wait
+// for asynchronous copies and MMAs already issued (false if the limit ran out).
+__device__ __forceinline__ bool drain_bar(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64(), limit = g_tc_spin_limit;
+  while (!try_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
 }
 
 __device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
@@ -197,6 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
   auto plane = [&](int slot) { return sbase + kOffA + (uint32_t)(slot * kSlotBytes + kPlaneLead); };   // pixel 0
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffMisc);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kOffMisc + 4);
+  const uint32_t drain = sbase + kOffMisc + 8;   // the MMA issuer's final commit
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 1) {   // TMEM: the ring of kBlocks output-row blocks of NB columns
@@ -213,6 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
       bar_init(accfull(j), 1);
       bar_init(accempty(j), kEpiWarps / 2);   // the 8 warps of the group that reads the block
     }
+    bar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
@@ -266,6 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
     // Nothing here waits on memory, so the producer runs ahead by the whole ring.
     const char* xg = reinterpret_cast<const char*>(A.x);
     const int hside = lane >> 2, hq = lane & 3;
+    const bool withhold = g_tc_withhold != 0 && blockIdx.x == 0;   // test hook: skip load 0's tensor copy
     int k = 0;
     for (int t = t_begin; t < t_end; ++t) {
       int b, y, x0;
@@ -286,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
           asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
           asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full(s)) : "memory");
         }
-        if (lane == 0) {
+        if (lane == 0 && !(withhold && k == 0)) {
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(kTxBytes)
                        : "memory");
           asm volatile(
@@ -298,6 +315,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
       }
       if (*abort_flag) break;
     }
+    // Drain before the CTA exits: this lane's halo copies, then (lane 0) the tensor
+    // copies of the last kSlots loads, which an aborted MMA issuer may not have waited
+    // for.  A load whose phase already completed returns at once; the load the test hook
+    // withheld never completes and is skipped.
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (lane == 0)
+      for (int kk = k > kSlots ? k - kSlots : 0; kk < k; ++kk)
+        if (!(withhold && kk == 0)) drain_bar(full(kk % kSlots), (uint32_t)((kk / kSlots) & 1));
+    __syncwarp();
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
@@ -313,7 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
           ok = wait_bar(full(s), (uint32_t)((k / kSlots) & 1), abort_flag);
           if (ok && rr + 1 <= n - 1) {   // first contribution to output row rr + 1: its block must be free
             const int i = i_s + rr + 1;
-            if (i >= kBlocks) ok = wait_bar(accempty(i % kBlocks), (uint32_t)(((i / kBlocks) - 1) & 1), abort_flag);
+            if (i >= kBlocks)
+              ok = wait_bar(accempty(i % kBlocks), (uint32_t)(((i / kBlocks) - 1) & 1), abort_flag);
           }
           if (!ok) break;
           // the halo chunks arrived through cp.async (generic proxy); the MMAs read
@@ -351,6 +378,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
         }
         ts = te + 1;
       }
+      // every MMA issued has completed before the tensor memory is freed (also after an abort)
+      mma_commit(drain);
+      drain_bar(drain, 0u);
     }
   } else {
     // ---------------------------------------------------------------- epilogue
@@ -568,6 +598,19 @@ int mpfc_cnn_conv_tc(const void* x, int B, int H, int W, const void* wk, const f
 
 extern "C" int mpfc_cnn_set_tensor_path(int use_tcgen05) {
   g_use_tc = use_tcgen05 ? 1 : 0;
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_cnn_test_withhold_load(int withhold, long long spin_cycles) {
+  if (withhold < 0 || withhold > 1 || spin_cycles < 0) return MPFC_ERR_INVALID;
+  const int w = withhold;
+  const long long lim = spin_cycles > 0 ? spin_cycles : kSpinLimit;
+  cudaError_t e = cudaMemcpyToSymbol(g_tc_withhold, &w, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_spin_limit, &lim, sizeof(long long));
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "tc test hook", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
   return MPFC_OK;
 }
 

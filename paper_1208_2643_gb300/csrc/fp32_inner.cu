@@ -421,14 +421,14 @@ size_t coarse32_smem(const Lev32& C) {
 constexpr int kSwX = 64;                    // tile width in cells (rows are float4-aligned)
 constexpr int kSwPad = 4;                   // columns staged left and right of the tile (>= 2)
 constexpr int kSwW = kSwX + 2 * kSwPad;     // staged row length (floats)
-constexpr int kSwThreads = 256;
+constexpr int kSwThreads = 320;             // 10 warps
 
 __device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // floats of one stage: e (3 planes, ty + 4 rows) then q, r1, r2, r3 (ty + 2 rows)
 __host__ __device__ __forceinline__ int sweep_stage_floats(int ty) { return kSwW * (3 * (ty + 4) + 4 * (ty + 2)); }
@@ -445,9 +445,38 @@ struct SweepSrc {
   float *dphi, *dmu, *dka;         // destination copy
 };
 
-__device__ __forceinline__ void sweep_tile_load(const Lev32& L, const SweepSrc& S, int x0, int y0, int ty, float* st) {
-  const int m = L.m, n = L.n, q4 = kSwW / 4, RE = ty + 4, RQ = ty + 2;
-  for (int t = threadIdx.x; t < RE * q4; t += blockDim.x) {
+// Stages the tile (x0, y0) of TY rows: cp.async copies of 16 bytes, e rows y0-2 .. y0+TY+1
+// and q / r rows y0-1 .. y0+TY, columns x0-4 .. x0+67.  A tile that reaches no domain
+// edge addresses rows and columns directly; the others wrap them (periodic) or clamp
+// the rows (Neumann ghost rows, (A.7)).
+template <int TY>
+__device__ __forceinline__ void sweep_tile_load(const Lev32& L, const SweepSrc& S, int x0, int y0, float* st) {
+  constexpr int q4 = kSwW / 4, RE = TY + 4, RQ = TY + 2;
+  const int m = L.m, n = L.n;
+  const bool inner = x0 >= kSwPad && x0 + kSwX + kSwPad <= m && y0 >= 2 && y0 + TY + 2 <= n;
+  float* qb = st + 3 * RE * kSwW;
+  if (inner) {
+    const size_t g0 = (size_t)(y0 - 2) * m + (x0 - kSwPad);
+    for (int t = threadIdx.x; t < RE * q4; t += kSwThreads) {
+      const int r = t / q4, c4 = t - r * q4;
+      const size_t g = g0 + (size_t)r * m + 4 * c4;
+      float* d = st + r * kSwW + 4 * c4;
+      cp_async16(d, S.ephi + g);
+      cp_async16(d + RE * kSwW, S.emu + g);
+      cp_async16(d + 2 * RE * kSwW, S.eka + g);
+    }
+    for (int t = threadIdx.x; t < RQ * q4; t += kSwThreads) {
+      const int r = t / q4, c4 = t - r * q4;
+      const size_t g = g0 + (size_t)(r + 1) * m + 4 * c4;
+      float* d = qb + r * kSwW + 4 * c4;
+      cp_async16(d, L.q + g);
+      cp_async16(d + RQ * kSwW, L.r1 + g);
+      cp_async16(d + 2 * RQ * kSwW, L.r2 + g);
+      cp_async16(d + 3 * RQ * kSwW, L.r3 + g);
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < RE * q4; t += kSwThreads) {
     const int r = t / q4, c4 = t - r * q4;
     const size_t g = (size_t)sw_row(y0 - 2 + r, n, L.nyn) * m + sw_col(x0 - kSwPad + 4 * c4, m);
     float* d = st + r * kSwW + 4 * c4;
@@ -455,8 +484,7 @@ __device__ __forceinline__ void sweep_tile_load(const Lev32& L, const SweepSrc& 
     cp_async16(d + RE * kSwW, S.emu + g);
     cp_async16(d + 2 * RE * kSwW, S.eka + g);
   }
-  float* qb = st + 3 * RE * kSwW;
-  for (int t = threadIdx.x; t < RQ * q4; t += blockDim.x) {
+  for (int t = threadIdx.x; t < RQ * q4; t += kSwThreads) {
     const int r = t / q4, c4 = t - r * q4;
     const size_t g = (size_t)sw_row(y0 - 1 + r, n, L.nyn) * m + sw_col(x0 - kSwPad + 4 * c4, m);
     float* d = qb + r * kSwW + 4 * c4;
@@ -485,67 +513,140 @@ __device__ __forceinline__ void sweep_tile_cell(const Coef32& k, const Coef32& k
   E2[ce] = d;
 }
 
-__global__ void __launch_bounds__(kSwThreads) k_sweep32_tiles(Lev32 L, SweepSrc S, Coef32 k, Coef32 kb, int ty) {
+// Red cells ((x + y) even) of a staged tile of tw x th cells and of its one-cell ring,
+// then (after a barrier) its black cells.
+//
+// A whole 64 x TY tile (FULL) maps each warp to 16 cells of one colour in each of two
+// adjacent rows.  A colour's cells in one row sit at every other word, all of one
+// parity, and the next row's at the other parity; with an even row stride (72 words)
+// the two half-warps then read disjoint bank sets, and every access of the cell update
+// (own cell, four neighbours, q and r) keeps that split, so none conflicts.  The red
+// work is the 32 interior red cells of each of the TY + 2 ring rows, in row pairs and
+// groups of 16, plus one item for the ring's 33rd red cell of each row (column x0-1 or
+// x0+64); the black work is the 32 black cells of each of the TY rows.  An edge tile
+// uses a plain loop over its ragged bounds.
+template <int TY, bool FULL>
+__device__ __forceinline__ void sweep_tile_compute(const Lev32& L, const Coef32& k, const Coef32& kb, float* E0, int x0,
+                                                   int y0, int tw, int th, const SweepSrc& S) {
+  constexpr int RE = TY + 4, RQ = TY + 2, kWarps = kSwThreads / 32;
+  float* E1 = E0 + RE * kSwW;
+  float* E2 = E1 + RE * kSwW;
+  const float* Qs = E2 + RE * kSwW;
+  const int m = L.m, n = L.n;
+  if (FULL) {
+    constexpr int kRingItems = (TY + 2 + 31) / 32;   // the ring's 33rd red cells, 32 rows per item
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int item = warp; item < TY + 2 + kRingItems; item += kWarps) {
+      int rr, cc;   // ring row (y = y0 - 1 + rr) and ring column (x = x0 - 1 + cc)
+      if (item < TY + 2) {
+        rr = 2 * (item >> 1) + (lane >> 4);
+        cc = 1 + ((x0 + y0 - 1 + rr) & 1) + 2 * (16 * (item & 1) + (lane & 15));
+      } else {
+        rr = 32 * (item - (TY + 2)) + lane;
+        if (rr >= TY + 2) continue;
+        cc = ((x0 + y0 - 2 + rr) & 1) == 0 ? 0 : kSwX + 1;
+      }
+      const int y = y0 - 1 + rr;
+      if (L.nyn && (y < 0 || y >= n)) continue;   // Neumann ghost rows hold no cells
+      const bool bnd = L.nyn && (y == 0 || y == n - 1);
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, RQ * kSwW,
+                      rr * kSwW + cc + kSwPad - 1);
+    }
+    __syncthreads();
+    // black cells; a warp then writes the 2 x 32 cells of its item (its black cells and
+    // the red ones between them, final since the barrier) to the destination copy
+    for (int item = warp; item < TY; item += kWarps) {
+      const int r0 = 2 * (item >> 1), c0 = 32 * (item & 1);
+      const int rr = r0 + (lane >> 4), y = y0 + rr;
+      const int cc = ((x0 + y + 1) & 1) + 2 * (16 * (item & 1) + (lane & 15));
+      const bool bnd = L.nyn && (y == 0 || y == n - 1);
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, RQ * kSwW,
+                      (rr + 1) * kSwW + cc + kSwPad);
+      __syncwarp();
+      for (int v = lane; v < 48; v += 32) {   // 3 planes x 2 rows x 8 float4
+        const int pl = v >> 4, row = (v >> 3) & 1, c4 = v & 7;
+        const float* src = E0 + pl * RE * kSwW + (r0 + row + 2) * kSwW + kSwPad + c0 + 4 * c4;
+        float* dst = (pl == 0 ? S.dphi : pl == 1 ? S.dmu : S.dka) + (size_t)(y0 + r0 + row) * m + x0 + c0 + 4 * c4;
+        *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
+      }
+    }
+    return;
+  }
+  {
+    const int rw = tw + 2, per = (rw + 1) >> 1, rows = th + 2;
+    for (int t = threadIdx.x; t < rows * per; t += kSwThreads) {
+      const int rr = t / per, y = y0 - 1 + rr;
+      const int cc = 2 * (t - rr * per) + ((x0 - 1 + y) & 1);
+      if (cc >= rw) continue;
+      if (L.nyn && (y < 0 || y >= n)) continue;   // Neumann ghost rows hold no cells
+      const bool bnd = L.nyn && (y == 0 || y == n - 1);
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, RQ * kSwW,
+                      rr * kSwW + cc + kSwPad - 1);
+    }
+  }
+  __syncthreads();
+  {
+    const int per = tw >> 1;
+    for (int t = threadIdx.x; t < th * per; t += kSwThreads) {
+      const int rr = t / per, y = y0 + rr;
+      const int cc = 2 * (t - rr * per) + ((x0 + y + 1) & 1);
+      const bool bnd = L.nyn && (y == 0 || y == n - 1);
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, RQ * kSwW,
+                      (rr + 1) * kSwW + cc + kSwPad);
+    }
+  }
+  __syncthreads();
+  // the tile to the destination copy, float4 rows
+  const int q4 = tw >> 2;
+  for (int t = threadIdx.x; t < th * q4; t += kSwThreads) {
+    const int rr = t / q4, c4 = t - rr * q4;
+    const size_t g = (size_t)(y0 + rr) * m + x0 + 4 * c4;
+    const int se = (rr + 2) * kSwW + kSwPad + 4 * c4;
+    *reinterpret_cast<float4*>(S.dphi + g) = *reinterpret_cast<const float4*>(E0 + se);
+    *reinterpret_cast<float4*>(S.dmu + g) = *reinterpret_cast<const float4*>(E1 + se);
+    *reinterpret_cast<float4*>(S.dka + g) = *reinterpret_cast<const float4*>(E2 + se);
+  }
+}
+
+template <int TY>
+__global__ void __launch_bounds__(kSwThreads) k_sweep32_tiles(Lev32 L, SweepSrc S, Coef32 k, Coef32 kb) {
   extern __shared__ float4 sw_smem[];
   pdl_enter();
+  constexpr int SF = kSwW * (3 * (TY + 4) + 4 * (TY + 2));
   const int m = L.m, n = L.n;
-  const int tiles_x = (m + kSwX - 1) / kSwX, ntiles = tiles_x * ((n + ty - 1) / ty);
-  const int SF = sweep_stage_floats(ty), RE = ty + 4, RQ = ty + 2;
+  const int tiles_x = (m + kSwX - 1) / kSwX, ntiles = tiles_x * ((n + TY - 1) / TY);
   float* const base = reinterpret_cast<float*>(sw_smem);   // stage s at base + s * SF
   int tile = blockIdx.x;
-  if (tile < ntiles) sweep_tile_load(L, S, (tile % tiles_x) * kSwX, (tile / tiles_x) * ty, ty, base);
+  if (tile < ntiles) sweep_tile_load<TY>(L, S, (tile % tiles_x) * kSwX, (tile / tiles_x) * TY, base);
   cp_async_commit();
   for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+    // this tile's copies have landed (every thread's), and every warp is done with the
+    // previous tile, whose stage the next tile's copies now reuse
+    cp_async_wait_all();
+    __syncthreads();
     const int next = tile + gridDim.x;
-    if (next < ntiles)
-      sweep_tile_load(L, S, (next % tiles_x) * kSwX, (next / tiles_x) * ty, ty, base + ((it + 1) & 1) * SF);
-    cp_async_commit();
-    cp_async_wait_prev();
-    __syncthreads();
+    if (next < ntiles) {
+      sweep_tile_load<TY>(L, S, (next % tiles_x) * kSwX, (next / tiles_x) * TY, base + ((it + 1) & 1) * SF);
+      cp_async_commit();
+    }
     float* E0 = base + (it & 1) * SF;
-    float* E1 = E0 + RE * kSwW;
-    float* E2 = E1 + RE * kSwW;
-    const float* Qs = E2 + RE * kSwW;
-    const int x0 = (tile % tiles_x) * kSwX, y0 = (tile / tiles_x) * ty;
-    const int tw = min(kSwX, m - x0), th = min(ty, n - y0);
-    // red cells ((x + y) even) of the tile and its ring: rows y0-1 .. y0+th, columns x0-1 .. x0+tw
-    {
-      const int rw = tw + 2, per = (rw + 1) >> 1;
-      for (int t = threadIdx.x; t < (th + 2) * per; t += blockDim.x) {
-        const int rr = t / per, y = y0 - 1 + rr;
-        const int cc = 2 * (t - rr * per) + ((x0 - 1 + y) & 1);
-        if (cc >= rw || (L.nyn && (y < 0 || y >= n))) continue;   // Neumann ghost rows hold no cells
-        const bool bnd = L.nyn && (y == 0 || y == n - 1);
-        sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, RQ * kSwW,
-                        rr * kSwW + cc + kSwPad - 1);
-      }
-    }
-    __syncthreads();
-    // black cells ((x + y) odd) of the tile
-    {
-      const int per = tw >> 1;
-      for (int t = threadIdx.x; t < th * per; t += blockDim.x) {
-        const int rr = t / per, y = y0 + rr;
-        const int cc = 2 * (t - rr * per) + ((x0 + y + 1) & 1);
-        const bool bnd = L.nyn && (y == 0 || y == n - 1);
-        sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, RQ * kSwW,
-                        (rr + 1) * kSwW + cc + kSwPad);
-      }
-    }
-    __syncthreads();
-    // the tile to the destination copy, float4 rows
-    {
-      const int q4 = tw >> 2;
-      for (int t = threadIdx.x; t < th * q4; t += blockDim.x) {
-        const int rr = t / q4, c4 = t - rr * q4;
-        const size_t g = (size_t)(y0 + rr) * m + x0 + 4 * c4;
-        const int se = (rr + 2) * kSwW + kSwPad + 4 * c4;
-        *reinterpret_cast<float4*>(S.dphi + g) = *reinterpret_cast<const float4*>(E0 + se);
-        *reinterpret_cast<float4*>(S.dmu + g) = *reinterpret_cast<const float4*>(E1 + se);
-        *reinterpret_cast<float4*>(S.dka + g) = *reinterpret_cast<const float4*>(E2 + se);
-      }
-    }
-    __syncthreads();   // the stage is reloaded two tiles on
+    const int x0 = (tile % tiles_x) * kSwX, y0 = (tile / tiles_x) * TY;
+    const int tw = min(kSwX, m - x0), th = min(TY, n - y0);
+    if (tw == kSwX && th == TY)
+      sweep_tile_compute<TY, true>(L, k, kb, E0, x0, y0, tw, th, S);
+    else
+      sweep_tile_compute<TY, false>(L, k, kb, E0, x0, y0, tw, th, S);
+  }
+}
+
+// The instantiation for a tile height (4, 8, 16 or 32 rows).
+using SweepKernel = void (*)(Lev32, SweepSrc, Coef32, Coef32);
+SweepKernel sweep_kernel(int ty) {
+  switch (ty) {
+    case 4: return k_sweep32_tiles<4>;
+    case 8: return k_sweep32_tiles<8>;
+    case 16: return k_sweep32_tiles<16>;
+    default: return k_sweep32_tiles<32>;
   }
 }
 
@@ -558,30 +659,21 @@ bool sweep_tiled(const mpfc_s* H, const Lev32& F) {
          sweep_tiles_per_sm(H->sweep_tile_rows) > 0;
 }
 
-// Resident CTAs per SM of the tiled sweep with tiles of ty rows on the current device,
-// cached per device and tile height.  The kernel's dynamic shared-memory limit is raised
-// once per device to what the tallest tiles (32 rows) need, so that no later setting
-// can leave it below a height whose occupancy is cached.
+// Resident CTAs per SM of the tiled sweep with tiles of ty rows on the current device
+// (raises that instantiation's dynamic shared-memory limit first), cached per device
+// and tile height; 0 if the GPU cannot run it.
 int sweep_tiles_per_sm(int ty) {
   constexpr int kDevs = 64;
   static std::atomic<int> cache[kDevs][6];   // tile heights 1 << idx; 0: not queried yet
-  static std::atomic<int> raised[kDevs];
   int dev = 0, idx = 0;
   while ((1 << idx) < ty && idx < 5) ++idx;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) dev = -1;
   if (dev >= 0)
     if (int c = cache[dev][idx].load()) return c;
-  const int max_smem = (int)(2 * sizeof(float) * (size_t)sweep_stage_floats(32));
-  if (dev < 0 || !raised[dev].load()) {
-    if (cudaFuncSetAttribute(k_sweep32_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) != cudaSuccess) {
-      (void)cudaGetLastError();
-      return 0;
-    }
-    if (dev >= 0) raised[dev].store(1);
-  }
   const size_t smem = 2 * sizeof(float) * (size_t)sweep_stage_floats(ty);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep32_tiles, kSwThreads, smem) != cudaSuccess ||
+  if (cudaFuncSetAttribute(sweep_kernel(ty), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(ty), kSwThreads, smem) != cudaSuccess ||
       per_sm < 1) {
     (void)cudaGetLastError();
     return 0;
@@ -600,7 +692,7 @@ void launch_sweep_tiles(const mpfc_s* H, const Lev32& F, const float* fp, const 
   const long long cap = (long long)per_sm * mpfc::sm_count();
   const int grid = (int)(ntiles < cap ? ntiles : cap);
   SweepSrc S = {fp, fm, fk, tp, tm, tk};
-  mpfc_launch(H->shape, k_sweep32_tiles, dim3(grid), dim3(kSwThreads), smem, s, F, S, kf, kb, ty);
+  mpfc_launch(H->shape, sweep_kernel(ty), dim3(grid), dim3(kSwThreads), smem, s, F, S, kf, kb);
 }
 
 // `sweeps` red-black sweeps of one level, one launch per colour.  (A single-launch

@@ -70,8 +70,8 @@ struct mpfc_s {
   // mixed precision
   Lev32 lev32[mpfc::kMaxLevels];
   float* K3f[2] = {nullptr, nullptr};
-  int sweep_tile_rows = 0;         // FP32 one-launch sweeps: tile height (0: two launches per sweep)
-  long long sweep_tile_cells = 0;  // ... on levels of at least this many cells
+  int sweep_tile_rows = 16;                     // FP32 one-launch sweeps: tile height (0: two launches per sweep)
+  long long sweep_tile_cells = 2048LL * 2048;   // ... on levels of at least this many cells
   int outer_max = 0;
   // learned initial guess
   MpfcGuess guess;

@@ -248,6 +248,49 @@ def test_conv32_both_tensor_paths_match_oracle(G, tensor_path, use_tc, H, W):
     assert rel(ob.float().cpu().numpy(), ref) < 1e-2
 
 
+def test_tensor_path_wait_timeout_is_reported_and_recovers(G, tensor_path):
+    """The tcgen05 convolution's waits are bounded.  Through the test hook the first CTA
+    withholds the tensor copy of its first input row (no out-of-bounds access): the MMA
+    issuer's wait runs out after 2e6 clock cycles, the CTA drains the copies and MMAs it
+    issued, frees its tensor memory and returns; the status call reports the timeout once.
+    The next launch, with the hook off, matches the oracle and reports no failure."""
+    import ctypes
+    from oracle import cnn
+    lib = G._lib()
+    lib.mpfc_cnn_test_withhold_load.argtypes = [ctypes.c_int, ctypes.c_longlong]
+    tensor_path(1)
+    rng = np.random.default_rng(9)
+    B, H, W = 1, 6, 256
+    s = torch.cuda.current_stream().cuda_stream
+    xr, xd = bf16(rng.normal(size=(B, H, W, 32)))
+    w = rng.normal(scale=0.2, size=(9, 32, 32)).astype(np.float32)
+    wr = torch.from_numpy(w).bfloat16().float().double().numpy()
+    bias = rng.normal(size=32).astype(np.float32)
+    wk = torch.empty(32 * 288, dtype=torch.bfloat16, device="cuda")
+    assert lib.mpfc_cnn_pack_weights(torch.from_numpy(w).cuda().data_ptr(), 32, 32, 32, 32, 0, wk.data_ptr(), s) == 0
+    bd = torch.from_numpy(bias).cuda()
+    y = torch.full((B, H, W, 32), 7.0, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    assert lib.mpfc_cnn_tensor_path_status() == 0
+    try:
+        assert lib.mpfc_cnn_test_withhold_load(1, 2000000) == 0
+        assert lib.mpfc_cnn_conv_forward(xd.data_ptr(), B, H, W, 32, wk.data_ptr(), bd.data_ptr(), 32, 32, 1, None,
+                                         y.data_ptr(), None, s) == 0
+        torch.cuda.synchronize()
+    finally:
+        assert lib.mpfc_cnn_test_withhold_load(0, 0) == 0
+    assert lib.mpfc_cnn_tensor_path_status() == -4      # MPFC_ERR_NOT_CONVERGED: a wait gave up
+    assert lib.mpfc_cnn_tensor_path_status() == 0       # reported once
+    ref = cnn.conv3x3(xr, wr, bias.astype(np.float64))
+    assert np.all(y.cpu().numpy()[0, 0, :128] == 7.0)   # the aborted CTA's tile stays unwritten
+    y.fill_(7.0)
+    assert lib.mpfc_cnn_conv_forward(xd.data_ptr(), B, H, W, 32, wk.data_ptr(), bd.data_ptr(), 32, 32, 1, None,
+                                     y.data_ptr(), None, s) == 0
+    torch.cuda.synchronize()
+    assert lib.mpfc_cnn_tensor_path_status() == 0
+    assert rel(y.cpu().numpy(), ref) < 1e-4
+
+
 def test_learned_guess_same_on_both_tensor_paths(G, tensor_path):
     """The packaged 256 x 256 model gives the same initial residual (to FP32 accumulation
     order) whichever tensor-core path runs its 32 -> 32 layers."""
