@@ -64,6 +64,9 @@ def parse_args():
                          "launches at --size^2 (ncu capture of the network's top kernel)")
     ap.add_argument("--profile-smooth", action="store_true",
                     help="only the finest-level sweep kernel, two sweeps (ncu capture of the top kernel)")
+    ap.add_argument("--profile-sweep32", action="store_true",
+                    help="only the mixed-precision form's tiled FP32 sweep at 2048^2, two there-and-back pairs "
+                         "(ncu capture of the HBM-bound kernel)")
     return ap.parse_args()
 
 
@@ -298,6 +301,15 @@ def run_ours(args):
         p.precision = mpfc.MPFC_FP32_INNER
     if args.profile and args.form == "learned":
         p.guess = mpfc.MPFC_GUESS_LEARNED
+    if args.profile_sweep32:
+        big = mpfc.Solver(mpfc.default_params(m=2048, n=2048, h=w["h"], dt=0.02, precision=mpfc.MPFC_FP32_INNER))
+        big.set_state(inputs.noise_field(2048, 2048, 0.07, 0.05, 3))
+        big.set_fp32_sweep(16, 2048 * 2048)
+        us = [big.fp32_time_smooth(0, 2) * 1e3 / 2 for _ in range(2)]
+        big.close()
+        if rank == 0:
+            print(json.dumps({"profile_sweep32": True, "us_per_sweep": us}), flush=True)
+        return
     if args.profile_conv:
         r = conv32_timing(size, launches=4, flush_between=False)
         if rank == 0:

@@ -210,6 +210,14 @@ int mpfc_step_cycles(mpfc_t* h, int scheme, int ncycles, mpfc_step_info* info);
  * Synchronises. */
 int mpfc_set_guess_model(mpfc_t* h, const float* params, size_t count);
 
+/* The learned guess's correction on the current state, for tests of the inference
+ * against the network's definition (no counterpart in the paper): d_out (m*n device
+ * doubles, overwritten) receives what the guess adds to the extrapolation 2 phi^k -
+ * phi^{k-1} at the next step, sy times the network's output on the features of
+ * (phi^k, phi^{k-1}, phi^{k-2}).  Handle created with MPFC_GUESS_LEARNED and a model
+ * loaded, else MPFC_ERR_INVALID.  Asynchronous on the handle's stream. */
+int mpfc_guess_correction(mpfc_t* h, double* d_out);
+
 /* Mass h^2 sum phi^k (conserved, Sec. 3.3, first theorem).  Synchronises. */
 int mpfc_mass(mpfc_t* h, double* out);
 

@@ -491,10 +491,16 @@ __global__ void k_features(const double* __restrict__ p0, const double* __restri
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < G; i += (long long)gridDim.x * blockDim.x) {
     const double a = p0[off + i], c1 = p1[off + i], c2 = p2[off + i];
     __nv_bfloat162 lo = __floats2bfloat162_rn((float)((a - mean) * inv0), (float)((a - c1) * inv1));
-    __nv_bfloat162 hi = __floats2bfloat162_rn((float)((a - 2.0 * c1 + c2) * inv2), 0.f);
+    __nv_bfloat162 hi = __floats2bfloat162_rn((float)(((a - c1) - (c1 - c2)) * inv2), 0.f);
     xo[i] = make_uint2(*reinterpret_cast<unsigned*>(&lo), *reinterpret_cast<unsigned*>(&hi));
     if (y && pn) y[off + i] = (float)((pn[off + i] - 2.0 * a + c1) * inv3);
   }
+}
+
+// Mean of one field into means[0] (partials in means[1 ..]), for the solver's guess.
+void mpfc_cnn_mean(const double* phik, long long G, double* means, cudaStream_t s) {
+  k_mean_partial<<<dim3(kMeanBlocks, 1), 256, 0, s>>>(phik, G, means + 1);
+  k_mean_final<<<1, 32, 0, s>>>(means + 1, G, means);
 }
 
 // ---------------------------------------------------------------------------

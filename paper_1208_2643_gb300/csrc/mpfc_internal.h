@@ -19,15 +19,30 @@ struct Lev32 {
   float *xphi, *xmu, *xka;   // second copy of e for out-of-place sweeps (nullptr: none)
 };
 
+// Inference-kernel arguments of the learned guess's first and last layers: the
+// weights, rounded to bf16 as the network computes with them, travel as kernel
+// parameters, so the multiply-adds read them from the constant bank.
+struct GuessInArgs {
+  float w[27][32];   // [tap * 3 + channel][output channel]
+  float b[32];
+  double inv[3];     // 1 / (s0, s1, s2), the input normalisation
+};
+struct GuessOutArgs {
+  float w[9][32];    // [tap][input channel]
+  float b;
+  double scale;      // sy: the output's scale back to phi
+};
+
 // Learned-guess buffers in the workspace (MPFC_GUESS_LEARNED).
 struct MpfcGuess {
   float* params = nullptr;     // fp32 model blob (normalisation, weights, biases)
   void* wk[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // packed bf16 weights
-  void* x = nullptr;           // network input, bf16 [m*n][4]
   void* act[2] = {nullptr, nullptr};   // activations, bf16 [m*n][32]
   double* phikm2 = nullptr;    // phi^{k-2}
   double* mean = nullptr;
   float norms_host[4] = {1.f, 1.f, 1.f, 1.f};   // host copy of the normalisation scales
+  GuessInArgs in_args;         // first layer (with the input features), host copy
+  GuessOutArgs out_args;       // last layer, host copy
   bool loaded = false;
 };
 
@@ -142,7 +157,8 @@ int mpfc_fp32_enqueue_step(mpfc_s* H, int scheme, cudaStream_t cs, cudaGraphCond
 int mpfc_fp32_step_stream(mpfc_s* H, int scheme);
 int mpfc_host_continue(const mpfc::Ctl* c);
 
-// learned initial guess (guess_cnn.cu)
+// learned initial guess (guess_cnn.cu, cnn.cu)
+void mpfc_cnn_mean(const double* phik, long long G, double* means, cudaStream_t s);
 size_t mpfc_guess_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base);
 bool mpfc_has_guess_model(const mpfc_s* H);
 void mpfc_enqueue_learned_guess(mpfc_s* H, cudaStream_t s);

@@ -292,7 +292,7 @@ def main(argv):
     t0 = time.time()
     n_traj = int(argv[0]) if len(argv) > 0 else 40
     steps = int(argv[1]) if len(argv) > 1 else 500
-    epochs = int(argv[2]) if len(argv) > 2 else 1
+    epochs = int(argv[2]) if len(argv) > 2 else 8
     out = argv[3] if len(argv) > 3 else DEFAULT_PATH
     trajs = generate_trajectories(n_traj, steps)
     print(f"data: {n_traj} x {steps} steps in {time.time() - t0:.1f} s", flush=True)

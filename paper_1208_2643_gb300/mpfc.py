@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
     lib.mpfc_set_fp32_sweep.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
     lib.mpfc_op_learned_guess.argtypes = [_VP]
+    lib.mpfc_guess_correction.argtypes = [_VP, _VP]
     lib.mpfc_batch_workspace_bytes.argtypes = [ctypes.c_int, P(mpfc_params)]
     lib.mpfc_batch_workspace_bytes.restype = ctypes.c_size_t
     lib.mpfc_batch_create.argtypes = [ctypes.c_int, P(mpfc_params), _VP, ctypes.c_size_t, _VP, P(_VP)]
