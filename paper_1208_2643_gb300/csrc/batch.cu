@@ -838,7 +838,10 @@ static int batch_run(mpfc_batch_s* B, int scheme, int nsteps, int fixed, int* st
   }
   kb_reset<<<(B->count + 127) / 128, 128, 0, B->stream>>>(B->d_ctl, B->d_glob, B->count, fixed);
   BCK(cudaGetLastError());
-  for (int k = 0; k < nsteps; ++k) BCK(cudaGraphLaunch(B->exec[scheme - 1], B->stream));
+  for (int k = 0; k < nsteps; ++k) {
+    MpfcRange range("mpfc batch step");
+    BCK(cudaGraphLaunch(B->exec[scheme - 1], B->stream));
+  }
   if (!sync) return MPFC_OK;
   std::vector<BCtl> c(B->count);
   BCK(cudaMemcpyAsync(c.data(), B->d_ctl, sizeof(BCtl) * B->count, cudaMemcpyDeviceToHost, B->stream));

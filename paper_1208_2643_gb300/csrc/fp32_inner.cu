@@ -1038,6 +1038,7 @@ int mpfc_fp32_enqueue_step(mpfc_s* H, int scheme, cudaStream_t cs, cudaGraphCond
 }
 
 int mpfc_fp32_step_stream(mpfc_s* H, int scheme) {
+  MpfcRange range("mpfc step (FP32 inner)");
   cudaStream_t s = H->stream;
   mpfc_enqueue_prologue(H, scheme, s);
   enqueue_defect(H, scheme, 0, 0, 0, s);
@@ -1050,6 +1051,7 @@ int mpfc_fp32_step_stream(mpfc_s* H, int scheme) {
       return MPFC_ERR_CUDA;
     }
     if (!mpfc_host_continue(&c)) break;
+    MpfcRange orange("outer iteration");
     outer_body(H, scheme, s, 0, 0);
   }
   mpfc_enqueue_commit(H, scheme, s);

@@ -42,6 +42,13 @@ using namespace mpfc;
 
 static char g_last_cuda_error[512];
 
+const char* mpfc_level_name(int l) {
+  static const char* const names[kMaxLevels] = {"level 0",  "level 1",  "level 2",  "level 3",  "level 4",  "level 5",
+                                                "level 6",  "level 7",  "level 8",  "level 9",  "level 10", "level 11",
+                                                "level 12", "level 13", "level 14", "level 15"};
+  return (l >= 0 && l < kMaxLevels) ? names[l] : "level";
+}
+
 namespace mpfc {
 int sm_count() {
   constexpr int kDevs = 64;
@@ -550,6 +557,7 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
   const int lt = tail_first_level(H);
   const int down = lt < L ? lt : L - 1;   // levels smoothed and restricted by per-level launches
   for (int l = 0; l < down; ++l) {
+    MpfcRange range(mpfc_level_name(l));
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
     launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu1, s);
@@ -557,9 +565,13 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
                 H->coef[SCH - 1][l], 1);
     mpfc_launch(sh, k_tau<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, C, H->coef[SCH - 1][l + 1]);
   }
-  if (lt < L) launch_tail<SCH>(H, lt, s);
-  else launch_coarse<SCH>(H, H->lev[L - 1], H->coef[SCH - 1][L - 1], s);
+  {
+    MpfcRange range(lt < L ? "coarse tail" : "coarsest solve");
+    if (lt < L) launch_tail<SCH>(H, lt, s);
+    else launch_coarse<SCH>(H, H->lev[L - 1], H->coef[SCH - 1][L - 1], s);
+  }
   for (int l = down - 1; l >= 0; --l) {
+    MpfcRange range(mpfc_level_name(l));
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
     ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n, C.nyn};
@@ -732,6 +744,7 @@ static bool host_continue(const Ctl& c) {
 // One step launched kernel by kernel on the stream, with the loop decision read
 // back after every residual test (same kernels, same order as the graph).
 static int step_stream_mode(mpfc_s* H, int scheme) {
+  MpfcRange range("mpfc step");
   cudaStream_t s = H->stream;
   if (H->p.precision == MPFC_FP32_INNER) return mpfc_fp32_step_stream(H, scheme);
   if (scheme == 1) {
@@ -746,6 +759,7 @@ static int step_stream_mode(mpfc_s* H, int scheme) {
     CK(cudaMemcpyAsync(&c, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (!host_continue(c)) break;
+    MpfcRange vrange("V-cycle");
     if (scheme == 1) {
       enqueue_vcycle<1>(H, s);
       enqueue_resnorm<1>(H, 1, 0, 0, s);
@@ -770,7 +784,10 @@ static int launch_steps(mpfc_s* H, int scheme, int nsteps) {
     }
     return MPFC_OK;
   }
-  for (int k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
+  for (int k = 0; k < nsteps; ++k) {
+    MpfcRange range("mpfc step");
+    CK(cudaGraphLaunch(H->exec[scheme - 1][0], H->stream));
+  }
   return MPFC_OK;
 }
 

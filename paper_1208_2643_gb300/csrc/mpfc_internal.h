@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -133,6 +134,18 @@ inline void mpfc_launch(const mpfc_launch_shape& sh, void (*kern)(KArgs...), dim
   cfg.numAttrs = ((long long)g.x * g.y * g.z <= sh.pdl_blocks) ? 1 : 0;
   (void)cudaLaunchKernelEx(&cfg, kern, args...);
 }
+
+// NVTX range for profiler timelines (a no-op unless a tool is attached): a time step
+// around its graph launch; in MPFC_LAUNCH_STREAM mode also each V-cycle and each
+// level's launches, which then show the device work they enqueue.
+struct MpfcRange {
+  explicit MpfcRange(const char* name) { nvtxRangePushA(name); }
+  ~MpfcRange() { nvtxRangePop(); }
+  MpfcRange(const MpfcRange&) = delete;
+  MpfcRange& operator=(const MpfcRange&) = delete;
+};
+// "level 0" .. "level 15" (static names for the per-level ranges)
+const char* mpfc_level_name(int l);
 
 void mpfc_set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void mpfc_drop_graphs(mpfc_s* H);
