@@ -11,9 +11,12 @@
 // coarsest grid.  Then u += e in FP64, and the loop test runs on the FP64 residual.
 // The converged answer is therefore the FP64 solution at the FP64 tolerance; FP32
 // only limits how much each outer iteration gains.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 
 #include <vector>
 
@@ -430,8 +433,49 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// floats of one stage: e (3 planes, ty + 4 rows) then q, r1, r2, r3 (ty + 2 rows)
-__host__ __device__ __forceinline__ int sweep_stage_floats(int ty) { return kSwW * (3 * (ty + 4) + 4 * (ty + 2)); }
+// One stage: e (3 planes of ty + 4 staged rows) then q, r1, r2, r3 (ty + 2 rows), each plane's
+// block starting on a 128-byte boundary (tensor copies write there).
+__host__ __device__ __forceinline__ int sweep_plane_e(int ty) { return (kSwW * (ty + 4) + 31) / 32 * 32; }
+__host__ __device__ __forceinline__ int sweep_plane_q(int ty) { return (kSwW * (ty + 2) + 31) / 32 * 32; }
+__host__ __device__ __forceinline__ int sweep_stage_floats(int ty) { return 3 * sweep_plane_e(ty) + 4 * sweep_plane_q(ty); }
+// dynamic shared memory of the kernel: two stages, two mbarriers, alignment slack
+__host__ __device__ __forceinline__ size_t sweep_smem_bytes(int ty) {
+  return 2 * sizeof(float) * (size_t)sweep_stage_floats(ty) + 16 + 128;
+}
+
+// Tensor maps of the planes a tile stages (interior tiles): the source copy of e and q, r.
+struct SweepMaps {
+  CUtensorMap e[3];
+  CUtensorMap qr[4];
+};
+
+__device__ __forceinline__ void sw_bar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+}
+__device__ __forceinline__ bool sw_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for a stage's tensor copies (about 1 s at the GPU's clock); false if
+// they did not arrive.
+constexpr long long kSwSpinLimit = 2000000000ll;
+__device__ __forceinline__ bool sw_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!sw_try_wait(bar, parity))
+    if (clock64() - t0 > kSwSpinLimit) return false;
+  return true;
+}
+__device__ __forceinline__ void sw_tma_2d(float* dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
 
 __device__ __forceinline__ int sw_col(int x, int m) { x %= m; return x < 0 ? x + m : x; }
 __device__ __forceinline__ int sw_row(int y, int n, int nyn) {
@@ -445,16 +489,32 @@ struct SweepSrc {
   float *dphi, *dmu, *dka;         // destination copy
 };
 
-// Stages the tile (x0, y0) of TY rows: cp.async copies of 16 bytes, e rows y0-2 .. y0+TY+1
-// and q / r rows y0-1 .. y0+TY, columns x0-4 .. x0+67.  A tile that reaches no domain
-// edge addresses rows and columns directly; the others wrap them (periodic) or clamp
-// the rows (Neumann ghost rows, (A.7)).
+// Stages the tile (x0, y0) of TY rows: e rows y0-2 .. y0+TY+1 and q / r rows y0-1 ..
+// y0+TY, columns x0-4 .. x0+67.  A tile that reaches no domain edge is staged by one
+// thread with seven 2-D tensor copies (boxes of 72 columns, x0-4 a multiple of 4, so
+// 16-byte aligned) completing on the stage's mbarrier; the others by 16-byte cp.async
+// copies of every thread, wrapping the columns and rows (periodic) or clamping the rows
+// (Neumann ghost rows, (A.7)).  Returns whether the tensor copies were used.
 template <int TY>
-__device__ __forceinline__ void sweep_tile_load(const Lev32& L, const SweepSrc& S, int x0, int y0, float* st) {
+__device__ __forceinline__ bool sweep_tile_load(const Lev32& L, const SweepSrc& S, const SweepMaps& M, bool use_tma,
+                                                int x0, int y0, float* st, uint32_t bar) {
   constexpr int q4 = kSwW / 4, RE = TY + 4, RQ = TY + 2;
+  const int PE = sweep_plane_e(TY), PQ = sweep_plane_q(TY);
   const int m = L.m, n = L.n;
   const bool inner = x0 >= kSwPad && x0 + kSwX + kSwPad <= m && y0 >= 2 && y0 + TY + 2 <= n;
-  float* qb = st + 3 * RE * kSwW;
+  float* qb = st + 3 * PE;
+  if (inner && use_tma) {
+    if (threadIdx.x == 0) {
+      // the stage was last read through the generic proxy (after the block barrier that
+      // precedes this call); order those reads before the tensor copies' writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      constexpr uint32_t kBytes = (uint32_t)(sizeof(float) * kSwW * (3 * RE + 4 * RQ));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBytes) : "memory");
+      for (int p = 0; p < 3; ++p) sw_tma_2d(st + p * PE, &M.e[p], x0 - kSwPad, y0 - 2, bar);
+      for (int p = 0; p < 4; ++p) sw_tma_2d(qb + p * PQ, &M.qr[p], x0 - kSwPad, y0 - 1, bar);
+    }
+    return true;
+  }
   if (inner) {
     const size_t g0 = (size_t)(y0 - 2) * m + (x0 - kSwPad);
     for (int t = threadIdx.x; t < RE * q4; t += kSwThreads) {
@@ -462,37 +522,40 @@ __device__ __forceinline__ void sweep_tile_load(const Lev32& L, const SweepSrc& 
       const size_t g = g0 + (size_t)r * m + 4 * c4;
       float* d = st + r * kSwW + 4 * c4;
       cp_async16(d, S.ephi + g);
-      cp_async16(d + RE * kSwW, S.emu + g);
-      cp_async16(d + 2 * RE * kSwW, S.eka + g);
+      cp_async16(d + PE, S.emu + g);
+      cp_async16(d + 2 * PE, S.eka + g);
     }
     for (int t = threadIdx.x; t < RQ * q4; t += kSwThreads) {
       const int r = t / q4, c4 = t - r * q4;
       const size_t g = g0 + (size_t)(r + 1) * m + 4 * c4;
       float* d = qb + r * kSwW + 4 * c4;
       cp_async16(d, L.q + g);
-      cp_async16(d + RQ * kSwW, L.r1 + g);
-      cp_async16(d + 2 * RQ * kSwW, L.r2 + g);
-      cp_async16(d + 3 * RQ * kSwW, L.r3 + g);
+      cp_async16(d + PQ, L.r1 + g);
+      cp_async16(d + 2 * PQ, L.r2 + g);
+      cp_async16(d + 3 * PQ, L.r3 + g);
     }
-    return;
+    cp_async_commit();
+    return false;
   }
   for (int t = threadIdx.x; t < RE * q4; t += kSwThreads) {
     const int r = t / q4, c4 = t - r * q4;
     const size_t g = (size_t)sw_row(y0 - 2 + r, n, L.nyn) * m + sw_col(x0 - kSwPad + 4 * c4, m);
     float* d = st + r * kSwW + 4 * c4;
     cp_async16(d, S.ephi + g);
-    cp_async16(d + RE * kSwW, S.emu + g);
-    cp_async16(d + 2 * RE * kSwW, S.eka + g);
+    cp_async16(d + PE, S.emu + g);
+    cp_async16(d + 2 * PE, S.eka + g);
   }
   for (int t = threadIdx.x; t < RQ * q4; t += kSwThreads) {
     const int r = t / q4, c4 = t - r * q4;
     const size_t g = (size_t)sw_row(y0 - 1 + r, n, L.nyn) * m + sw_col(x0 - kSwPad + 4 * c4, m);
     float* d = qb + r * kSwW + 4 * c4;
     cp_async16(d, L.q + g);
-    cp_async16(d + RQ * kSwW, L.r1 + g);
-    cp_async16(d + 2 * RQ * kSwW, L.r2 + g);
-    cp_async16(d + 3 * RQ * kSwW, L.r3 + g);
+    cp_async16(d + PQ, L.r1 + g);
+    cp_async16(d + 2 * PQ, L.r2 + g);
+    cp_async16(d + 3 * PQ, L.r3 + g);
   }
+  cp_async_commit();
+  return false;
 }
 
 // The cell update of smooth32_cell on staged values: ce indexes the cell in the e
@@ -528,10 +591,11 @@ __device__ __forceinline__ void sweep_tile_cell(const Coef32& k, const Coef32& k
 template <int TY, bool FULL>
 __device__ __forceinline__ void sweep_tile_compute(const Lev32& L, const Coef32& k, const Coef32& kb, float* E0, int x0,
                                                    int y0, int tw, int th, const SweepSrc& S) {
-  constexpr int RE = TY + 4, RQ = TY + 2, kWarps = kSwThreads / 32;
-  float* E1 = E0 + RE * kSwW;
-  float* E2 = E1 + RE * kSwW;
-  const float* Qs = E2 + RE * kSwW;
+  constexpr int kWarps = kSwThreads / 32;
+  const int PE = sweep_plane_e(TY), PQ = sweep_plane_q(TY);
+  float* E1 = E0 + PE;
+  float* E2 = E1 + PE;
+  const float* Qs = E2 + PE;
   const int m = L.m, n = L.n;
   if (FULL) {
     constexpr int kRingItems = (TY + 2 + 31) / 32;   // the ring's 33rd red cells, 32 rows per item
@@ -549,7 +613,7 @@ __device__ __forceinline__ void sweep_tile_compute(const Lev32& L, const Coef32&
       const int y = y0 - 1 + rr;
       if (L.nyn && (y < 0 || y >= n)) continue;   // Neumann ghost rows hold no cells
       const bool bnd = L.nyn && (y == 0 || y == n - 1);
-      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, RQ * kSwW,
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, PQ,
                       rr * kSwW + cc + kSwPad - 1);
     }
     __syncthreads();
@@ -560,12 +624,12 @@ __device__ __forceinline__ void sweep_tile_compute(const Lev32& L, const Coef32&
       const int rr = r0 + (lane >> 4), y = y0 + rr;
       const int cc = ((x0 + y + 1) & 1) + 2 * (16 * (item & 1) + (lane & 15));
       const bool bnd = L.nyn && (y == 0 || y == n - 1);
-      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, RQ * kSwW,
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, PQ,
                       (rr + 1) * kSwW + cc + kSwPad);
       __syncwarp();
       for (int v = lane; v < 48; v += 32) {   // 3 planes x 2 rows x 8 float4
         const int pl = v >> 4, row = (v >> 3) & 1, c4 = v & 7;
-        const float* src = E0 + pl * RE * kSwW + (r0 + row + 2) * kSwW + kSwPad + c0 + 4 * c4;
+        const float* src = E0 + pl * PE + (r0 + row + 2) * kSwW + kSwPad + c0 + 4 * c4;
         float* dst = (pl == 0 ? S.dphi : pl == 1 ? S.dmu : S.dka) + (size_t)(y0 + r0 + row) * m + x0 + c0 + 4 * c4;
         *reinterpret_cast<float4*>(dst) = *reinterpret_cast<const float4*>(src);
       }
@@ -580,7 +644,7 @@ __device__ __forceinline__ void sweep_tile_compute(const Lev32& L, const Coef32&
       if (cc >= rw) continue;
       if (L.nyn && (y < 0 || y >= n)) continue;   // Neumann ghost rows hold no cells
       const bool bnd = L.nyn && (y == 0 || y == n - 1);
-      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, RQ * kSwW,
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 1) * kSwW + cc + kSwPad - 1, Qs, PQ,
                       rr * kSwW + cc + kSwPad - 1);
     }
   }
@@ -591,7 +655,7 @@ __device__ __forceinline__ void sweep_tile_compute(const Lev32& L, const Coef32&
       const int rr = t / per, y = y0 + rr;
       const int cc = 2 * (t - rr * per) + ((x0 + y + 1) & 1);
       const bool bnd = L.nyn && (y == 0 || y == n - 1);
-      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, RQ * kSwW,
+      sweep_tile_cell(k, kb, bnd, E0, E1, E2, (rr + 2) * kSwW + cc + kSwPad, Qs, PQ,
                       (rr + 1) * kSwW + cc + kSwPad);
     }
   }
@@ -609,38 +673,75 @@ __device__ __forceinline__ void sweep_tile_compute(const Lev32& L, const Coef32&
 }
 
 template <int TY>
-__global__ void __launch_bounds__(kSwThreads) k_sweep32_tiles(Lev32 L, SweepSrc S, Coef32 k, Coef32 kb) {
-  extern __shared__ float4 sw_smem[];
+__global__ void __launch_bounds__(kSwThreads) k_sweep32_tiles(Lev32 L, SweepSrc S, Coef32 k, Coef32 kb,
+                                                              const __grid_constant__ SweepMaps M, int use_tma) {
+  extern __shared__ unsigned char sw_raw[];
+  const int SF = sweep_stage_floats(TY);
+  float* const base = reinterpret_cast<float*>(
+      sw_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(sw_raw) & 127u)) & 127u));   // stage s at base + s SF
+  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(base + 2 * SF);            // mbarrier of stage s: bar0 + 8 s
+  if (threadIdx.x == 0) {
+    sw_bar_init(bar0);
+    sw_bar_init(bar0 + 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   pdl_enter();
-  constexpr int SF = kSwW * (3 * (TY + 4) + 4 * (TY + 2));
   const int m = L.m, n = L.n;
   const int tiles_x = (m + kSwX - 1) / kSwX, ntiles = tiles_x * ((n + TY - 1) / TY);
-  float* const base = reinterpret_cast<float*>(sw_smem);   // stage s at base + s * SF
+  uint32_t parity = 0u;   // bit s: phase parity of stage s's next tensor-copy wait
   int tile = blockIdx.x;
-  if (tile < ntiles) sweep_tile_load<TY>(L, S, (tile % tiles_x) * kSwX, (tile / tiles_x) * TY, base);
-  cp_async_commit();
+  bool tma_cur = false;
+  if (tile < ntiles)
+    tma_cur = sweep_tile_load<TY>(L, S, M, use_tma != 0, (tile % tiles_x) * kSwX, (tile / tiles_x) * TY, base, bar0);
   for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
-    // this tile's copies have landed (every thread's), and every warp is done with the
-    // previous tile, whose stage the next tile's copies now reuse
-    cp_async_wait_all();
-    __syncthreads();
-    const int next = tile + gridDim.x;
-    if (next < ntiles) {
-      sweep_tile_load<TY>(L, S, (next % tiles_x) * kSwX, (next / tiles_x) * TY, base + ((it + 1) & 1) * SF);
-      cp_async_commit();
+    // this tile's copies have landed (every thread's, or the tensor copies on the
+    // stage's mbarrier), and every warp is done with the previous tile, whose stage
+    // the next tile's copies now reuse
+    const int st = it & 1;
+    bool ok = true;
+    if (tma_cur) {
+      ok = sw_wait(bar0 + 8u * st, (parity >> st) & 1u);
+      parity ^= 1u << st;
+    } else {
+      cp_async_wait_all();
     }
-    float* E0 = base + (it & 1) * SF;
+    if (__syncthreads_or(!ok)) {
+      // a tensor copy did not arrive: poison this CTA's tiles so that the defect the
+      // solver computes from them is not finite and the step reports DIVERGED, give
+      // the copy a last bounded wait, and stop
+      const float nan = __int_as_float(0x7fffffff);
+      for (int t2 = tile; t2 < ntiles; t2 += gridDim.x) {
+        const int x0 = (t2 % tiles_x) * kSwX, y0 = (t2 / tiles_x) * TY;
+        const int tw = min(kSwX, m - x0), th = min(TY, n - y0);
+        for (int q = threadIdx.x; q < tw * th; q += kSwThreads) {
+          const size_t g = (size_t)(y0 + q / tw) * m + x0 + q % tw;
+          S.dphi[g] = nan;
+          S.dmu[g] = nan;
+          S.dka[g] = nan;
+        }
+      }
+      if (threadIdx.x == 0) sw_wait(bar0 + 8u * st, (parity >> st) & 1u);
+      return;
+    }
+    const int next = tile + gridDim.x;
+    bool tma_next = false;
+    if (next < ntiles)
+      tma_next = sweep_tile_load<TY>(L, S, M, use_tma != 0, (next % tiles_x) * kSwX, (next / tiles_x) * TY,
+                                     base + (st ^ 1) * SF, bar0 + 8u * (st ^ 1));
+    float* E0 = base + st * SF;
     const int x0 = (tile % tiles_x) * kSwX, y0 = (tile / tiles_x) * TY;
     const int tw = min(kSwX, m - x0), th = min(TY, n - y0);
     if (tw == kSwX && th == TY)
       sweep_tile_compute<TY, true>(L, k, kb, E0, x0, y0, tw, th, S);
     else
       sweep_tile_compute<TY, false>(L, k, kb, E0, x0, y0, tw, th, S);
+    tma_cur = tma_next;
   }
 }
 
 // The instantiation for a tile height (4, 8, 16 or 32 rows).
-using SweepKernel = void (*)(Lev32, SweepSrc, Coef32, Coef32);
+using SweepKernel = void (*)(Lev32, SweepSrc, Coef32, Coef32, SweepMaps, int);
 SweepKernel sweep_kernel(int ty) {
   switch (ty) {
     case 4: return k_sweep32_tiles<4>;
@@ -670,7 +771,7 @@ int sweep_tiles_per_sm(int ty) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) dev = -1;
   if (dev >= 0)
     if (int c = cache[dev][idx].load()) return c;
-  const size_t smem = 2 * sizeof(float) * (size_t)sweep_stage_floats(ty);
+  const size_t smem = sweep_smem_bytes(ty);
   int per_sm = 0;
   if (cudaFuncSetAttribute(sweep_kernel(ty), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel(ty), kSwThreads, smem) != cudaSuccess ||
@@ -682,30 +783,55 @@ int sweep_tiles_per_sm(int ty) {
   return per_sm;
 }
 
+// The driver's tensor-map encoder (cuTensorMapEncodeTiled), looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 sweep_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2-D tensor map of one m x n FP32 plane with boxes of kSwW columns x rows rows (no
+// swizzle; the plane and its row pitch m * 4 bytes are 16-byte aligned, m % 4 == 0).
+bool sweep_plane_map(CUtensorMap* map, const float* plane, int m, int n, int rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = sweep_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(plane) & 15) || (m % 4)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)m * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)kSwW, (cuuint32_t)rows};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(plane), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Launches one tiled sweep reading e from (fp, fm, fk) and writing it to (tp, tm, tk).
 void launch_sweep_tiles(const mpfc_s* H, const Lev32& F, const float* fp, const float* fm, const float* fk, float* tp,
                         float* tm, float* tk, const Coef32& kf, const Coef32& kb, cudaStream_t s) {
   const int ty = H->sweep_tile_rows;
-  const size_t smem = 2 * sizeof(float) * (size_t)sweep_stage_floats(ty);
+  const size_t smem = sweep_smem_bytes(ty);
   const int per_sm = sweep_tiles_per_sm(ty);   // >= 1 (sweeps32 falls back when it is 0)
   const long long ntiles = (long long)((F.m + kSwX - 1) / kSwX) * ((F.n + ty - 1) / ty);
   const long long cap = (long long)per_sm * mpfc::sm_count();
   const int grid = (int)(ntiles < cap ? ntiles : cap);
   SweepSrc S = {fp, fm, fk, tp, tm, tk};
-  mpfc_launch(H->shape, sweep_kernel(ty), dim3(grid), dim3(kSwThreads), smem, s, F, S, kf, kb);
+  SweepMaps M;
+  memset(&M, 0, sizeof(M));
+  const float* eplanes[3] = {fp, fm, fk};
+  const float* qplanes[4] = {F.q, F.r1, F.r2, F.r3};
+  bool tma = true;
+  for (int p = 0; p < 3 && tma; ++p) tma = sweep_plane_map(&M.e[p], eplanes[p], F.m, F.n, ty + 4);
+  for (int p = 0; p < 4 && tma; ++p) tma = sweep_plane_map(&M.qr[p], qplanes[p], F.m, F.n, ty + 2);
+  mpfc_launch(H->shape, sweep_kernel(ty), dim3(grid), dim3(kSwThreads), smem, s, F, S, kf, kb, M, tma ? 1 : 0);
 }
 
-// `sweeps` red-black sweeps of one level, one launch per colour.  (A single-launch
-// sweep over shared-memory tiles with a 2-cell halo halves the DRAM reads at 2048^2 but
-// was slower on GB300 at every level size measured: its staging is latency bound.  So
-// was temporal blocking, a level's nu sweeps plus its restriction in one launch over
-// tiles with a (2 nu + 1)-cell halo, at every level from 64^2 to 2048^2.  A colour-split
-// layout of the FP32 planes (each colour's cells stored apart) cut a half sweep's DRAM
-// reads at 2048^2 from all seven planes, 117 MB, to its own colour's planes plus the
-// other colour's e, and the sweep from 57.9 to 49.8 us; but the transfer kernels and
-// the shared-memory tail slowed down under its addressing, and at the 1024^2 workload,
-// whose planes sit in L2, the form ran 977 against 1018 steps/s, so the layout stays
-// row-major.)
 void sweeps32(const mpfc_s* H, const Lev32& F, const Coef32& kf, const Coef32& kb, int sweeps, cudaStream_t s) {
   const mpfc_launch_shape& sh = H->shape;
   int done = 0;

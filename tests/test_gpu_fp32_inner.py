@@ -115,15 +115,18 @@ def test_fp32_inner_nonfinite_state_diverges_and_keeps_state(mp, bad):
     assert info["status"] == 0 and info["res"] <= 1e-10
 
 
-@pytest.mark.parametrize("case", ["periodic1", "periodic2", "ragged2", "neumann2", "pinned2", "odd_sweeps1"])
+@pytest.mark.parametrize("case", ["periodic1", "periodic2", "ragged2", "neumann2", "pinned2", "odd_sweeps1",
+                                  "large1", "largeneumann2"])
 def test_fp32_tiled_sweeps_are_bitwise_the_two_launch_sweeps(mp, case):
     """One-launch red-black sweeps over shared-memory tiles (out of place, in pairs)
     give exactly the bits of two in-place half-sweep launches, for every tile height,
-    over whole steps (same outer counts, same state)."""
+    over whole steps (same outer counts, same state).  The large cases have interior
+    tiles, which are staged by tensor copies (the others by cp.async)."""
     scheme = int(case[-1])
-    m, n = (96, 160) if case.startswith("ragged") else (128, 128) if case != "neumann2" else (128, 64)
+    m, n = {"ragged2": (96, 160), "neumann2": (128, 64), "large1": (384, 256),
+            "largeneumann2": (256, 192)}.get(case, (128, 128))
     kw = dict(m=m, n=n, h=0.5, dt=0.05, precision=mp.MPFC_FP32_INNER)
-    if case.startswith("neumann"):
+    if "neumann" in case:
         kw["bc"] = mp.MPFC_BC_NEUMANN_Y
     if case.startswith("pinned"):
         kw["pinning"] = 1
