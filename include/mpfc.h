@@ -187,6 +187,17 @@ int mpfc_fp32_time_smooth(mpfc_t* h, int level, int sweeps, float* ms);
  * not MPFC_FP32_INNER. */
 int mpfc_set_fp32_sweep(mpfc_t* h, int tile_rows, int min_cells);
 
+/* Test hook of the tiled FP32 sweep's failure handling (no counterpart in the paper; for
+ * tests of its bounded waits without a GPU fault).  withhold = 1: in every following
+ * tiled sweep, the tensor copies that stage tile (1, 1) (columns 64..127, the second
+ * row of tiles) are not issued (no memory is touched out of bounds) when that tile is
+ * staged by tensor copies, so the owning CTA's wait runs out after spin_cycles clock
+ * cycles; the CTA then writes NaN into all its remaining output tiles and returns, and
+ * the step's defect is not finite: the step reports MPFC_ERR_DIVERGED and keeps its
+ * state.  withhold = 0, spin_cycles = 0 restore normal operation (waits limited to about
+ * 1 s).  Process-wide, synchronous.  MPFC_ERR_INVALID for other values. */
+int mpfc_fp32_test_withhold_copy(int withhold, long long spin_cycles);
+
 /* Launch shapes of the time step's per-cell kernels (a tuning choice: results do not
  * depend on it).  Launches of at least small_cells cells use blocks of 32 x rows
  * threads (rows 1, 2, 4 or 8), smaller ones one-warp blocks; grids of at most

@@ -461,13 +461,17 @@ __device__ __forceinline__ bool sw_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for a stage's tensor copies (about 1 s at the GPU's clock); false if
-// they did not arrive.
+// Bounded wait for a stage's tensor copies (about 1 s at the GPU's clock by default);
+// false if they did not arrive.  The limit and the test hook's switch
+// (mpfc_fp32_test_withhold_copy: the tensor copies of tile (1, 1), the second tile of
+// the second tile row, are skipped) live in device variables.
 constexpr long long kSwSpinLimit = 2000000000ll;
+__device__ long long g_sw_spin_limit = kSwSpinLimit;
+__device__ int g_sw_withhold = 0;
 __device__ __forceinline__ bool sw_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
+  const long long t0 = clock64(), limit = g_sw_spin_limit;
   while (!sw_try_wait(bar, parity))
-    if (clock64() - t0 > kSwSpinLimit) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void sw_tma_2d(float* dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -497,14 +501,14 @@ struct SweepSrc {
 // (Neumann ghost rows, (A.7)).  Returns whether the tensor copies were used.
 template <int TY>
 __device__ __forceinline__ bool sweep_tile_load(const Lev32& L, const SweepSrc& S, const SweepMaps& M, bool use_tma,
-                                                int x0, int y0, float* st, uint32_t bar) {
+                                                int x0, int y0, float* st, uint32_t bar, bool withhold = false) {
   constexpr int q4 = kSwW / 4, RE = TY + 4, RQ = TY + 2;
   const int PE = sweep_plane_e(TY), PQ = sweep_plane_q(TY);
   const int m = L.m, n = L.n;
   const bool inner = x0 >= kSwPad && x0 + kSwX + kSwPad <= m && y0 >= 2 && y0 + TY + 2 <= n;
   float* qb = st + 3 * PE;
   if (inner && use_tma) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !withhold) {
       // the stage was last read through the generic proxy (after the block barrier that
       // precedes this call); order those reads before the tensor copies' writes
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -692,8 +696,10 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep32_tiles(Lev32 L, SweepSrc 
   uint32_t parity = 0u;   // bit s: phase parity of stage s's next tensor-copy wait
   int tile = blockIdx.x;
   bool tma_cur = false;
+  const int withheld = g_sw_withhold != 0 ? tiles_x + 1 : -1;   // test hook: tile (1, 1) gets no copies
   if (tile < ntiles)
-    tma_cur = sweep_tile_load<TY>(L, S, M, use_tma != 0, (tile % tiles_x) * kSwX, (tile / tiles_x) * TY, base, bar0);
+    tma_cur = sweep_tile_load<TY>(L, S, M, use_tma != 0, (tile % tiles_x) * kSwX, (tile / tiles_x) * TY, base, bar0,
+                                  tile == withheld);
   for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
     // this tile's copies have landed (every thread's, or the tensor copies on the
     // stage's mbarrier), and every warp is done with the previous tile, whose stage
@@ -721,14 +727,14 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep32_tiles(Lev32 L, SweepSrc 
           S.dka[g] = nan;
         }
       }
-      if (threadIdx.x == 0) sw_wait(bar0 + 8u * st, (parity >> st) & 1u);
+      if (threadIdx.x == 0) sw_wait(bar0 + 8u * st, (parity ^ (1u << st)) >> st & 1u);
       return;
     }
     const int next = tile + gridDim.x;
     bool tma_next = false;
     if (next < ntiles)
       tma_next = sweep_tile_load<TY>(L, S, M, use_tma != 0, (next % tiles_x) * kSwX, (next / tiles_x) * TY,
-                                     base + (st ^ 1) * SF, bar0 + 8u * (st ^ 1));
+                                     base + (st ^ 1) * SF, bar0 + 8u * (st ^ 1), next == withheld);
     float* E0 = base + st * SF;
     const int x0 = (tile % tiles_x) * kSwX, y0 = (tile / tiles_x) * TY;
     const int tw = min(kSwX, m - x0), th = min(TY, n - y0);
@@ -1101,6 +1107,19 @@ size_t mpfc_fp32_carve(mpfc_s* H, const mpfc_params* p, size_t* off, char* base,
     h *= 2.0;
   }
   return *off - start;
+}
+
+extern "C" int mpfc_fp32_test_withhold_copy(int withhold, long long spin_cycles) {
+  if (withhold < 0 || withhold > 1 || spin_cycles < 0) return MPFC_ERR_INVALID;
+  const int w = withhold;
+  const long long lim = spin_cycles > 0 ? spin_cycles : kSwSpinLimit;
+  cudaError_t e = cudaMemcpyToSymbol(g_sw_withhold, &w, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sw_spin_limit, &lim, sizeof(long long));
+  if (e != cudaSuccess) {
+    mpfc_set_cuda_error(e, "fp32 sweep test hook", __FILE__, __LINE__);
+    return MPFC_ERR_CUDA;
+  }
+  return MPFC_OK;
 }
 
 extern "C" int mpfc_set_fp32_sweep(mpfc_t* H, int tile_rows, int min_cells) {

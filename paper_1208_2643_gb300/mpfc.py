@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_launch_counts.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
     lib.mpfc_set_fp32_sweep.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
+    lib.mpfc_fp32_test_withhold_copy.argtypes = [ctypes.c_int, ctypes.c_longlong]
     lib.mpfc_op_learned_guess.argtypes = [_VP]
     lib.mpfc_guess_correction.argtypes = [_VP, _VP]
     lib.mpfc_batch_workspace_bytes.argtypes = [ctypes.c_int, P(mpfc_params)]

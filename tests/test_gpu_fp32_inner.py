@@ -153,6 +153,39 @@ def test_fp32_tiled_sweeps_are_bitwise_the_two_launch_sweeps(mp, case):
             assert np.array_equal(a, b)
 
 
+def test_fp32_tiled_sweep_wait_timeout_diverges_and_recovers(mp):
+    """The tiled sweep's waits for its tensor copies are bounded.  Through the test hook
+    the copies of tile (1, 1) are not issued (no out-of-bounds access): the owning CTA's
+    wait runs out after 2e6 clock cycles, the CTA writes NaN into its output tiles and
+    returns, and the step reports DIVERGED with its state unchanged.  With the hook off,
+    the same step converges to the bits of the two-launch sweeps."""
+    m, n = 384, 256
+    kw = dict(m=m, n=n, h=0.5, dt=0.05, precision=mp.MPFC_FP32_INNER)
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 11)
+    lib = mp.load()
+    runs = []
+    for rows in (0, 16):
+        g = mp.Solver(mp.default_params(**kw))
+        g.set_fp32_sweep(rows, 0)
+        g.set_state(phi0)
+        if rows:
+            try:
+                assert lib.mpfc_fp32_test_withhold_copy(1, 2000000) == 0
+                rc, infos = g.step(1, 1, raise_on_error=False)
+            finally:
+                assert lib.mpfc_fp32_test_withhold_copy(0, 0) == 0
+            assert rc == mp.MPFC_ERR_DIVERGED and infos[0]["status"] == mp.MPFC_ERR_DIVERGED
+            assert np.array_equal(g.get_state()[0], phi0)
+        info = g.step(1, 1)[0]
+        assert info["status"] == 0 and info["res"] <= 1e-10
+        runs.append((info["cycles"], g.get_state()))
+        g.close()
+    assert runs[1][0] == runs[0][0]
+    for a, b in zip(runs[1][1], runs[0][1]):
+        assert np.array_equal(a, b)
+    assert lib.mpfc_fp32_test_withhold_copy(2, 0) == mp.MPFC_ERR_INVALID
+
+
 def test_fp32_sweep_setting_checked(mp):
     g = mp.Solver(mp.default_params(m=64, n=64, precision=mp.MPFC_FP32_INNER))
     for bad in (3, 12, 64, -1):
