@@ -395,11 +395,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv3x3_tc(const __grid_constan
     const float* bias_h = bias_s + (16 * h & 31);   // this half's 16 biases (shared-memory broadcast)
     const bool f32_out = A.mode == kModeLinear || A.mode == kModeGeluGrad || A.z_f32 != nullptr;
     unsigned char* ob = smem + kOffOut + grp * kOutBytes;  // this group's stage buffer
+    int b = 0, y = 0, x0 = 0;   // tile t of the order, advanced by two tiles per iteration (no divisions)
+    if (t_begin + grp < t_end) order.decode(t_begin + grp, b, y, x0);
     for (int i = grp, t = t_begin + grp; t < t_end; t += 2, i += 2) {
       const int blk = i % kBlocks;
-      int b, y, x0;
-      order.decode(t, b, y, x0);
       const size_t pix0 = ((size_t)b * A.H + y) * A.W + x0;
+      for (y += 2; y >= A.H;) {   // strip-major: down the strip, then the next strip, then the next image
+        y -= A.H;
+        x0 += kTM;
+        if (x0 >= A.W) {
+          x0 = 0;
+          ++b;
+        }
+      }
       float4 zin[4];
       if (A.mode == kModeGeluGrad) {
         const float4* zg = reinterpret_cast<const float4*>(A.z_f32 + (pix0 + p) * 32 + h * 16);
