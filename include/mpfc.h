@@ -64,7 +64,8 @@ extern "C" {
 typedef struct {
   int m, n;          /* cells in x and y; the hierarchy halves both while they stay even
                         and at least `coarsest` cells per side remain; m n <= 2^30 (the
-                        kernels index cells in 32-bit ints)                              */
+                        kernels index cells in 32-bit ints) and n <= 65535 (rows are a
+                        launch grid's y dimension)                                       */
   double h;          /* grid spacing (App. A), L_x = m h, L_y = n h                      */
   double M;          /* mobility (Sec. 2)                                                 */
   double epsilon;    /* alpha = 1 - epsilon (Sec. 2, (2.1))                               */

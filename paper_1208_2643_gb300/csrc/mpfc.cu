@@ -129,6 +129,8 @@ static bool params_valid(const mpfc_params* p) {
   // the kernels index cells and stride their grid loops in 32-bit ints: at most 2^30
   // cells keeps every index, every cell count and every index-plus-stride below 2^31
   if ((size_t)p->m * (size_t)p->n > ((size_t)1 << 30)) return false;
+  // the per-cell launches put the rows on the grid's y dimension (at most 65535 blocks)
+  if (p->n > 65535) return false;
   return true;
 }
 

@@ -37,6 +37,57 @@ def uniform(seed: int, count: int, lo: float = -1.0, hi: float = 1.0, offset: in
     return lo + (hi - lo) * u
 
 
+def uniform_at(seed: int, index, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """uniform() evaluated at the given output indices k (any integer array shape): the
+    values uniform(seed, count, lo, hi) holds at positions k, bit for bit."""
+    k = np.asarray(index, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) * _GOLDEN + (k + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    u = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return lo + (hi - lo) * u
+
+
+def noise_at(m: int, mean: float, amp: float, seed: int, rows, cols) -> np.ndarray:
+    """The values noise_field(m, n, mean, amp, seed) holds at (rows[j], cols[i]) (any
+    n), as a len(rows) x len(cols) array: for patches of fields too large to build on
+    the host."""
+    idx = np.asarray(rows, dtype=np.int64)[:, None] * m + np.asarray(cols, dtype=np.int64)[None, :]
+    return mean + amp * uniform_at(seed, idx)
+
+
+def _s64(v: int) -> int:
+    return v - (1 << 64) if v >= (1 << 63) else v
+
+
+def noise_field_torch(m: int, n: int, mean: float, amp: float, seed: int, device="cuda", chunk: int = 1 << 25):
+    """noise_field() built by torch on `device` (float64, shape (n, m)), bit for bit the
+    same values: SplitMix64 in int64 arithmetic (wrapping products, logical shifts as
+    arithmetic shifts with the sign bits masked off), the same float64 operations in the
+    same order.  For fields too large to build on the host and copy."""
+    import torch
+    out = torch.empty(n * m, dtype=torch.float64, device=device)
+    gold, m1, m2 = _s64(0x9E3779B97F4A7C15), _s64(0xBF58476D1CE4E5B9), _s64(0x94D049BB133111EB)
+    base = _s64((seed * 0x9E3779B97F4A7C15) % (1 << 64))
+
+    def lsr(z, sh):
+        return (z >> sh) & ((1 << (64 - sh)) - 1)
+
+    for a in range(0, n * m, chunk):
+        b = min(a + chunk, n * m)
+        k = torch.arange(a + 1, b + 1, dtype=torch.int64, device=device)
+        z = k * gold + base
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        z = z ^ lsr(z, 31)
+        u = lsr(z, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+        out[a:b] = (u * 2.0 + (-1.0)) * amp + mean
+        del k, z, u
+    return out.view(n, m)
+
+
 def cell_centres(m: int, n: int, h: float):
     x = (np.arange(m) + 0.5) * h
     y = (np.arange(n) + 0.5) * h

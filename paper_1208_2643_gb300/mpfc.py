@@ -197,9 +197,13 @@ class Solver:
         self.levels = self.lib.mpfc_levels(self.h)
 
     def close(self):
+        """Destroys the handle and releases its workspace once the work queued on the
+        handle's stream has finished."""
         if getattr(self, "h", None):
+            self.stream.synchronize()
             self.lib.mpfc_destroy(self.h)
             self.h = None
+        self.workspace = None
 
     def __del__(self):
         try:
@@ -412,9 +416,12 @@ class BatchSolver:
         self.levels = self.lib.mpfc_batch_levels(self.h)
 
     def close(self):
+        """Destroys the handle and releases its workspace (as Solver.close)."""
         if getattr(self, "h", None):
+            self.stream.synchronize()
             self.lib.mpfc_batch_destroy(self.h)
             self.h = None
+        self.workspace = None
 
     def __del__(self):
         try:

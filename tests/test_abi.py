@@ -56,6 +56,7 @@ def test_default_params_and_workspace(lib):
                                 dict(m=2, n=2),                 # below the 4-cell minimum per side
                                 dict(m=65536, n=65536),         # more than 2^30 cells
                                 dict(m=65536, n=32768),         # 2^31 cells: past the 32-bit index range
+                                dict(m=16384, n=65536),         # 2^30 cells but more rows than a grid's y extent
                                 dict(m=254, n=254),             # coarsening stops at 127^2 > 64 cells
                                 dict(epsilon=1.5), dict(inner_cycles=65), dict(bc=5), dict(model=3),
                                 dict(pinning=2),

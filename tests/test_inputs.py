@@ -52,3 +52,18 @@ def test_cell_centres_and_field_shapes():
     assert X[0, 0] == 0.25 and X[0, 5] == 2.75 and Y[3, 0] == 1.75
     f = inputs.noise_field(6, 4, 0.07, 0.05, 1)
     assert f.shape == (4, 6) and np.all(np.abs(f - 0.07) <= 0.05)
+
+
+def test_patch_and_device_generators_give_the_field_bits():
+    """noise_at (values at given rows and columns, with wrap-around indices) and
+    noise_field_torch (built by torch, here on the CPU, in small chunks) hold exactly
+    the values of noise_field."""
+    torch = __import__("pytest").importorskip("torch")
+    f = inputs.noise_field(96, 40, 0.07, 0.05, 8)
+    t = inputs.noise_field_torch(96, 40, 0.07, 0.05, 8, device="cpu", chunk=1000)
+    assert t.dtype == torch.float64 and tuple(t.shape) == (40, 96)
+    np.testing.assert_array_equal(t.numpy(), f)
+    rows, cols = [39, 0, 1, 17], [95, 0, 1, 50, 94]
+    np.testing.assert_array_equal(inputs.noise_at(96, 0.07, 0.05, 8, rows, cols), f[np.ix_(rows, cols)])
+    big = (1 << 15) * (1 << 15) - 5   # indices past 2^30 address the same stream
+    np.testing.assert_array_equal(inputs.uniform_at(3, [big, big + 4]), inputs.uniform(3, 5, offset=big)[[0, 4]])
