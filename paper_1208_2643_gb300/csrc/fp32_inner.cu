@@ -888,14 +888,24 @@ __device__ __forceinline__ void prolong32_fine(const float* ec, float* ef, int m
 size_t tail32_smem(const Lev32* levs, int nlev) {
   size_t cells = 0;
   for (int l = 0; l < nlev; ++l) cells += (size_t)levs[l].m * levs[l].n;
-  return 7 * cells * sizeof(float) + coarse32_smem(levs[nlev - 1]);
+  const size_t gc = (size_t)levs[nlev - 1].m * levs[nlev - 1].n;
+  return 7 * cells * sizeof(float) + coarse32_smem(levs[nlev - 1]) + 2 * gc * gc * sizeof(float);
 }
 
 __global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant__ Tail32Args A) {
   extern __shared__ float ts[];
   __shared__ Lev32 sl[kMaxTail32];
-  pdl_enter();
   const int tid = threadIdx.x, nt = blockDim.x;
+  // shared layout: the levels' planes, the coarse solve's scratch, then a copy of the
+  // coarsest grid's K3 and c L blocks, loaded before the wait for the previous kernel
+  // (they are written once, when the handle is created), out of the coarse solve's path
+  float* scratch = ts;
+  for (int l = 0; l < A.nlev; ++l) scratch += 7 * A.g[l].m * A.g[l].n;
+  const Lev32& Cg = A.g[A.nlev - 1];
+  const int gcc = Cg.m * Cg.n;
+  float* k3s = scratch + gcc * (gcc + 1) + 4 * gcc;
+  for (int t = tid; t < 2 * gcc * gcc; t += nt) k3s[t] = A.K3f[t];
+  pdl_enter();
   if (tid == 0) {
     float* p = ts;
     for (int l = 0; l < A.nlev; ++l) {
@@ -913,8 +923,6 @@ __global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant
     }
   }
   __syncthreads();
-  float* scratch = ts;
-  for (int l = 0; l < A.nlev; ++l) scratch += 7 * A.g[l].m * A.g[l].n;
   {
     const Lev32& T = sl[0];
     const Lev32& G0 = A.g[0];
@@ -949,7 +957,7 @@ __global__ void __launch_bounds__(kTail32Threads) k_tail32(const __grid_constant
     for (int t = tid; t < cc; t += nt) restrict_defect32_cell<false>(F, C, A.k[l], t % C.m, t / C.m);
     __syncthreads();
   }
-  coarse32_block(sl[A.nlev - 1], A.k[A.nlev - 1], A.K3f, scratch);
+  coarse32_block(sl[A.nlev - 1], A.k[A.nlev - 1], k3s, scratch);
   __syncthreads();
   for (int l = A.nlev - 2; l >= 0; --l) {
     const Lev32& F = sl[l];
