@@ -9,9 +9,9 @@ dependence) from the seeded generator's values at those cells, and the oracle's
 source (App. B.1/B.2), residual and red-black sweep on the patch give the cell's
 value (tests/test_oracle_patches.py shows on the CPU that this reproduces the
 whole-grid oracle bit for bit).  Inputs are built on the device by the same
-counter-based generator, bit for bit.  Whole time steps (FP64, and FP32 inner cycles with FP64 defect correction) are
-checked by properties: convergence to the tolerance, conservation of mass, and the two
-forms' agreement at the sampled cells.
+counter-based generator, bit for bit.  Whole time steps (FP64, and FP32 inner cycles
+with FP64 defect correction) are checked by properties: convergence to the tolerance,
+conservation of mass, and the two forms' agreement at the sampled cells.
 """
 import numpy as np
 import pytest
