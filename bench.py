@@ -69,6 +69,9 @@ def parse_args():
                          "launches at --size^2 (ncu capture of the network's top kernel)")
     ap.add_argument("--profile-smooth", action="store_true",
                     help="only the finest-level sweep kernel, two sweeps (ncu capture of the top kernel)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="only the batched form's sweep kernel: 16 instances of the --size^2 workload, default tiles, "
+                         "two red-black sweeps of their finest levels (ncu capture of kb_smooth)")
     ap.add_argument("--profile-sweep32", action="store_true",
                     help="only the mixed-precision form's tiled FP32 sweep at 2048^2, two there-and-back pairs "
                          "(ncu capture of the HBM-bound kernel)")
@@ -314,6 +317,15 @@ def run_ours(args):
         big.close()
         if rank == 0:
             print(json.dumps({"profile_sweep32": True, "us_per_sweep": us}), flush=True)
+        return
+    if args.profile_batch:
+        bq = mpfc.BatchSolver([mpfc.default_params(m=size, n=size, h=w["h"], dt=w["dt"]) for _ in range(16)])
+        for i in range(16):
+            bq.set_state(i, inputs.noise_field(size, size, 0.07, 0.05, 1 + i))
+        ms = bq.time_smooth(scheme, 0, reps=1)
+        bq.close()
+        if rank == 0:
+            print(json.dumps({"profile_batch": True, "ms": ms}), flush=True)
         return
     if args.profile_conv:
         r = conv32_timing(size, launches=4, flush_between=False)
@@ -579,12 +591,21 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
+        # the batch's dominant kernel: one red-black sweep of every instance's finest level
+        # (kb_smooth, the tuned tiles), against the same FP64 rate as the headline's sweep
+        ms_kb = b64.time_smooth(scheme, 0, reps=10)
+        kb_tf = SMOOTH_FLOPS_PER_CELL * 64 * size * size / (ms_kb * 1e-3) / 1e12
         forms["batched_64x1024"] = {"workload": "64 x the headline workload (1024^2) in one batch, fp64, tol 1e-10",
                                     "instance_steps_per_s": world * 64 * 2 / (ms64 * 1e-3),
                                     "cell_updates_per_s": world * 64 * size * size * 2 / (ms64 * 1e-3),
                                     "vs_single_instance_cell_updates": (64 * size * size * 2 / (ms64 * 1e-3)) /
                                                                        (steps_per_s / world * size * size),
-                                    "vcycles_per_instance_step": float(np.mean(cy64)) / 2, "steps": 2}
+                                    "vcycles_per_instance_step": float(np.mean(cy64)) / 2, "steps": 2,
+                                    "smooth_roofline": {"kernel": "kb_smooth<1>, one red+black sweep of the 64 finest "
+                                                                  "levels (two launches)",
+                                                        "ms": ms_kb, "bound": "alu", "achieved": kb_tf,
+                                                        "peak": fp64_peak, "unit": "TFLOP/s (FP64, FMA = 2)",
+                                                        "frac": kb_tf / fp64_peak}}
         b64.close()
 
     # learned initial guess (model trained by paper_1208_2643_gb300.guess on solver data at 256^2)
