@@ -650,11 +650,14 @@ def run_ours(args):
                                                  "vcycle_histogram": hist(recx),
                                                  "res0_mean": float(np.mean([r["res0"] for r in recx]))},
                                 "network_ms_per_step": ev0.elapsed_time(ev1) / 10,
+                                "guess_gate": 2.6e4 * w["tol"],
+                                "gated_steps_in_extrapolated_run": int(sum(r["res0"] >= 2.6e4 * w["tol"] for r in recx)),
                                 "speedup_vs_fp64": msx / msl,
                                 "conv32": conv32_timing(size),
                                 "model": "5 x conv3x3 (3-32-32-32-32-1), GELU, bf16/fp32-acc; the 32-input-channel "
                                          "layers on tcgen05 (TMEM accumulators, TMA), the first on mma.sync; "
-                                         "trained on solver trajectories at 256^2"}
+                                         "trained on solver trajectories at 256^2; run on the steps whose "
+                                         "extrapolated guess has a scaled residual of at least guess_gate"}
             sl.close()
 
     # the PFC variant (Sec. 1, (1)) on the headline workload

@@ -222,6 +222,17 @@ int mpfc_step_cycles(mpfc_t* h, int scheme, int ncycles, mpfc_step_info* info);
  * Synchronises. */
 int mpfc_set_guess_model(mpfc_t* h, const float* params, size_t count);
 
+/* When the learned guess runs (FP64 handles with guess = MPFC_GUESS_LEARNED; no
+ * counterpart in the paper): each step forms the extrapolated guess and its scaled
+ * residual first, and the network corrects the guess only if that residual is at least
+ * res0_threshold (kappa, mu and the residual are then formed again from the corrected
+ * phi); elsewhere the step is the extrapolated guess's, bit for bit.  0 runs the network
+ * on every step.  Default: 2.6e4 tol, the residual above which the extrapolated guess
+ * needs more V-cycles than the network's corrected one on the 1024^2 headline workload.
+ * Drops the handle's captured graphs.  MPFC_ERR_INVALID for other handles or a
+ * negative or NaN threshold. */
+int mpfc_set_guess_gate(mpfc_t* h, double res0_threshold);
+
 /* The learned guess's correction on the current state, for tests of the inference
  * against the network's definition (no counterpart in the paper): d_out (m*n device
  * doubles, overwritten) receives what the guess adds to the extrapolation 2 phi^k -

@@ -185,6 +185,12 @@ struct Carver {
   }
 };
 
+// Default gate of the learned guess, as a multiple of the tolerance: on the headline
+// workload (1024^2, tol 1e-10) the extrapolated guess needs four or more V-cycles exactly
+// when its scaled residual is at least 2.6e-6, and the network's own error floor (a
+// scaled residual near 7e-7) still leaves three, so only those steps gain a cycle.
+constexpr double kGuessGateTolMultiple = 2.6e4;
+
 // Walks the layout; with base == nullptr only computes the size.
 static size_t carve(mpfc_s* H, const mpfc_params* p, char* base) {
   Carver c{base, 0};
@@ -349,6 +355,7 @@ extern "C" int mpfc_create(const mpfc_params* p, void* d_workspace, size_t bytes
   mpfc_s* H = new mpfc_s();
   H->p = *p;
   H->shape = mpfc_default_launch_shape(p->precision);
+  H->guess_gate = kGuessGateTolMultiple * p->tol;
   H->stream = (cudaStream_t)cuda_stream;
   H->ws = (char*)d_workspace;
   H->ws_bytes = bytes;
@@ -583,8 +590,23 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
   }
 }
 
+// The learned guess's gate: sets the condition of the step graph's IF node that holds
+// the network's correction from the scaled residual of the extrapolated guess.
+__global__ void k_guess_gate(const Ctl* ctl, double threshold, cudaGraphConditionalHandle h) {
+  pdl_enter();
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, (ctl->status == 0 && ctl->res0 >= threshold) ? 1u : 0u);
+}
+
+
+// Whether the step runs the learned guess behind its gate (FP64 handles).
+static bool guess_gated(const mpfc_s* H) {
+  return H->p.guess == MPFC_GUESS_LEARNED && H->p.precision == MPFC_FP64 && H->guess_gate > 0.0;
+}
+
+// The prologue: source and extrapolated guess; with `network`, the learned correction
+// of the guess (always, where no gate decides); then kappa and mu consistent with phi.
 template <int SCH>
-static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
+static void enqueue_prologue(mpfc_s* H, cudaStream_t s, bool network = true) {
   const mpfc_params& p = H->p;
   const Lev& L0 = H->lev[0];
   mpfc_launch(H->shape, k_step_begin, dim3(1), dim3(32), 0, s, H->ctl);
@@ -599,7 +621,7 @@ static void enqueue_prologue(mpfc_s* H, cudaStream_t s) {
   A.guess = (p.guess == MPFC_GUESS_PREV) ? 0 : 1;   // the learned guess corrects the extrapolation
   dim3 g0 = grid_for(L0.m, L0.n, kBlk2d);
   mpfc_launch(H->shape, k_source_guess<SCH>, g0, kBlk2d, 0, s, L0, A);
-  if (p.guess == MPFC_GUESS_LEARNED) mpfc_enqueue_learned_guess(H, s);
+  if (p.guess == MPFC_GUESS_LEARNED && network) mpfc_enqueue_learned_guess(H, s);
   if (SCH == 2)
     for (int l = 1; l < H->nlev; ++l) {
       const Lev& C = H->lev[l];
@@ -639,6 +661,24 @@ static void enqueue_resnorm(mpfc_s* H, int mode, cudaGraphConditionalHandle hnd,
 
 // Body of the FP64 WHILE node: one V-cycle, then the residual test that sets the
 // loop condition.
+// The gated learned correction: the network adds its correction to the extrapolated
+// guess, kappa and mu are formed again from the corrected phi, and the residual test of
+// the guess runs again (it sets the V-cycle loop's condition).
+template <int SCH>
+static void enqueue_learned_correction(mpfc_s* H, cudaGraphConditionalHandle hnd, int set_cond, cudaStream_t s) {
+  const Lev& L0 = H->lev[0];
+  dim3 g0 = grid_for(L0.m, L0.n, kBlk2d);
+  mpfc_enqueue_learned_guess(H, s);
+  mpfc_launch(H->shape, k_guess_kappa, g0, kBlk2d, 0, s, L0, H->coef[SCH - 1][0]);
+  mpfc_launch(H->shape, k_guess_mu<SCH>, g0, kBlk2d, 0, s, L0, H->coef[SCH - 1][0]);
+  enqueue_resnorm<SCH>(H, 0, hnd, set_cond, s);
+}
+
+static void learned_body(mpfc_s* H, int scheme, cudaStream_t s) {
+  if (scheme == 1) enqueue_learned_correction<1>(H, H->cur_handle, 1, s);
+  else enqueue_learned_correction<2>(H, H->cur_handle, 1, s);
+}
+
 static void fp64_body(mpfc_s* H, int scheme, cudaStream_t s) {
   cudaGraphConditionalHandle hnd = H->cur_handle;
   if (scheme == 1) {
@@ -668,9 +708,17 @@ static int build_step_graph(mpfc_s* H) {
   if (H->p.precision == MPFC_FP32_INNER) {
     rc = mpfc_fp32_enqueue_step(H, SCH, cs, hnd);
   } else {
-    enqueue_prologue<SCH>(H, cs);
+    const bool gated = guess_gated(H);
+    enqueue_prologue<SCH>(H, cs, !gated);
     enqueue_resnorm<SCH>(H, 0, hnd, 1, cs);
-    rc = mpfc_capture_while(H, cs, hnd, &fp64_body, SCH);
+    rc = MPFC_OK;
+    if (gated) {   // IF(res0 >= gate){ network; kappa, mu; resnorm(mode 0, sets cond) }
+      cudaGraphConditionalHandle hif;
+      CKCAP(cudaGraphConditionalHandleCreate(&hif, graph, 0, 0), cs);
+      mpfc_launch(H->shape, k_guess_gate, dim3(1), dim3(32), 0, cs, (const Ctl*)H->ctl, H->guess_gate, hif);
+      rc = mpfc_capture_conditional(H, cs, hif, cudaGraphCondTypeIf, &learned_body, SCH);
+    }
+    if (rc == MPFC_OK) rc = mpfc_capture_while(H, cs, hnd, &fp64_body, SCH);
     if (rc == MPFC_OK) enqueue_commit<SCH>(H, cs);
   }
   if (rc != MPFC_OK) {
@@ -706,6 +754,11 @@ void mpfc_abort_capture(cudaStream_t s) {
 
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd, void (*body_fn)(mpfc_s*, int, cudaStream_t),
                        int scheme) {
+  return mpfc_capture_conditional(H, cs, hnd, cudaGraphCondTypeWhile, body_fn, scheme);
+}
+
+int mpfc_capture_conditional(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd, cudaGraphConditionalNodeType type,
+                             void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme) {
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
@@ -714,7 +767,7 @@ int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hn
   std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
   cp.conditional.handle = hnd;
-  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.type = type;
   cp.conditional.size = 1;
   cudaGraphNode_t cnode;
   CK(cudaGraphAddNode(&cnode, graph, dv.data(), nullptr, dv.size(), &cp));
@@ -749,12 +802,22 @@ static int step_stream_mode(mpfc_s* H, int scheme) {
   MpfcRange range("mpfc step");
   cudaStream_t s = H->stream;
   if (H->p.precision == MPFC_FP32_INNER) return mpfc_fp32_step_stream(H, scheme);
+  const bool gated = guess_gated(H);
   if (scheme == 1) {
-    enqueue_prologue<1>(H, s);
+    enqueue_prologue<1>(H, s, !gated);
     enqueue_resnorm<1>(H, 0, 0, 0, s);
   } else {
-    enqueue_prologue<2>(H, s);
+    enqueue_prologue<2>(H, s, !gated);
     enqueue_resnorm<2>(H, 0, 0, 0, s);
+  }
+  if (gated) {   // the gate read on the host
+    Ctl c;
+    CK(cudaMemcpyAsync(&c, H->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c.status == 0 && c.res0 >= H->guess_gate) {
+      if (scheme == 1) enqueue_learned_correction<1>(H, 0, 0, s);
+      else enqueue_learned_correction<2>(H, 0, 0, s);
+    }
   }
   for (;;) {
     Ctl c;
@@ -800,6 +863,14 @@ extern "C" int mpfc_set_launch_shape(mpfc_t* H, int rows, int small_cells, int p
     return MPFC_ERR_INVALID;
   if (tail_ctas > mpfc_tail_max_ctas()) return MPFC_ERR_INVALID;
   H->shape = mpfc_launch_shape{rows, small_cells, pdl_blocks, tail_cells, tail_ctas};
+  mpfc_drop_graphs(H);
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_set_guess_gate(mpfc_t* H, double res0_threshold) {
+  if (!H || H->p.guess != MPFC_GUESS_LEARNED || H->p.precision != MPFC_FP64 || !(res0_threshold >= 0.0))
+    return MPFC_ERR_INVALID;
+  H->guess_gate = res0_threshold;
   mpfc_drop_graphs(H);
   return MPFC_OK;
 }

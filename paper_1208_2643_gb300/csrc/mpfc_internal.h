@@ -74,6 +74,9 @@ struct mpfc_s {
   double* partials = nullptr;
   double* bpart = nullptr;   // per-warp residual sums of the finest level's last half sweep
   int nbpart = 0;
+  // learned guess (FP64 handles): the network corrects the extrapolated guess only when
+  // that guess's scaled residual is at least guess_gate (0: on every step)
+  double guess_gate = 0.0;
   mpfc::StepRecord* info = nullptr;
   float* K3[2] = {nullptr, nullptr};    // coarsest grid, per scheme: I - c theta L^3 then c L (FP32)
   double* px[mpfc::kMaxLevels];
@@ -159,6 +162,9 @@ mpfc_launch_shape mpfc_default_launch_shape(int precision);
 void mpfc_abort_capture(cudaStream_t s);
 int mpfc_capture_while(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd,
                        void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme);
+// The same for a conditional node of any type (IF for the learned guess's gate).
+int mpfc_capture_conditional(mpfc_s* H, cudaStream_t cs, cudaGraphConditionalHandle hnd, cudaGraphConditionalNodeType type,
+                             void (*body_fn)(mpfc_s*, int, cudaStream_t), int scheme);
 void mpfc_enqueue_prologue(mpfc_s* H, int scheme, cudaStream_t s);
 void mpfc_enqueue_commit(mpfc_s* H, int scheme, cudaStream_t s);
 

@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_fp32_time_smooth.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     lib.mpfc_launch_counts.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
+    lib.mpfc_set_guess_gate.argtypes = [_VP, ctypes.c_double]
     lib.mpfc_set_fp32_sweep.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
     lib.mpfc_fp32_test_withhold_copy.argtypes = [ctypes.c_int, ctypes.c_longlong]
     lib.mpfc_op_learned_guess.argtypes = [_VP]
@@ -290,6 +291,11 @@ class Solver:
         """Mixed-precision handles: inner sweeps as one launch over 64 x tile_rows tiles
         on levels of at least min_cells cells (tile_rows 0: two launches per sweep)."""
         _check(self.lib.mpfc_set_fp32_sweep(self.h, tile_rows, min_cells), "mpfc_set_fp32_sweep")
+
+    def set_guess_gate(self, res0_threshold: float):
+        """Learned guess: run the network only when the extrapolated guess's scaled
+        residual is at least res0_threshold (0: on every step)."""
+        _check(self.lib.mpfc_set_guess_gate(self.h, res0_threshold), "mpfc_set_guess_gate")
 
     def step_async(self, scheme: int, nsteps: int = 1):
         """Enqueues steps without synchronising (records via records())."""

@@ -175,6 +175,7 @@ def test_learned_guess_trains_and_lowers_res0(G):
         g = mpfc.Solver(mpfc.default_params(m=m, n=m, guess=gs))
         if gs == mpfc.MPFC_GUESS_LEARNED:
             G.attach(g, blob)
+            g.set_guess_gate(0.0)   # the network on every step: this tests the network
         g.set_state(phi0)
         g.step(1, 20)
         infos = g.step(1, 40)
@@ -206,6 +207,63 @@ def test_learned_guess_saves_vcycles_early_in_the_headline_run(G):
         cyc[gs] = np.mean([i["cycles"] for i in infos])
         g.close()
     assert cyc[mpfc.MPFC_GUESS_LEARNED] <= cyc[mpfc.MPFC_GUESS_EXTRAP] - 0.2, cyc
+
+
+def test_learned_guess_gate(G):
+    """The gate of the learned guess on the benchmark's workload (1024^2): steps whose
+    extrapolated guess has a scaled residual below the threshold are the extrapolated
+    guess's steps bit for bit; a threshold below every residual gives the ungated
+    network's steps bit for bit; in graph and stream launch modes alike.  Over steps
+    11-110 the gated guess takes no more V-cycles than the extrapolated one."""
+    from paper_1208_2643_gb300 import inputs, mpfc
+    blob = G.load()
+    m = 1024
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
+
+    def run(gs, gate=None, stream=False, steps=12):
+        g = mpfc.Solver(mpfc.default_params(m=m, n=m, guess=gs))
+        if gs == mpfc.MPFC_GUESS_LEARNED:
+            G.attach(g, blob)
+            if gate is not None:
+                g.set_guess_gate(gate)
+        if stream:
+            g.set_launch_mode(mpfc.MPFC_LAUNCH_STREAM)
+        g.set_state(phi0)
+        infos = g.step(1, steps)
+        st = g.get_state()
+        g.close()
+        return infos, st
+
+    ext, st_ext = run(mpfc.MPFC_GUESS_EXTRAP)
+    never, st_never = run(mpfc.MPFC_GUESS_LEARNED, gate=1e30)
+    assert [i["cycles"] for i in never] == [i["cycles"] for i in ext]
+    for a, b in zip(st_never, st_ext):
+        assert np.array_equal(a, b)
+    always, st_always = run(mpfc.MPFC_GUESS_LEARNED, gate=0.0)
+    tiny, st_tiny = run(mpfc.MPFC_GUESS_LEARNED, gate=1e-300)
+    assert [i["res0"] for i in tiny] == [i["res0"] for i in always]
+    for a, b in zip(st_tiny, st_always):
+        assert np.array_equal(a, b)
+    dflt, st_d = run(mpfc.MPFC_GUESS_LEARNED)
+    dflt_s, st_ds = run(mpfc.MPFC_GUESS_LEARNED, stream=True)
+    assert [i["cycles"] for i in dflt] == [i["cycles"] for i in dflt_s]
+    for a, b in zip(st_d, st_ds):
+        assert np.array_equal(a, b)
+    # until the network first runs, the default gate's steps are the extrapolated guess's
+    gate = 2.6e4 * 1e-10
+    for i, e in zip(dflt, ext):
+        if e["res0"] >= gate:
+            break
+        assert i["res0"] == e["res0"] and i["cycles"] == e["cycles"]
+    cyc = {}
+    for name in ("extrap", "gated"):
+        gs = mpfc.MPFC_GUESS_EXTRAP if name == "extrap" else mpfc.MPFC_GUESS_LEARNED
+        infos, _ = run(gs, steps=110)
+        cyc[name] = np.mean([i["cycles"] for i in infos[10:]])
+    assert cyc["gated"] <= cyc["extrap"], cyc
+    with pytest.raises(mpfc.MPFCError):
+        g = mpfc.Solver(mpfc.default_params(m=64, n=64))
+        g.set_guess_gate(1.0)
 
 
 @pytest.fixture
@@ -365,6 +423,7 @@ def test_learned_guess_same_on_both_tensor_paths(G, tensor_path):
         tensor_path(use_tc)
         g = mpfc.Solver(mpfc.default_params(m=m, n=m, guess=mpfc.MPFC_GUESS_LEARNED))
         G.attach(g, G.load())
+        g.set_guess_gate(0.0)
         g.set_state(phi0)
         g.step(1, 3)
         infos = g.step(1, 3)
