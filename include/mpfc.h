@@ -44,7 +44,8 @@ extern "C" {
 
 #define MPFC_GUESS_PREV 0    /* phi^(0) = phi^k                                            */
 #define MPFC_GUESS_EXTRAP 1  /* phi^(0) = 2 phi^k - phi^{k-1}                              */
-#define MPFC_GUESS_LEARNED 2 /* extrapolation plus the learned correction (mpfc_set_guess_model) */
+#define MPFC_GUESS_LEARNED 2 /* extrapolation plus the learned correction (mpfc_set_guess_model),
+                                 behind a residual gate on FP64 handles (mpfc_set_guess_gate)   */
 
 /* Boundary conditions (App. A): periodic in both directions, (A.8)-(A.9); or, as in the
  * polycrystal run of Sec. 4.5, periodic in x and homogeneous Neumann in y with the ghost
