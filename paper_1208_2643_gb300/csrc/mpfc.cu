@@ -307,9 +307,13 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
 }
 
 // Default launch shapes, from interleaved timings on GB300 (V-cycle at 1024^2):
-//   FP64: one-warp blocks everywhere and programmatic launch for grids of at most 4 x SMs
-//     blocks, 743 us per V-cycle, against 822 with 32 x 8 blocks and no programmatic
-//     launch; programmatic launch of the large grids too was slower (779);
+//   FP64: one-warp blocks everywhere and programmatic launch only for grids of at most
+//     16 blocks (the coarse tail, the coarsest levels' one-warp launches): 341 steps/s
+//     at 1024^2 (scheme 1) against 328 with programmatic launch up to 4 x SMs blocks and
+//     315 for every grid; 756 against 689 at 512^2, 662 against 613 for scheme 2 at
+//     512^2, 111 against 109 at 2048^2; only grids of about 128^2 gain from it (1466
+//     against 1501 steps/s there).  (An earlier driver favoured 4 x SMs: 743 against
+//     822 us per V-cycle with 32 x 8 blocks and none.)
 //   FP32 inner cycles (memory-latency bound, they want occupancy): 32 x 4 blocks and the
 //     same programmatic launch, 472 us per outer iteration against 479 (32 x 8, none)
 //     and 725 with one-warp blocks;
@@ -320,9 +324,8 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
 //   the FP32 inner cycles' levels of at most 32 x 32 cells in one CTA with the levels in
 //     shared memory: 430 us per outer iteration at 1024^2 against 475 (64 x 64: 457).
 mpfc_launch_shape mpfc_default_launch_shape(int precision) {
-  const int pdl = 4 * mpfc::sm_count();
-  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, pdl, 32 * 32, 1};
-  return mpfc_launch_shape{1, 0, pdl, 256, 1};
+  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * mpfc::sm_count(), 32 * 32, 1};
+  return mpfc_launch_shape{1, 0, 16, 256, 1};
 }
 
 // The coarsest grid's matrices for one scheme as the FP32 block the coarse solves read:
