@@ -600,7 +600,6 @@ __global__ void k_guess_gate(const Ctl* ctl, double threshold, cudaGraphConditio
   if (threadIdx.x == 0) cudaGraphSetConditional(h, (ctl->status == 0 && ctl->res0 >= threshold) ? 1u : 0u);
 }
 
-
 // Whether the step runs the learned guess behind its gate (FP64 handles).
 static bool guess_gated(const mpfc_s* H) {
   return H->p.guess == MPFC_GUESS_LEARNED && H->p.precision == MPFC_FP64 && H->guess_gate > 0.0;
