@@ -49,6 +49,34 @@ def test_fp32_inner_matches_fp64_oracle(mp, oracle_mod, scheme, m, n, h, s, step
         assert e <= BOUND, (k, e)
 
 
+@pytest.mark.parametrize("inner", [1, 3, 4, 6])
+@pytest.mark.parametrize("scheme,m,s", [(1, 128, 0.02), (2, 96, 1.0)])
+def test_fp32_inner_cycle_counts_match_fp64_oracle(mp, oracle_mod, inner, scheme, m, s):
+    """Other numbers of FP32 inner V-cycles per FP64 outer iteration (the benchmark runs
+    3 and 4 on some workloads) reach the same tolerance and stay within the mixed form's
+    1e-8 of the oracle solved to 1e-13, step by step; the outer iterations per step do
+    not grow with more inner cycles."""
+    n = m
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 1)
+    outers = {}
+    for ic in (2, inner):
+        g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=s, precision=mp.MPFC_FP32_INNER, inner_cycles=ic))
+        g.set_state(phi0)
+        o = oracle_mod.Solver(oracle_mod.Params(m=m, n=n, h=0.5, s=s))
+        o.set_state(phi0)
+        cyc = []
+        for k in range(4):
+            info = g.step(scheme, 1)[0]
+            assert info["status"] == 0 and info["res"] <= 1e-10
+            cyc.append(info["cycles"])
+            assert o.step(scheme, tol=1e-13, guess=1)["status"] == 0
+            assert relerr(g.get_state()[0], o.get_state()[0]) <= BOUND, (ic, k)
+        outers[ic] = sum(cyc)
+        g.close()
+    if inner > 2:
+        assert outers[inner] <= outers[2], outers
+
+
 def test_fp32_inner_stream_mode_matches_graph(mp):
     m = 64
     phi0 = inputs.noise_field(m, m, 0.07, 0.05, 1)
