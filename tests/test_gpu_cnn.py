@@ -266,6 +266,34 @@ def test_learned_guess_gate(G):
         g.set_guess_gate(1.0)
 
 
+def test_learned_guess_gate_scheme2(G):
+    """The gate's two bitwise limits for the second-order scheme (whose step also
+    restricts phi^k to the coarse levels) at 256^2: a gate above every residual gives
+    the extrapolated guess's steps, one below every residual the ungated network's."""
+    from paper_1208_2643_gb300 import inputs, mpfc
+    blob = G.load()
+    m = 256
+    phi0 = inputs.noise_field(m, m, 0.07, 0.05, 3)
+
+    def run(gs, gate=None):
+        g = mpfc.Solver(mpfc.default_params(m=m, n=m, h=0.5, dt=0.05, guess=gs))
+        if gs == mpfc.MPFC_GUESS_LEARNED:
+            G.attach(g, blob)
+            g.set_guess_gate(gate)
+        g.set_state(phi0)
+        infos = g.step(2, 4)
+        assert all(i["status"] == 0 for i in infos)
+        st = g.get_state()
+        g.close()
+        return [(i["cycles"], i["res0"]) for i in infos], st
+
+    for (a, sa), (b, sb) in ((run(mpfc.MPFC_GUESS_LEARNED, 1e30), run(mpfc.MPFC_GUESS_EXTRAP)),
+                             (run(mpfc.MPFC_GUESS_LEARNED, 1e-300), run(mpfc.MPFC_GUESS_LEARNED, 0.0))):
+        assert a == b
+        for x, y in zip(sa, sb):
+            assert np.array_equal(x, y)
+
+
 @pytest.fixture
 def tensor_path(G):
     """Yields a setter of the 32 -> 32 convolutions' tensor-core path; restores tcgen05."""
