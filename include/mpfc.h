@@ -211,6 +211,16 @@ int mpfc_fp32_test_withhold_copy(int withhold, long long spin_cycles);
  * next step).  Returns MPFC_ERR_INVALID for other values. */
 int mpfc_set_launch_shape(mpfc_t* h, int rows, int small_cells, int pdl_blocks, int tail_cells, int tail_ctas);
 
+/* Thread layout of the FP64 V-cycle's grid transfers (App. B: the FAS restriction of u and
+ * of the residual, and the bilinear prolongation of the correction; a tuning choice:
+ * results do not depend on it, bit for bit).  Onto or from fine levels of at most
+ * fine_cells cells that run as per-level launches, the restriction takes four threads per
+ * coarse cell and the prolongation one thread per fine cell, which shortens each thread's
+ * FP64 chain on small levels; larger levels keep one thread per coarse cell.  0: never.
+ * Default 256 x 256 (65536) for FP64 handles.  Kept by mpfc_set_launch_shape.  Drops the handle's captured graphs.  MPFC_ERR_INVALID
+ * for a negative value. */
+int mpfc_set_transfer_split(mpfc_t* h, int fine_cells);
+
 /* One step with exactly ncycles V-cycles (no tolerance test), for lockstep
  * comparisons.  Same state update and synchronisation as mpfc_step. */
 int mpfc_step_cycles(mpfc_t* h, int scheme, int ncycles, mpfc_step_info* info);

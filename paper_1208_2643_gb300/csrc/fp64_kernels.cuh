@@ -222,6 +222,69 @@ __global__ void k_resid_restrict(Lev F, Lev C, Coef kf, int keep_b) {
   resid_restrict_cell<SCH>(F, C, kf, keep_b, I, J);
 }
 
+// The same restriction with four threads per coarse cell, for small levels, where a
+// launch lasts about the FP64 latency of one thread's chain (a warp-wide FP64
+// instruction holds its sub-partition's pipe for some 80 cycles, however many lanes are
+// active).  Lanes 4c .. 4c+3 of a warp serve one coarse cell: lane q < 3 forms the block
+// and border sums of field q (phi, mu, kappa) and the block sum of S_{q+1}; lane q loads
+// the values of fine cell q = 2 dj + di of the block, and every lane sums the nonlinear
+// term of the four in order; the partner lanes' sums, shuffled in, then give lane q row
+// q + 1 of the restricted residual.  Each sum keeps the association of
+// resid_restrict_cell, so the bits are the same.  Blocks are one warp (32 x 1); lane 3
+// and quads past the grid compute on clamped indices and write nothing (the shuffles
+// take the whole warp).
+template <int SCH>
+__global__ void __launch_bounds__(32) k_resid_restrict4(Lev F, Lev C, Coef kf, int keep_b) {
+  pdl_enter();
+  const unsigned FULL = 0xffffffffu;
+  const int q = threadIdx.x & 3, base = threadIdx.x & ~3;
+  const int Iq = (blockIdx.x * 32 + threadIdx.x) >> 2, J = blockIdx.y;
+  const bool live = Iq < C.m && q < 3;
+  const int I = Iq < C.m ? Iq : C.m - 1;
+  const int m = F.m, i0 = 2 * I, j0 = 2 * J;
+  const int iw = wrapm(i0 - 1, m), ie = wrapm(i0 + 2, m);
+  const int js = ywrap(j0 - 1, F.n, F.nyn), jn = ywrap(j0 + 2, F.n, F.nyn);
+  const size_t r0 = (size_t)j0 * m, r1 = r0 + m, rs = (size_t)js * m, rn = (size_t)jn * m;
+  const double* f = q == 1 ? F.mu : q == 2 ? F.ka : F.phi;
+  const double* S = q == 1 ? F.S2 : q == 2 ? F.S3 : F.S1;
+  const double blk = (__ldg(f + r0 + i0) + __ldg(f + r0 + i0 + 1)) + (__ldg(f + r1 + i0) + __ldg(f + r1 + i0 + 1));
+  const double outer = ((__ldg(f + r0 + iw) + __ldg(f + r1 + iw)) + (__ldg(f + r0 + ie) + __ldg(f + r1 + ie))) +
+                       ((__ldg(f + rs + i0) + __ldg(f + rs + i0 + 1)) + (__ldg(f + rn + i0) + __ldg(f + rn + i0 + 1)));
+  const double ss = (__ldg(S + r0 + i0) + __ldg(S + r0 + i0 + 1)) + (__ldg(S + r1 + i0) + __ldg(S + r1 + i0 + 1));
+  // the nonlinear sum in resid_restrict_cell's form (its additions take the cubic's last
+  // product fused), from the four cells' values loaded one per lane
+  const size_t idq = ((q & 2) ? r1 : r0) + i0 + (q & 1);
+  const double pq = __ldg(F.phi + idq);
+  const double pkq = (SCH == 2) ? __ldg(F.pk + idq) : 0.0;
+  const double wq = (SCH == 2 && F.W) ? __ldg(F.W + idq) : 0.0;
+  double gs = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double p = __shfl_sync(FULL, pq, base + c);
+    const double pk = (SCH == 2) ? __shfl_sync(FULL, pkq, base + c) : 0.0;
+    gs += g_of<SCH>(p, pk);
+    if (SCH == 2 && F.W) gs = fma(__shfl_sync(FULL, wq, base + c), p, gs);
+  }
+  // row q + 1 takes the block and border sums of field (q + 1) mod 3, row 2 also phi's
+  // block sum:
+  //   sr1 = cmu (om - 2 sm) + (ss1 - sp)
+  //   sr2 = ih2 (ok - 2 sk) + ((gam sp + (ss2 - sm)) + gs)
+  //   sr3 = th2 (op - 2 sp) + (ss3 - sk)
+  const int nxt = base + (q == 0 ? 1 : q == 1 ? 2 : 0);
+  const double X = __shfl_sync(FULL, blk, nxt), Y = __shfl_sync(FULL, outer, nxt);
+  const double sp = __shfl_sync(FULL, blk, base);
+  const double z0 = ss - blk;
+  const double Z = (q == 1) ? fma(kf.gam, sp, z0) + gs : z0;
+  const double cq = q == 0 ? kf.cmu : q == 1 ? kf.ih2 : kf.th2;
+  const double sr = fma(cq, fma(-2.0, X, Y), Z);
+  if (!live) return;
+  const size_t cid = (size_t)J * C.m + I;
+  const double u = 0.25 * blk;
+  (q == 0 ? C.phi : q == 1 ? C.mu : C.ka)[cid] = u;
+  if (keep_b) (q == 0 ? C.b1 : q == 1 ? C.b2 : C.b3)[cid] = u;
+  (q == 0 ? C.S1 : q == 1 ? C.S2 : C.S3)[cid] = 0.25 * sr;
+}
+
 // FAS restriction, part 2: S_c += N_c(u_c).
 template <int SCH, int LD = kLdNC>
 __device__ __forceinline__ void tau_cell(const Lev& C, const Coef& k, int i, int j) {
@@ -343,6 +406,18 @@ __device__ __forceinline__ void prolong_fine_plane(const double* cn, const doubl
   const double w9 = 9.0 / 16.0, w3 = 3.0 / 16.0, w1 = 1.0 / 16.0;
   const size_t id = (size_t)fj * (2 * mc) + fi;
   f[id] = ldown<LD>(f + id) + fma(w3, ex + ey, fma(w1, exy, w9 * e00));
+}
+
+// The correction with one thread per fine cell (its three components), for small levels:
+// a thread's chain is about half the FP64 instructions of a coarse cell's thread in
+// k_prolong, over four times the threads.  Same bits as k_prolong.
+static __global__ void k_prolong_fine(ProlongArgs A) {
+  pdl_enter();
+  const int fi = blockIdx.x * blockDim.x + threadIdx.x, fj = blockIdx.y * blockDim.y + threadIdx.y;
+  if (fi >= 2 * A.mc || fj >= 2 * A.nc) return;
+  prolong_fine_plane<kLdPlain>(A.cphi, A.ophi, A.fphi, A.mc, A.nc, A.nyn, fi, fj);
+  prolong_fine_plane<kLdPlain>(A.cmu, A.omu, A.fmu, A.mc, A.nc, A.nyn, fi, fj);
+  prolong_fine_plane<kLdPlain>(A.cka, A.oka, A.fka, A.mc, A.nc, A.nyn, fi, fj);
 }
 
 // ---------------------------------------------------------------------------

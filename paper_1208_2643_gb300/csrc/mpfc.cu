@@ -324,8 +324,10 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
 //   the FP32 inner cycles' levels of at most 32 x 32 cells in one CTA with the levels in
 //     shared memory: 430 us per outer iteration at 1024^2 against 475 (64 x 64: 457).
 mpfc_launch_shape mpfc_default_launch_shape(int precision) {
-  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * mpfc::sm_count(), 32 * 32, 1};
-  return mpfc_launch_shape{1, 0, 16, 256, 1};
+  if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * mpfc::sm_count(), 32 * 32, 1, 0};
+  // split transfers up to 256^2 fine cells: 2.917 against 2.975 ms per step at 1024^2
+  // (0: 2.975, 64^2: 2.934, 128^2: 2.920, 512^2: 2.962, 1024^2: 3.160)
+  return mpfc_launch_shape{1, 0, 16, 256, 1, 256 * 256};
 }
 
 // The coarsest grid's matrices for one scheme as the FP32 block the coarse solves read:
@@ -573,8 +575,12 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
     launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu1, s);
-    mpfc_launch(sh, k_resid_restrict<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C,
-                H->coef[SCH - 1][l], 1);
+    if ((long long)F.m * F.n <= sh.split_cells)
+      mpfc_launch(sh, k_resid_restrict4<SCH>, dim3((4 * C.m + 31) / 32, C.n), dim3(32), 0, s, F, C,
+                  H->coef[SCH - 1][l], 1);
+    else
+      mpfc_launch(sh, k_resid_restrict<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, F, C,
+                  H->coef[SCH - 1][l], 1);
     mpfc_launch(sh, k_tau<SCH>, mpfc_grid_of(sh, C.m, C.n), mpfc_blk_for(sh, C.m, C.n), 0, s, C, H->coef[SCH - 1][l + 1]);
   }
   {
@@ -587,7 +593,10 @@ static void enqueue_vcycle(mpfc_s* H, cudaStream_t s) {
     const Lev& F = H->lev[l];
     const Lev& C = H->lev[l + 1];
     ProlongArgs A{C.phi, C.mu, C.ka, C.b1, C.b2, C.b3, F.phi, F.mu, F.ka, C.m, C.n, C.nyn};
-    mpfc_launch(sh, k_prolong, grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s, A);
+    if ((long long)F.m * F.n <= sh.split_cells)
+      mpfc_launch(sh, k_prolong_fine, mpfc_grid_of(sh, F.m, F.n), mpfc_blk_for(sh, F.m, F.n), 0, s, A);
+    else
+      mpfc_launch(sh, k_prolong, grid_for(C.m, C.n, kBlk2d), kBlk2d, 0, s, A);
     launch_smooth<SCH>(sh, F, H->coef[SCH - 1][l], H->coefb[SCH - 1][l], p.nu2, s,
                        (l == 0 && vcycle_fuses_norm(H)) ? H->bpart : nullptr);
   }
@@ -864,7 +873,14 @@ extern "C" int mpfc_set_launch_shape(mpfc_t* H, int rows, int small_cells, int p
       tail_cells < 0 || (tail_ctas != 1 && tail_ctas != 8 && tail_ctas != 16))
     return MPFC_ERR_INVALID;
   if (tail_ctas > mpfc_tail_max_ctas()) return MPFC_ERR_INVALID;
-  H->shape = mpfc_launch_shape{rows, small_cells, pdl_blocks, tail_cells, tail_ctas};
+  H->shape = mpfc_launch_shape{rows, small_cells, pdl_blocks, tail_cells, tail_ctas, H->shape.split_cells};
+  mpfc_drop_graphs(H);
+  return MPFC_OK;
+}
+
+extern "C" int mpfc_set_transfer_split(mpfc_t* H, int fine_cells) {
+  if (!H || fine_cells < 0) return MPFC_ERR_INVALID;
+  H->shape.split_cells = fine_cells;
   mpfc_drop_graphs(H);
   return MPFC_OK;
 }

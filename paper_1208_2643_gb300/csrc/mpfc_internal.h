@@ -54,6 +54,8 @@ struct mpfc_launch_shape {
   int pdl_blocks;    // programmatic dependent launch for grids of at most this many blocks
   int tail_cells;    // levels of at most this many cells run in one cluster launch (0: none)
   int tail_ctas;     // CTAs of that cluster (8, or 16 where the GPU allows it)
+  int split_cells;   // FP64 transfers onto or from fine levels of at most this many cells:
+                     // four threads per coarse cell (restriction), one per fine cell (prolongation)
 };
 
 struct mpfc_s {

@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
     lib.mpfc_fp32_time_smooth.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     lib.mpfc_launch_counts.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.mpfc_set_launch_shape.argtypes = [_VP] + [ctypes.c_int] * 5
+    lib.mpfc_set_transfer_split.argtypes = [_VP, ctypes.c_int]
     lib.mpfc_set_guess_gate.argtypes = [_VP, ctypes.c_double]
     lib.mpfc_set_fp32_sweep.argtypes = [_VP, ctypes.c_int, ctypes.c_int]
     lib.mpfc_fp32_test_withhold_copy.argtypes = [ctypes.c_int, ctypes.c_longlong]
@@ -286,6 +287,11 @@ class Solver:
         levels (at most tail_cells cells) run as one launch of tail_ctas CTAs."""
         _check(self.lib.mpfc_set_launch_shape(self.h, rows, small_cells, pdl_blocks, tail_cells, tail_ctas),
                "mpfc_set_launch_shape")
+
+    def set_transfer_split(self, fine_cells: int):
+        """FP64 grid transfers onto or from fine levels of at most fine_cells cells with four
+        threads per coarse cell (restriction) and one per fine cell (prolongation)."""
+        _check(self.lib.mpfc_set_transfer_split(self.h, fine_cells), "mpfc_set_transfer_split")
 
     def set_fp32_sweep(self, tile_rows: int, min_cells: int = 0):
         """Mixed-precision handles: inner sweeps as one launch over 64 x tile_rows tiles

@@ -472,6 +472,52 @@ def test_tail_cluster_is_bitwise_the_per_level_cycle(mp, case, ctas):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("case", ["periodic1", "periodic2", "ragged1", "ragged2", "neumann2", "pinned2"])
+def test_transfer_split_is_bitwise_the_per_coarse_cell_transfers(mp, case):
+    """The restriction with four threads per coarse cell and the prolongation with one
+    thread per fine cell give exactly the bits of the one-thread-per-coarse-cell kernels,
+    over several steps: on every per-level launch (no tail, down to a 6 x 10 coarsest
+    grid on the ragged case, where a warp's last quads lie past the grid), on the levels
+    of at most 64^2 cells only, and beside the default coarse tail."""
+    scheme = int(case[-1])
+    m, n = (96, 160) if case.startswith("ragged") else (128, 128)
+    kw = {}
+    if case.startswith("neumann"):
+        kw["bc"] = mp.MPFC_BC_NEUMANN_Y
+    if case.startswith("pinned"):
+        kw["pinning"] = 1
+    phi0 = inputs.noise_field(m, n, 0.07, 0.05, 13)
+    runs = []
+    for tail_cells, split in ((0, 0), (0, 1 << 30), (0, 64 * 64), (256, 1 << 30)):
+        g = mp.Solver(mp.default_params(m=m, n=n, h=0.5, dt=0.05, **kw))
+        if case.startswith("pinned"):
+            W = np.zeros((n, m))
+            W[:10] = 2.0
+            W[-10:] = 2.0
+            g.set_pinning(W, inputs.noise_field(m, n, 0.1, 0.05, 4))
+        g.set_launch_shape(1, 0, 16, tail_cells, 1)
+        g.set_transfer_split(split)
+        g.set_state(phi0)
+        infos = g.step(scheme, 3)
+        assert all(i["status"] == 0 for i in infos)
+        runs.append(([i["cycles"] for i in infos], g.get_state()))
+        g.close()
+    for cyc, st in runs[1:]:
+        assert cyc == runs[0][0]
+        for a, b in zip(st, runs[0][1]):
+            assert np.array_equal(a, b)
+
+
+def test_transfer_split_rules(mp):
+    g = mp.Solver(mp.default_params(m=64, n=64))
+    with pytest.raises(mp.MPFCError):
+        g.set_transfer_split(-1)
+    g.set_transfer_split(1 << 20)
+    g.set_launch_shape(1, 0, 16, 0, 1)
+    assert g.launch_counts(1) == (6, 4 * 11 + 2)   # the same launches, other thread layouts
+    g.close()
+
+
 def test_launch_counts(mp):
     """Kernels per step and per V-cycle under the default launch shape: 64^2 has levels
     64, 32, 16, 8, 4; the levels of at most 16 x 16 cells run as one launch, so two
