@@ -326,8 +326,11 @@ void mpfc_build_K3(const Lev& C, const Coef& k, std::vector<double>& K3) {
 mpfc_launch_shape mpfc_default_launch_shape(int precision) {
   if (precision == MPFC_FP32_INNER) return mpfc_launch_shape{4, 0, 4 * mpfc::sm_count(), 32 * 32, 1, 0};
   // split transfers up to 256^2 fine cells: 2.917 against 2.975 ms per step at 1024^2
-  // (0: 2.975, 64^2: 2.934, 128^2: 2.920, 512^2: 2.962, 1024^2: 3.160)
-  return mpfc_launch_shape{1, 0, 16, 256, 1, 256 * 256};
+  // (0: 2.975, 64^2: 2.934, 128^2: 2.920, 512^2: 2.962, 1024^2: 3.160); with them,
+  // programmatic launch up to 128 blocks (the split kernels' grids on levels up to 64^2):
+  // 2.916 against 2.926 ms with 16 blocks, 3.003 with 256 (the 128^2 sweeps), and 1.853
+  // against 1.864 ms for scheme 2 at 512^2; tails from 8^2 and 32^2 stay slower
+  return mpfc_launch_shape{1, 0, 128, 256, 1, 256 * 256};
 }
 
 // The coarsest grid's matrices for one scheme as the FP32 block the coarse solves read:
