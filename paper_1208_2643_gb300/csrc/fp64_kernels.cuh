@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(32) k_resid_restrict4(Lev F, Lev C, Coef kf, i
   const double outer = ((__ldg(f + r0 + iw) + __ldg(f + r1 + iw)) + (__ldg(f + r0 + ie) + __ldg(f + r1 + ie))) +
                        ((__ldg(f + rs + i0) + __ldg(f + rs + i0 + 1)) + (__ldg(f + rn + i0) + __ldg(f + rn + i0 + 1)));
   const double ss = (__ldg(S + r0 + i0) + __ldg(S + r0 + i0 + 1)) + (__ldg(S + r1 + i0) + __ldg(S + r1 + i0 + 1));
-  // the nonlinear sum in resid_restrict_cell's form (its additions take the cubic's last
-  // product fused), from the four cells' values loaded one per lane
+  // the nonlinear sum written exactly as in resid_restrict_cell (an addition of the cubic,
+  // which the compiler may fuse with the cubic's last product, so the form must match),
+  // from the four cells' values loaded one per lane
   const size_t idq = ((q & 2) ? r1 : r0) + i0 + (q & 1);
   const double pq = __ldg(F.phi + idq);
   const double pkq = (SCH == 2) ? __ldg(F.pk + idq) : 0.0;
